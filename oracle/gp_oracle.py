@@ -1,0 +1,442 @@
+"""Plain FP64 CPU oracle for the sparse exact-GP hot path of arXiv 2205.09070.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute this module: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference arm of ``bench.py`` use it.  It shares no code, constants
+or helpers with the CUDA library; the two meet only through the seeded input
+generators, which hold none of the method's arithmetic.
+
+Everything is float64 numpy, written for a reader to check against the paper
+by eye: brute-force O(N^2) pair enumeration, dense matrices, dense Cholesky.
+
+Paper sections used (arXiv 2205.09070):
+  * Sec. 2.1, Eq. (eqn:log_likelihood): ln L = -1/2 y^T K^-1 y - 1/2 ln|K|
+    (additive constant dropped, prior mean m = 0).
+  * Sec. 2.2, Eq. (eq:bump_kernel): k_s = k~(x1,x2) * sum_i f_i(x1) f_i(x2).
+  * Sec. 2.2, Eq. (eq:bump): f_i(x) = sum_j a_ij exp[beta - beta/(1-|x-x0|^2/r^2)]
+    times the indicator of the bump's support.
+  * Sec. 2.2, Eq. (eq:kstat): the compactly supported stationary kernel k~.
+  * Sec. 2.2, Eq. (eq:sparsity_estimate) and the two equations after it: the
+    sparsity upper bound used as a statistical check.
+  * Sec. 2.5: CG for K x = y and a randomized log-determinant.
+
+Readings where the paper is silent, garbled or inconsistent (each is listed in
+the design doc as well):
+  * Eq. (eq:bump) prints the indicator as chi(r < |x - x0|); the text calls the
+    bumps compactly supported, so the support is the open ball |x - x0| < r.
+  * beta is a fixed shape constant (default 1), not a hyperparameter: the
+    climate example counts 42 hyperparameters for n1=2, n2=4 in 3-D
+    (Sec. 3), which is 2*4*(3+2) + 2 with no beta.
+  * K carries a stationary amplitude A and observation noise sigma_n^2 on the
+    diagonal: K = A * k~ * sum_m f_m f_m^T + sigma_n^2 I  (V = sigma_n^2 I of
+    Eq. eq:likelihoodGP folded into K, m = 0).
+  * The stationary support test is strict (d < r), as printed in Eq. (eq:kstat).
+  * The sparsity pattern is the support predicate {i == j} union
+    {d_ij < r_s and x_i, x_j share the support of some f_m}; entries whose
+    value cancels to zero are still part of the pattern.
+  * The log-determinant estimator is stochastic Lanczos quadrature (SLQ) on the
+    Jacobi-scaled active block, with Rademacher probes from a counter-based
+    SplitMix64 stream; inactive rows (outside every bump) are exact.
+
+Hyperparameter vector layout, P = n1*n2*(dim+2) + 3 doubles:
+  for m < n1, b < n2: [centre_mb[0..dim-1], r_mb, a_mb]; then r_s, A, sigma_n^2.
+
+Parity pins (tests/test_oracle_pins.py) tie every function here to something
+other than itself: an independently derived power series and its derivative,
+closed-form special values, brute-force properties (symmetry, PSD, exact zeros
+for disjoint supports), Euler homogeneity identities, central finite
+differences, eigen-decomposition special cases and the published SplitMix64
+output sequence.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Prefactor of Eq. (eq:kstat): sqrt(2) / (3 sqrt(pi)); it is also k~(0).
+KSTAT_PREFACTOR = math.sqrt(2.0) / (3.0 * math.sqrt(math.pi))
+
+
+# ----------------------------------------------------------------------------
+# hyperparameters
+# ----------------------------------------------------------------------------
+
+def n_params(dim: int, n1: int, n2: int) -> int:
+    """Number of hyperparameters: per bump a centre, a radius and an amplitude
+    (Eq. eq:bump), then the stationary radius r_s, amplitude A and noise."""
+    return n1 * n2 * (dim + 2) + 3
+
+
+def unpack_h(h, dim: int, n1: int, n2: int):
+    """Split the flat hyperparameter vector into its named parts."""
+    h = np.asarray(h, dtype=np.float64)
+    if h.shape != (n_params(dim, n1, n2),):
+        raise ValueError("hyperparameter vector has the wrong length")
+    nb = n1 * n2 * (dim + 2)
+    b = h[:nb].reshape(n1, n2, dim + 2)
+    return {
+        "centres": b[:, :, :dim],
+        "radii": b[:, :, dim],
+        "amps": b[:, :, dim + 1],
+        "r_s": float(h[nb]),
+        "A": float(h[nb + 1]),
+        "sigma2": float(h[nb + 2]),
+    }
+
+
+# ----------------------------------------------------------------------------
+# Eq. (eq:kstat): compactly supported stationary kernel
+# ----------------------------------------------------------------------------
+
+def kstat(rho):
+    """k~ as a function of rho = d / r, exactly as printed in Eq. (eq:kstat):
+
+        sqrt(2)/(3 sqrt(pi)) * (3 rho^2 log(rho / (1 + sqrt(1 - rho^2)))
+                                 + (2 rho^2 + 1) sqrt(1 - rho^2))   if rho < 1
+        0                                                          otherwise.
+
+    At rho = 0 the term rho^2 log(rho) is taken at its limit, 0.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    out = np.zeros_like(rho)
+    inside = rho < 1.0
+    r = rho[inside]
+    s = np.sqrt(1.0 - r * r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        log_term = np.where(r > 0.0, 3.0 * r * r * np.log(r / (1.0 + s)), 0.0)
+    out[inside] = KSTAT_PREFACTOR * (log_term + (2.0 * r * r + 1.0) * s)
+    return out
+
+
+def kstat_drho(rho):
+    """d k~ / d rho for Eq. (eq:kstat), differentiated by hand.
+
+    With s = sqrt(1 - rho^2) and ds/drho = -rho/s, the derivative of the
+    bracket collapses to 6 rho log(rho/(1+s)) + 6 rho s; since
+    rho/(1+s) = sqrt((1-s)/(1+s)), log(rho/(1+s)) = -atanh(s), so
+    d k~/d rho = 6 C rho (s - atanh(s)) for rho < 1 and 0 outside.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    out = np.zeros_like(rho)
+    inside = rho < 1.0
+    r = rho[inside]
+    s = np.sqrt(1.0 - r * r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        # at rho = 0, rho * atanh(1) is taken at its limit, 0
+        out[inside] = np.where(r > 0.0, 6.0 * KSTAT_PREFACTOR * r * (s - np.arctanh(s)), 0.0)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Eq. (eq:bump): bump functions
+# ----------------------------------------------------------------------------
+
+def bump_phi(x, centre, radius, amp, beta=1.0):
+    """One bump a * exp(beta - beta / (1 - |x - c|^2 / r^2)) on the open ball
+    |x - c| < r, zero elsewhere (Eq. eq:bump with the support reading above).
+    Returns (phi, inside) for points x of shape (N, dim)."""
+    x = np.asarray(x, dtype=np.float64)
+    q = np.sum((x - centre) ** 2, axis=1) / (radius * radius)
+    inside = q < 1.0
+    phi = np.zeros(x.shape[0])
+    u = 1.0 - q[inside]
+    phi[inside] = amp * np.exp(beta - beta / u)
+    return phi, inside
+
+
+def bump_phi_grads(x, centre, radius, amp, beta=1.0):
+    """Partial derivatives of one bump w.r.t. its centre (N, dim), radius (N,)
+    and amplitude (N,), differentiated by hand from Eq. (eq:bump):
+    with q = |x-c|^2/r^2 and u = 1-q, d phi/d q = -beta phi / u^2, so
+      d phi / d c_k = 2 beta phi (x_k - c_k) / (r^2 u^2)
+      d phi / d r   = 2 beta phi q / (r u^2)
+      d phi / d a   = phi / a  (= exp(beta - beta/u)).
+    All three vanish outside the support."""
+    x = np.asarray(x, dtype=np.float64)
+    n, dim = x.shape
+    diff = x - centre
+    q = np.sum(diff ** 2, axis=1) / (radius * radius)
+    inside = q < 1.0
+    d_c = np.zeros((n, dim))
+    d_r = np.zeros(n)
+    d_a = np.zeros(n)
+    u = 1.0 - q[inside]
+    e = np.exp(beta - beta / u)
+    phi = amp * e
+    d_c[inside] = (2.0 * beta * phi / (radius * radius * u * u))[:, None] * diff[inside]
+    d_r[inside] = 2.0 * beta * phi * q[inside] / (radius * u * u)
+    d_a[inside] = e
+    return d_c, d_r, d_a
+
+
+def bump_table(x, h, dim, n1, n2, beta=1.0):
+    """F[i, m] = f_m(x_i) (Eq. eq:bump) and the support mask
+    M_i = sum over m of 2^m [x_i lies in the support of some bump of f_m]."""
+    p = unpack_h(h, dim, n1, n2)
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    F = np.zeros((n, n1))
+    mask = np.zeros(n, dtype=np.int64)
+    for m in range(n1):
+        in_m = np.zeros(n, dtype=bool)
+        for b in range(n2):
+            phi, inside = bump_phi(x, p["centres"][m, b], p["radii"][m, b], p["amps"][m, b], beta)
+            F[:, m] += phi
+            in_m |= inside
+        mask |= in_m.astype(np.int64) << m
+    return F, mask
+
+
+# ----------------------------------------------------------------------------
+# Eq. (eq:bump_kernel) with Eq. (eq:kstat): the covariance matrix K
+# ----------------------------------------------------------------------------
+
+def pair_rows(x, h, dim, n1, n2, rows, beta=1.0):
+    """Brute force over all N columns for the given rows (original order).
+
+    Returns (pattern, values) of shape (len(rows), N):
+      pattern[a, j] = (j == rows[a]) or (d^2 < r_s^2 and M_i & M_j != 0)
+      values[a, j]  = A k~(d / r_s) sum_m F_im F_jm + sigma_n^2 [j == rows[a]]
+    """
+    p = unpack_h(h, dim, n1, n2)
+    x = np.asarray(x, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    F, mask = bump_table(x, h, dim, n1, n2, beta)
+    d2 = np.sum((x[rows, None, :] - x[None, :, :]) ** 2, axis=2)
+    diag = rows[:, None] == np.arange(x.shape[0])[None, :]
+    pattern = diag | ((d2 < p["r_s"] ** 2) & ((mask[rows, None] & mask[None, :]) != 0))
+    rho = np.sqrt(d2) / p["r_s"]
+    S = np.zeros(d2.shape)
+    for m in range(n1):                       # sum_m f_m(x_i) f_m(x_j), term by term
+        S += F[rows, m][:, None] * F[:, m][None, :]
+    vals = p["A"] * kstat(rho) * S + p["sigma2"] * diag
+    vals = np.where(pattern, vals, 0.0)
+    return pattern, vals
+
+
+def assemble_csr(x, h, dim, n1, n2, beta=1.0, chunk=512):
+    """CSR of K in original point order with ascending columns, by brute force
+    over all N^2 pairs (chunked over rows to bound memory).
+    Returns (row_ptr int64 [N+1], col int64 [nnz], val float64 [nnz])."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    cols, vals = [], []
+    for start in range(0, n, chunk):
+        rows = np.arange(start, min(n, start + chunk))
+        pat, v = pair_rows(x, h, dim, n1, n2, rows, beta)
+        r_idx, c_idx = np.nonzero(pat)
+        cols.append(c_idx.astype(np.int64))
+        vals.append(v[r_idx, c_idx])
+        row_ptr[rows + 1] = np.sum(pat, axis=1)
+    row_ptr = np.cumsum(row_ptr)
+    col = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    val = np.concatenate(vals) if vals else np.zeros(0)
+    return row_ptr, col, val
+
+
+def dense_K(x, h, dim, n1, n2, beta=1.0):
+    """Dense K (N x N) by brute force; entries outside the pattern are zero."""
+    x = np.asarray(x, dtype=np.float64)
+    _, vals = pair_rows(x, h, dim, n1, n2, np.arange(x.shape[0]), beta)
+    return vals
+
+
+# ----------------------------------------------------------------------------
+# Eq. (eqn:log_likelihood): exact LML and its exact gradient
+# ----------------------------------------------------------------------------
+
+def lml_exact(K, y):
+    """-1/2 y^T K^-1 y - 1/2 ln|K| by dense Cholesky (Sec. 2.1, Sec. 2.5)."""
+    L = np.linalg.cholesky(K)
+    w = np.linalg.solve(L, y)
+    return -0.5 * float(w @ w) - float(np.sum(np.log(np.diag(L))))
+
+
+def dK_dtheta_all(x, h, dim, n1, n2, beta=1.0):
+    """Yield (index, dK) for every hyperparameter, dK dense N x N, from the
+    chain rule on K = A k~(d/r_s) sum_m F_m F_m^T + sigma_n^2 I."""
+    p = unpack_h(h, dim, n1, n2)
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[0]
+    F, _ = bump_table(x, h, dim, n1, n2, beta)
+    d = np.sqrt(np.sum((x[:, None, :] - x[None, :, :]) ** 2, axis=2))
+    rho = d / p["r_s"]
+    kt = kstat(rho)
+    A = p["A"]
+    idx = 0
+    for m in range(n1):
+        for b in range(n2):
+            d_c, d_r, d_a = bump_phi_grads(x, p["centres"][m, b], p["radii"][m, b], p["amps"][m, b], beta)
+            for dphi in [d_c[:, k] for k in range(dim)] + [d_r, d_a]:
+                dS = np.outer(dphi, F[:, m]) + np.outer(F[:, m], dphi)
+                yield idx, A * kt * dS
+                idx += 1
+    S = np.zeros((n, n))
+    for m in range(n1):
+        S += np.outer(F[:, m], F[:, m])
+    yield idx, A * (kstat_drho(rho) * (-rho / p["r_s"])) * S      # r_s
+    yield idx + 1, kt * S                                          # A
+    yield idx + 2, np.eye(n)                                       # sigma_n^2
+
+
+def lml_grad_exact(x, y, h, dim, n1, n2, beta=1.0):
+    """Exact ln L and d ln L / d theta = 1/2 alpha^T K_theta alpha
+    - 1/2 tr(K^-1 K_theta), alpha = K^-1 y, via a dense Cholesky inverse."""
+    K = dense_K(x, h, dim, n1, n2, beta)
+    y = np.asarray(y, dtype=np.float64)
+    L = np.linalg.cholesky(K)
+    Linv = np.linalg.solve(L, np.eye(K.shape[0]))
+    Kinv = Linv.T @ Linv
+    alpha = Kinv @ y
+    lml = -0.5 * float(y @ alpha) - float(np.sum(np.log(np.diag(L))))
+    grad = np.zeros(n_params(dim, n1, n2))
+    for i, dK in dK_dtheta_all(x, h, dim, n1, n2, beta):
+        grad[i] = 0.5 * float(alpha @ (dK @ alpha)) - 0.5 * float(np.sum(Kinv * dK))
+    return lml, grad
+
+
+# ----------------------------------------------------------------------------
+# Probes: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) as a counter stream
+# ----------------------------------------------------------------------------
+
+_SM_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_SM_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_SM_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed, k):
+    """k-th output (k = 0, 1, ...) of the SplitMix64 stream whose state starts
+    at `seed`: the state after k+1 increments by the golden gamma, pushed
+    through the published 30/27/31 xor-shift-multiply finaliser."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (np.asarray(k, dtype=np.uint64) + np.uint64(1)) * _SM_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _SM_M1
+        z = (z ^ (z >> np.uint64(27))) * _SM_M2
+        return z ^ (z >> np.uint64(31))
+
+
+def rademacher(seed, n_probes, orig_index):
+    """Rademacher probe matrix Z (len(orig_index) x n_probes) with
+    Z[i, l] = +1 if bit 63 of splitmix64(seed, l * 2^40 + orig_index[i]) is 0
+    and -1 otherwise."""
+    idx = np.asarray(orig_index, dtype=np.uint64)
+    out = np.empty((idx.shape[0], n_probes))
+    for l in range(n_probes):
+        z = splitmix64(seed, np.uint64(l) * np.uint64(1 << 40) + idx)
+        out[:, l] = np.where((z >> np.uint64(63)) == 0, 1.0, -1.0)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Stochastic estimators on the same probes as the GPU path
+# ----------------------------------------------------------------------------
+
+def active_split(K, mask):
+    """Rows with mask 0 lie outside every bump: their row of K is sigma_n^2 on
+    the diagonal only.  Returns (active index array, inactive index array)."""
+    mask = np.asarray(mask)
+    return np.nonzero(mask != 0)[0], np.nonzero(mask == 0)[0]
+
+
+def lanczos_quadrature(Khat, z, m):
+    """Gauss quadrature estimate of z^T log(Khat) z from m Lanczos steps
+    started at z/|z|, with full re-orthogonalisation (Golub & Meurant):
+    T = Q Theta Q^T, estimate = |z|^2 sum_k Q[0,k]^2 log theta_k.
+    Stops early if the Krylov space is exhausted."""
+    n = Khat.shape[0]
+    nz = float(np.linalg.norm(z))
+    V = np.zeros((n, m + 1))
+    V[:, 0] = z / nz
+    a, b = [], []
+    for j in range(m):
+        w = Khat @ V[:, j]
+        if j > 0:
+            w = w - b[-1] * V[:, j - 1]
+        a.append(float(V[:, j] @ w))
+        w = w - a[-1] * V[:, j]
+        for _ in range(2):
+            w = w - V[:, : j + 1] @ (V[:, : j + 1].T @ w)
+        beta = float(np.linalg.norm(w))
+        if j == m - 1 or beta <= 1e-12 * max(1.0, abs(a[-1])):
+            break
+        b.append(beta)
+        V[:, j + 1] = w / beta
+    k = len(a)
+    T = np.diag(a) + np.diag(b[: k - 1], 1) + np.diag(b[: k - 1], -1)
+    theta, Q = np.linalg.eigh(T)
+    return nz * nz * float(np.sum(Q[0, :] ** 2 * np.log(theta)))
+
+
+def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
+                         beta=1.0, with_grad=True):
+    """The stochastic LML and gradient the GPU path estimates, computed densely.
+
+    K splits into the active block K_a (rows inside some bump) and
+    sigma_n^2 I on the inactive rows.  With D = diag(K_a) and
+    Khat = D^-1/2 K_a D^-1/2, and Rademacher probes z_l on the active rows
+    (SplitMix64, original point index as counter):
+      ln|K|  ~  sum log D + (1/nv) sum_l SLQ_m(Khat, z_l) + N_inact log sigma_n^2
+      y^T K^-1 y exact (dense solve)
+      tr(K^-1 K_theta) ~ (1/nv) sum_l z_l^T Khat^-1 Khat_theta z_l
+                         + [inactive rows, exact: N_inact / sigma_n^2 for noise]
+    where Khat_theta = D^-1/2 K_theta D^-1/2 (D held fixed).
+    Returns (lml, grad or None, info dict with the pieces)."""
+    p = unpack_h(h, dim, n1, n2)
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    K = dense_K(x, h, dim, n1, n2, beta)
+    _, mask = bump_table(x, h, dim, n1, n2, beta)
+    act, inact = active_split(K, mask)
+    s2 = p["sigma2"]
+    Ka = K[np.ix_(act, act)]
+    D = np.diag(Ka).copy()
+    Dm = 1.0 / np.sqrt(D)
+    Khat = Ka * Dm[:, None] * Dm[None, :]
+    Z = rademacher(seed, n_probes, act)
+    quad = np.array([lanczos_quadrature(Khat, Z[:, l], lanczos_steps) for l in range(n_probes)]) \
+        if act.size else np.zeros(n_probes)
+    logdet = float(np.sum(np.log(D))) + (float(np.mean(quad)) if act.size else 0.0) \
+        + inact.size * math.log(s2)
+    alpha = np.zeros_like(y)
+    if act.size:
+        alpha[act] = np.linalg.solve(Ka, y[act])
+    alpha[inact] = y[inact] / s2
+    quad_form = float(y @ alpha)
+    lml = -0.5 * quad_form - 0.5 * logdet
+    info = {"logdet": logdet, "quad_form": quad_form, "slq_terms": quad, "n_active": int(act.size),
+            "alpha": alpha}
+    if not with_grad:
+        return lml, None, info
+    # U_hat = Khat^-1 Z; the estimator per parameter is (1/nv) tr(U_hat^T Khat_theta Z).
+    Uhat = np.linalg.solve(Khat, Z) if act.size else np.zeros((0, n_probes))
+    grad = np.zeros(n_params(dim, n1, n2))
+    for i, dK in dK_dtheta_all(x, h, dim, n1, n2, beta):
+        dKa = dK[np.ix_(act, act)]
+        dKhat = dKa * Dm[:, None] * Dm[None, :]
+        tr_act = float(np.sum(Uhat * (dKhat @ Z))) / n_probes if act.size else 0.0
+        tr_inact = float(np.sum(np.diag(dK)[inact])) / s2
+        grad[i] = 0.5 * float(alpha @ (dK @ alpha)) - 0.5 * (tr_act + tr_inact)
+    return lml, grad, info
+
+
+# ----------------------------------------------------------------------------
+# Sparsity estimate (Eq. eq:sparsity_estimate and the two equations after it)
+# ----------------------------------------------------------------------------
+
+def ball_volume(dim, r):
+    """Volume of a dim-dimensional ball: pi^(dim/2) / Gamma(dim/2 + 1) r^dim."""
+    return math.pi ** (dim / 2.0) / math.gamma(dim / 2.0 + 1.0) * r ** dim
+
+
+def sparsity_upper_bound(h, dim, n1, n2, domain_volume=1.0):
+    """sum_i sum_j sum_k Vol(r_ij) Vol(r_ik) / Vol(X)^2: the upper bound on the
+    fraction of non-zero covariances for uniformly distributed points."""
+    p = unpack_h(h, dim, n1, n2)
+    total = 0.0
+    for i in range(n1):
+        v = [ball_volume(dim, r) for r in p["radii"][i]]
+        total += sum(v) ** 2
+    return total / domain_volume ** 2

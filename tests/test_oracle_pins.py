@@ -1,0 +1,331 @@
+"""Pins for the FP64 CPU oracle: each check ties an oracle function to
+something other than itself (an independently derived formula, a closed-form
+special case, a library routine on a special case, a brute-force loop, an
+exact identity, finite differences, or a published test vector)."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gp_oracle as O
+from paper_2205_09070_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def golden():
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+def series_kstat(rho, terms=2000):
+    """k~/C as the positive power series in s = sqrt(1 - rho^2), derived by
+    expanding atanh: sum_{n>=2} 6 s^(2n+1) / ((2n-1)(2n+1))."""
+    s = np.sqrt(1.0 - rho * rho)
+    n = np.arange(2, terms)[:, None]
+    return O.KSTAT_PREFACTOR * np.sum(6.0 * s ** (2 * n + 1) / ((2 * n - 1) * (2 * n + 1)), axis=0)
+
+
+def small_problem(seed=11, n=150, dim=2, n1=2, n2=2, r_s=0.35, radii=(0.3, 0.5), sigma2=1e-2):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (n, dim))
+    y = np.sin(3 * x[:, 0]) + rng.normal(0, 0.1, n)
+    c = rng.uniform(0.2, 0.8, (n1, n2, dim))
+    r = rng.uniform(radii[0], radii[1], (n1, n2))
+    a = rng.normal(0, 1, (n1, n2))
+    h = W.pack_h(c, r, a, r_s, 1.3, sigma2)
+    return x, y, h, dim, n1, n2
+
+
+# --------------------------------------------------------------------- k~
+
+def test_kstat_value_at_zero_matches_paper_prefactor():
+    g = golden()
+    assert O.kstat(np.array([0.0]))[0] == pytest.approx(g["kstat_at_zero"], rel=1e-15)
+
+
+def test_kstat_matches_independent_series():
+    rho = np.linspace(0.45, 0.999999, 4001)
+    ref = series_kstat(rho)
+    got = O.kstat(rho)
+    # the closed form loses digits to cancellation near rho -> 1: compare on
+    # the kernel's own scale k~(0)
+    assert np.max(np.abs(got - ref)) < 1e-14 * O.KSTAT_PREFACTOR
+    mid = rho < 0.95
+    assert np.max(np.abs(got[mid] / ref[mid] - 1.0)) < 1e-12
+
+
+def test_kstat_support_and_monotone():
+    rho = np.linspace(0.0, 1.5, 3001)
+    k = O.kstat(rho)
+    assert np.all(k[rho >= 1.0] == 0.0)
+    assert np.all(k[rho < 1.0] > 0.0)
+    assert np.all(np.diff(k[rho <= 1.0]) <= 0.0)
+
+
+def test_kstat_derivative_fd_and_series():
+    rho = np.linspace(0.01, 0.99, 99)
+    eps = 1e-6
+    fd = (O.kstat(rho + eps) - O.kstat(rho - eps)) / (2 * eps)
+    d = O.kstat_drho(rho)
+    assert np.max(np.abs(fd - d)) < 1e-8
+    # the series converges slowly as s -> 1; check it where 4000 terms suffice
+    r2 = rho[rho >= 0.3]
+    s = np.sqrt(1 - r2 ** 2)
+    n = np.arange(1, 4000)[:, None]
+    ser = -6 * O.KSTAT_PREFACTOR * r2 * np.sum(s ** (2 * n + 1) / (2 * n + 1), axis=0)
+    assert np.max(np.abs(ser - O.kstat_drho(r2))) < 1e-12
+    assert np.all(O.kstat_drho(np.array([1.0, 1.2])) == 0.0)
+
+
+# --------------------------------------------------------------------- bumps
+
+def test_bump_special_values():
+    c = np.array([0.3, 0.4])
+    r, a = 0.2, -1.7
+    for beta in (0.5, 1.0, 3.0):
+        x = np.array([c, c + [r * math.sqrt(0.5), 0.0], c + [r, 0.0], c + [0.0, 1.01 * r]])
+        phi, inside = O.bump_phi(x, c, r, a, beta)
+        assert phi[0] == pytest.approx(a, rel=1e-15)                   # centre: a
+        assert phi[1] == pytest.approx(a * math.exp(-beta), rel=1e-12)  # q = 1/2: a e^-beta
+        assert phi[2] == 0.0 and phi[3] == 0.0                          # on / outside the sphere
+        assert list(inside) == [True, True, False, False]
+
+
+def test_bump_beta_limits():
+    # beta -> 0: the bump becomes a times the indicator of its ball;
+    # beta -> infinity: it vanishes away from the centre (a delta function).
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, (500, 3))
+    c, r, a = np.zeros(3), 0.8, 2.5
+    phi0, inside = O.bump_phi(x, c, r, a, beta=1e-15)
+    assert np.allclose(phi0, a * inside, rtol=1e-9, atol=0)
+    far = np.linalg.norm(x, axis=1) > 0.05
+    phi_inf, _ = O.bump_phi(x, c, r, a, beta=1e4)
+    assert np.max(np.abs(phi_inf[far])) < 1e-300 or np.all(phi_inf[far] == 0)
+
+
+def test_bump_gradients_fd():
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0, 1, (400, 3))
+    c, r, a = np.array([0.5, 0.45, 0.55]), 0.37, 0.8
+    d_c, d_r, d_a = O.bump_phi_grads(x, c, r, a, beta=1.3)
+    eps = 1e-6
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        fd = (O.bump_phi(x, c + e, r, a, 1.3)[0] - O.bump_phi(x, c - e, r, a, 1.3)[0]) / (2 * eps)
+        assert np.max(np.abs(fd - d_c[:, k])) < 1e-7
+    fd = (O.bump_phi(x, c, r + eps, a, 1.3)[0] - O.bump_phi(x, c, r - eps, a, 1.3)[0]) / (2 * eps)
+    assert np.max(np.abs(fd - d_r)) < 1e-7
+    fd = (O.bump_phi(x, c, r, a + eps, 1.3)[0] - O.bump_phi(x, c, r, a - eps, 1.3)[0]) / (2 * eps)
+    assert np.max(np.abs(fd - d_a)) < 1e-8
+
+
+def test_bump_table_sums_and_mask():
+    x, y, h, dim, n1, n2 = small_problem()
+    p = O.unpack_h(h, dim, n1, n2)
+    F, mask = O.bump_table(x, h, dim, n1, n2)
+    for m in range(n1):
+        tot = np.zeros(len(x))
+        ins = np.zeros(len(x), bool)
+        for b in range(n2):
+            # pure-python evaluation of one bump, point by point
+            for i, xi in enumerate(x):
+                q = sum((xi[k] - p["centres"][m, b, k]) ** 2 for k in range(dim)) / p["radii"][m, b] ** 2
+                if q < 1:
+                    tot[i] += p["amps"][m, b] * math.exp(1.0 - 1.0 / (1.0 - q))
+                    ins[i] = True
+        assert np.allclose(F[:, m], tot, rtol=1e-13, atol=0)
+        assert np.array_equal(((mask >> m) & 1).astype(bool), ins)
+
+
+# --------------------------------------------------------------------- K
+
+def test_param_count_matches_climate_example():
+    g = golden()
+    # n1 = 2, n2 = 4, dim = 3 without the noise variance: 42 (Sec. 3)
+    assert O.n_params(3, 2, 4) - 1 == g["climate_param_count_without_noise"]
+    assert O.n_params(3, 4, 8) == 163
+
+
+def test_pattern_matches_pure_python_brute_force():
+    x, y, h, dim, n1, n2 = small_problem(n=90, r_s=0.25)
+    p = O.unpack_h(h, dim, n1, n2)
+    _, mask = O.bump_table(x, h, dim, n1, n2)
+    row_ptr, col, val = O.assemble_csr(x, h, dim, n1, n2, chunk=17)
+    for i in range(len(x)):
+        expect = [j for j in range(len(x))
+                  if j == i or (math.dist(x[i], x[j]) ** 2 < p["r_s"] ** 2 and (mask[i] & mask[j]) != 0)]
+        assert list(col[row_ptr[i]:row_ptr[i + 1]]) == expect
+
+
+def test_K_symmetric_psd_and_unit_bump_separation():
+    for dim in (1, 2, 3):
+        x, y, h, _, n1, n2 = small_problem(seed=20 + dim, n=300, dim=dim, r_s=0.4)
+        K = O.dense_K(x, h, dim, n1, n2)
+        assert np.array_equal(K, K.T)
+        ev = np.linalg.eigvalsh(K)
+        assert ev[0] > -1e-12 * ev[-1]
+    # n1 = n2 = 1: K_ij / (f_i f_j) = A k~(d/r_s) wherever f_i f_j != 0
+    x, y, h, dim, n1, n2 = small_problem(seed=5, n=200, n1=1, n2=1, radii=(0.6, 0.7))
+    p = O.unpack_h(h, dim, n1, n2)
+    K = O.dense_K(x, h, dim, n1, n2) - p["sigma2"] * np.eye(len(x))
+    F, _ = O.bump_table(x, h, dim, n1, n2)
+    f = F[:, 0]
+    nz = np.abs(np.outer(f, f)) > 1e-8
+    d = np.sqrt(np.sum((x[:, None] - x[None]) ** 2, axis=2))
+    rr = np.minimum(d / p["r_s"], 1.0)
+    expect = p["A"] * series_kstat(rr.ravel(), terms=4000).reshape(d.shape)
+    expect[d >= p["r_s"]] = 0
+    far = nz & (rr >= 0.3)                 # where the series has converged
+    ratio = K[far] / np.outer(f, f)[far]
+    assert np.allclose(ratio, expect[far], rtol=1e-9, atol=1e-13)
+    on = np.abs(f) > 1e-4                  # diagonal: A k~(0) f_i^2
+    assert np.allclose(np.diag(K)[on] / f[on] ** 2, p["A"] * golden()["kstat_at_zero"], rtol=1e-13)
+
+
+def test_disjoint_supports_give_exact_zeros():
+    # f_0 lives on the left half, f_1 on the right; points near x = 0.5 are
+    # within r_s of each other but share no function: K must be exactly 0.
+    rng = np.random.default_rng(3)
+    x = np.column_stack([rng.uniform(0.3, 0.7, 400), rng.uniform(0.4, 0.6, 400)])
+    c = np.array([[[0.25, 0.5]], [[0.75, 0.5]]])
+    r = np.array([[0.249], [0.249]])
+    a = np.array([[1.0], [1.0]])
+    h = W.pack_h(c, r, a, 0.2, 1.0, 1e-3)
+    K = O.dense_K(x, h, 2, 2, 1)
+    _, mask = O.bump_table(x, h, 2, 2, 1)
+    cross = (mask[:, None] == 1) & (mask[None, :] == 2)
+    assert cross.sum() > 1000
+    assert np.all(K[cross] == 0.0)
+    near = cross & (np.sum((x[:, None] - x[None]) ** 2, axis=2) < 0.04)
+    assert near.sum() > 100
+
+
+def test_sparsity_bound_holds_for_uniform_points():
+    rng = np.random.default_rng(9)
+    dim, n1, n2 = 2, 2, 3
+    c = rng.uniform(0.25, 0.75, (n1, n2, dim))
+    r = rng.uniform(0.05, 0.12, (n1, n2))
+    a = np.ones((n1, n2))
+    h = W.pack_h(c, r, a, 2.0, 1.0, 1e-3)   # r_s > sqrt(2): stationary term never cuts
+    x = rng.uniform(0, 1, (3000, dim))
+    row_ptr, col, _ = O.assemble_csr(x, h, dim, n1, n2)
+    frac = (row_ptr[-1] - len(x)) / len(x) ** 2
+    bound = O.sparsity_upper_bound(h, dim, n1, n2)
+    assert 0 < frac <= bound * 1.05
+    g = golden()
+    assert O.ball_volume(3, 1.0) == pytest.approx(g["ball_volume_dim3_r1"], rel=1e-15)
+
+
+# --------------------------------------------------------------------- LML
+
+def test_lml_closed_forms():
+    # N = 1: -y^2/(2k) - log(k)/2
+    assert O.lml_exact(np.array([[2.5]]), np.array([1.5])) == pytest.approx(-1.5 ** 2 / 5 - 0.5 * math.log(2.5))
+    # N = 2 via the adjugate inverse and det = ad - b^2
+    a, b, d = 2.0, 0.7, 1.3
+    y = np.array([0.4, -1.1])
+    det = a * d - b * b
+    quad = (d * y[0] ** 2 - 2 * b * y[0] * y[1] + a * y[1] ** 2) / det
+    K = np.array([[a, b], [b, d]])
+    assert O.lml_exact(K, y) == pytest.approx(-0.5 * quad - 0.5 * math.log(det), rel=1e-14)
+
+
+def test_all_inactive_is_exact_noise_model():
+    x, y, h, dim, n1, n2 = small_problem()
+    p = O.unpack_h(h, dim, n1, n2)
+    c = np.full((n1, n2, dim), 5.0)              # every bump far outside the data
+    h2 = W.pack_h(c, p["radii"], p["amps"], p["r_s"], p["A"], p["sigma2"])
+    s2 = p["sigma2"]
+    expect = -0.5 * float(y @ y) / s2 - 0.5 * len(y) * math.log(s2)
+    assert O.lml_exact(O.dense_K(x, h2, dim, n1, n2), y) == pytest.approx(expect, rel=1e-13)
+    lml, grad, info = O.lml_grad_same_probes(x, y, h2, dim, n1, n2, 4, 10, 7)
+    assert lml == pytest.approx(expect, rel=1e-13)
+    assert grad[-1] == pytest.approx(0.5 * float(y @ y) / s2 ** 2 - 0.5 * len(y) / s2, rel=1e-12)
+    assert np.all(grad[:-1] == 0.0)
+
+
+def test_exact_gradient_matches_central_fd():
+    x, y, h, dim, n1, n2 = small_problem(n=120)
+    lml, grad = O.lml_grad_exact(x, y, h, dim, n1, n2)
+    eps = 1e-6
+    for i in range(len(h)):
+        e = np.zeros_like(h)
+        e[i] = eps
+        fp = O.lml_exact(O.dense_K(x, h + e, dim, n1, n2), y)
+        fm = O.lml_exact(O.dense_K(x, h - e, dim, n1, n2), y)
+        fd = (fp - fm) / (2 * eps)
+        assert fd == pytest.approx(grad[i], rel=2e-5, abs=1e-4 * (1 + abs(lml)) * 1e-3), i
+
+
+def test_exact_gradient_homogeneity_identities():
+    # K = A k~ o (F F^T) + s2 I is homogeneous of degree 1 in (A, s2) and F is
+    # linear in the amplitudes, so (Euler):
+    #   A dL/dA + s2 dL/ds2 = 1/2 y^T K^-1 y - N/2
+    #   sum_b a_b dL/da_b  = 2 A dL/dA
+    x, y, h, dim, n1, n2 = small_problem(n=160)
+    p = O.unpack_h(h, dim, n1, n2)
+    lml, g = O.lml_grad_exact(x, y, h, dim, n1, n2)
+    K = O.dense_K(x, h, dim, n1, n2)
+    quad = float(y @ np.linalg.solve(K, y))
+    A, s2 = p["A"], p["sigma2"]
+    assert A * g[-2] + s2 * g[-1] == pytest.approx(0.5 * quad - 0.5 * len(y), rel=1e-10)
+    amp_idx = [(m * n2 + b) * (dim + 2) + dim + 1 for m in range(n1) for b in range(n2)]
+    lhs = sum(h[i] * g[i] for i in amp_idx)
+    assert lhs == pytest.approx(2 * A * g[-2], rel=1e-9, abs=1e-9)
+
+
+# --------------------------------------------------------------------- estimators
+
+def test_splitmix64_published_stream():
+    # SplitMix64 with state 0: the first three outputs of the reference stream
+    assert [int(O.splitmix64(0, k)) for k in range(3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_rademacher_balanced():
+    Z = O.rademacher(42, 8, np.arange(20000))
+    assert set(np.unique(Z)) == {-1.0, 1.0}
+    assert abs(Z.mean()) < 0.02
+    assert np.abs(np.corrcoef(Z.T) - np.eye(8)).max() < 0.05
+
+
+def test_lanczos_quadrature_exact_when_krylov_space_is_full():
+    rng = np.random.default_rng(4)
+    B = rng.normal(size=(40, 40))
+    M = B @ B.T / 40 + 0.5 * np.eye(40)
+    z = np.sign(rng.normal(size=40))
+    lam, V = np.linalg.eigh(M)
+    exact = float(np.sum((V.T @ z) ** 2 * np.log(lam)))
+    assert O.lanczos_quadrature(M, z, 40) == pytest.approx(exact, rel=1e-10)
+    # only 3 distinct eigenvalues: Lanczos stops after 3 steps and is exact
+    Q, _ = np.linalg.qr(rng.normal(size=(40, 40)))
+    lam3 = np.repeat([0.5, 1.0, 4.0], [10, 15, 15])
+    M3 = (Q * lam3) @ Q.T
+    exact3 = float(np.sum((Q.T @ z) ** 2 * np.log(lam3)))
+    assert O.lanczos_quadrature(M3, z, 30) == pytest.approx(exact3, rel=1e-9)
+
+
+def test_same_probe_estimator_identities_and_statistics():
+    x, y, h, dim, n1, n2 = small_problem(n=200, sigma2=5e-2)
+    p = O.unpack_h(h, dim, n1, n2)
+    lml, g, info = O.lml_grad_same_probes(x, y, h, dim, n1, n2, 16, 30, 99)
+    # exact for any probe set: the estimator is linear in dK and dK/dA*A + dK/ds2*s2 = K
+    assert p["A"] * g[-2] + p["sigma2"] * g[-1] == pytest.approx(0.5 * info["quad_form"] - 0.5 * len(y), rel=1e-9)
+    # statistical: SLQ and Hutchinson within 5 standard errors of the exact values
+    K = O.dense_K(x, h, dim, n1, n2)
+    lml_x, g_x = O.lml_grad_exact(x, y, h, dim, n1, n2)
+    nv = 400
+    lml_s, g_s, info_s = O.lml_grad_same_probes(x, y, h, dim, n1, n2, nv, 60, 5)
+    se = np.std(info_s["slq_terms"]) / math.sqrt(nv)
+    assert abs(info_s["logdet"] - 2 * np.sum(np.log(np.diag(np.linalg.cholesky(K))))) < 5 * se + 1e-8
+    assert np.median(np.abs(g_s - g_x) / (np.abs(g_x) + 1e-3)) < 0.2
