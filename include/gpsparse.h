@@ -1,0 +1,176 @@
+/*
+ * gpsparse.h -- C ABI of the GB300 sparse exact-GP library.
+ *
+ * The library evaluates the exact Gaussian process of arXiv 2205.09070
+ * (Noack, Krishnan, Risser, Reyes, "Exact Gaussian Processes for Massive
+ * Datasets via Non-Stationary Sparsity-Discovering Kernels") on one GPU:
+ *
+ *   K = A * k~(|x_i - x_j| ; r_s) * sum_m f_m(x_i) f_m(x_j) + sigma_n^2 I
+ *       (Sec. 2.2, Eq. eq:bump_kernel with the stationary kernel of
+ *        Eq. eq:kstat; f_m is the bump sum of Eq. eq:bump)
+ *   ln L = -1/2 y^T K^-1 y - 1/2 ln|K|          (Sec. 2.1, Eq. eqn:log_likelihood)
+ *
+ * K is assembled as a sparse CSR matrix (cell-list pair search, count, scan,
+ * fill); y^T K^-1 y comes from conjugate gradients and ln|K| from stochastic
+ * Lanczos quadrature on the same CG iterations (Sec. 2.5 solves K x = y by
+ * CG and estimates the log-determinant by randomized linear algebra).
+ *
+ * Conventions shared by every entry point
+ *  - Points x: N x dim doubles, row-major (x[i*dim + k]).  Targets y: N doubles.
+ *  - Array arguments may be HOST or DEVICE pointers; the library detects which
+ *    (cudaPointerGetAttributes) and copies host data itself.  The caller owns
+ *    every array it passes; the library never keeps a caller pointer beyond
+ *    the call.
+ *  - Hyperparameters h: host array of gp_n_params() doubles laid out as
+ *      for m < n_funcs, b < n_bumps: [centre (dim), radius r_mb, amplitude a_mb]
+ *      then r_s (stationary support radius), A (stationary amplitude),
+ *      sigma_n^2 (noise variance).
+ *    This is the hyperparameter set of Eq. eq:bump / eq:kstat; the bump shape
+ *    beta is a fixed constant of the context (Sec. 3 counts 42 parameters for
+ *    n_funcs = 2, n_bumps = 4, dim = 3: no beta among them).
+ *  - The prior mean is zero and the additive constant -N/2 ln(2 pi) is
+ *    dropped, as in Eq. eqn:log_likelihood.
+ *  - Every call is ordered on the context's CUDA stream.  Calls that return
+ *    host scalars synchronise that stream before returning.
+ *  - Return value: GP_OK (0) or one of the GP_ERR_* codes; no C++ exception
+ *    crosses this boundary and no kernel traps.  On an error, outputs are
+ *    unspecified unless stated otherwise.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef GPSPARSE_H
+#define GPSPARSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GP_OK                 0
+#define GP_ERR_INVALID_ARG    1  /* bad size, null pointer, non-finite or out-of-range h */
+#define GP_ERR_CUDA           2  /* a CUDA runtime call failed */
+#define GP_ERR_OOM            3  /* device allocation failed */
+#define GP_ERR_NOT_CONVERGED  4  /* CG hit max_iter before every column met cg_rtol; outputs are filled */
+#define GP_ERR_NOT_SPD        5  /* CG breakdown: p^T K p <= 0 or not finite (K not positive definite) */
+#define GP_ERR_TIMEOUT        6  /* a bounded device-side wait gave up */
+#define GP_ERR_NOT_ASSEMBLED  7  /* gp_solve / gp_get_csr before a successful gp_assemble */
+#define GP_ERR_UNSUPPORTED    8  /* a size above a compiled limit (dim > 3, n_funcs > 32, ...) */
+
+/* arithmetic of the path */
+#define GP_FP64        0  /* coordinates, kernel values, vectors and scalars in FP64; single-RHS CG */
+#define GP_FP32_MIXED  1  /* FP32 kernel values, CSR and CG vectors (batched [y, probes]);
+                             FP64 dot products, CG scalars, Lanczos eigensolve and log-det sums;
+                             FP64 re-check of every support test inside a guard band */
+
+typedef struct gp_ctx gp_ctx; /* opaque: owns the CSR matrix and all device workspaces */
+
+/* Kernel family (Eq. eq:bump_kernel): dim in 1..3, n_funcs (n1) in 1..32,
+ * n_bumps (n2) >= 1 with n_funcs*n_bumps <= 512, beta > 0 (shape of every bump). */
+typedef struct {
+  int32_t dim;
+  int32_t n_funcs;
+  int32_t n_bumps;
+  double beta;
+} gp_kernel_desc;
+
+typedef struct {
+  int32_t precision;      /* GP_FP64 or GP_FP32_MIXED */
+  int32_t n_probes;       /* Rademacher probes for SLQ / Hutchinson, 1..64 */
+  int32_t lanczos_steps;  /* Lanczos (CG) steps used by SLQ, 1..64 */
+  int32_t max_iter;       /* CG iteration cap */
+  double cg_rtol;         /* stop a column when |r| <= cg_rtol |r0| (Jacobi-scaled system) */
+  uint64_t seed;          /* probe stream: SplitMix64 counter l*2^40 + original point index */
+  int32_t check_every;    /* iterations between host convergence checks (0: default 16) */
+  int32_t flags;          /* GP_FLAG_* bits */
+} gp_opts;
+
+/* gp_opts.flags: time every launch of the SpMM, pair-fill and adjoint kernels
+ * with CUDA events on the context stream (reported in gp_info.t_*_kernel_ms). */
+#define GP_FLAG_TIME_KERNELS 1
+
+typedef struct {
+  int64_t n;              /* points */
+  int64_t n_active;       /* points inside the support of some bump (rows that couple) */
+  int64_t nnz;            /* stored entries of the active block (diagonal included) */
+  int32_t iters;          /* CG iterations run (max over columns / solves) */
+  int32_t status_detail;  /* column that failed, or -1 */
+  double max_rel_resid;   /* largest recursive relative residual at exit */
+  double quad_form;       /* y^T K^-1 y */
+  double logdet;          /* estimated ln|K| */
+  double logdet_stderr;   /* standard error of the SLQ mean over probes (x N_active) */
+  double t_assemble_ms;
+  double t_solve_ms;
+  double t_grad_ms;
+  double cell_size;       /* edge of the uniform search grid */
+  int64_t n_cells;        /* cells in the search grid */
+  int64_t launches;       /* kernels this call launched (no-op CG launches after convergence included) */
+  int32_t n_spmm;         /* SpMM launches that did work (GP_FLAG_TIME_KERNELS) */
+  int32_t kp;             /* padded RHS columns of the batched CG */
+  double t_spmm_kernel_ms;    /* summed device time of those SpMM launches */
+  double t_fill_kernel_ms;    /* device time of the pair-fill kernel */
+  double t_adjoint_kernel_ms; /* device time of the adjoint pair kernel */
+} gp_info;
+
+/* Number of hyperparameters: n_funcs*n_bumps*(dim+2) + 3. */
+int64_t gp_n_params(const gp_kernel_desc* desc);
+
+/* Default options: FP32_MIXED, 32 probes, 50 Lanczos steps, 10000 iterations,
+ * rtol 1e-6, seed 0x5eed, check every 16 iterations. */
+void gp_default_opts(gp_opts* opts);
+
+/* Create a context on CUDA device `device`, ordered on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The context allocates
+ * device memory lazily and keeps it (grow-only) until gp_destroy. */
+int gp_create(gp_ctx** out, const gp_kernel_desc* desc, int device, void* cuda_stream);
+int gp_destroy(gp_ctx* ctx);
+/* Change the stream later calls are ordered on. */
+int gp_set_stream(gp_ctx* ctx, void* cuda_stream);
+
+/* Assemble K for points x (N x dim) and hyperparameters h (Sec. 2.2,
+ * Eq. eq:bump_kernel): bump table, active-point compaction, Morton-sorted
+ * cell list with edge >= r_s, per-row pair count, prefix scan, fill.
+ * Uses opts->precision only.  Synchronises the stream once (to size the CSR).
+ * N may be 0.  The matrix stays in the context until the next assemble. */
+int gp_assemble(gp_ctx* ctx, const double* x, int64_t n, const double* h,
+                const gp_opts* opts, gp_info* info);
+
+/* Copy the assembled active block out (diagnostics and tests).
+ * Internal row order is the Morton order of the active points; perm[r] is the
+ * original index of internal row r; columns are internal indices, ascending
+ * within a row; values are unscaled K entries (doubles) whatever the precision.
+ * Pass NULL arrays to query the sizes only: sizes[0] = n_active, sizes[1] = nnz.
+ * Arrays: row_ptr n_active+1, col nnz, val nnz, perm n_active (host or device). */
+int gp_get_csr(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
+               int32_t* perm, int64_t sizes[2]);
+
+/* Solve K alpha = y with the last assembled K (Sec. 2.5: CG).  Rows outside
+ * every bump decouple: alpha_i = y_i / sigma_n^2 there.  alpha: N doubles. */
+int gp_solve(gp_ctx* ctx, const double* y, double* alpha, const gp_opts* opts, gp_info* info);
+
+/* Assemble K and evaluate ln L (Eq. eqn:log_likelihood) with
+ * ln|K| = sum ln D + SLQ(D^-1/2 K D^-1/2) + N_inactive ln sigma_n^2, D = diag K. */
+int gp_lml(gp_ctx* ctx, const double* x, const double* y, int64_t n, const double* h,
+           const gp_opts* opts, double* lml, gp_info* info);
+
+/* As gp_lml, plus d ln L / d h (host array of gp_n_params doubles):
+ * 1/2 alpha^T K_h alpha - 1/2 tr(K^-1 K_h), the trace by Hutchinson's
+ * estimator on the same probes, K_h recomputed on the CSR pattern and never
+ * stored (the paper lists gradient-based training as future work, Sec. 4). */
+int gp_lml_grad(gp_ctx* ctx, const double* x, const double* y, int64_t n, const double* h,
+                const gp_opts* opts, double* lml, double* grad, gp_info* info);
+
+/* Many independent GPs that share the kernel family.  Instance k owns points
+ * offsets[k] .. offsets[k+1]-1 of x / y (offsets: host, n_inst+1 entries) and
+ * hyperparameters h[k*P .. (k+1)*P).  lml: n_inst doubles, grad: n_inst*P
+ * doubles (host or device); grad may be NULL.  info (may be NULL) gets totals. */
+int gp_lml_grad_batched(gp_ctx* ctx, int32_t n_inst, const int64_t* offsets,
+                        const double* x, const double* y, const double* h,
+                        const gp_opts* opts, double* lml, double* grad, gp_info* info);
+
+const char* gp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPSPARSE_H */

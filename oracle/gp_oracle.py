@@ -193,8 +193,9 @@ def bump_table(x, h, dim, n1, n2, beta=1.0):
 # Eq. (eq:bump_kernel) with Eq. (eq:kstat): the covariance matrix K
 # ----------------------------------------------------------------------------
 
-def pair_rows(x, h, dim, n1, n2, rows, beta=1.0):
+def pair_rows(x, h, dim, n1, n2, rows, beta=1.0, table=None):
     """Brute force over all N columns for the given rows (original order).
+    `table` may pass a precomputed (F, mask) = bump_table(x, h, ...).
 
     Returns (pattern, values) of shape (len(rows), N):
       pattern[a, j] = (j == rows[a]) or (d^2 < r_s^2 and M_i & M_j != 0)
@@ -203,7 +204,7 @@ def pair_rows(x, h, dim, n1, n2, rows, beta=1.0):
     p = unpack_h(h, dim, n1, n2)
     x = np.asarray(x, dtype=np.float64)
     rows = np.asarray(rows, dtype=np.int64)
-    F, mask = bump_table(x, h, dim, n1, n2, beta)
+    F, mask = table if table is not None else bump_table(x, h, dim, n1, n2, beta)
     d2 = np.sum((x[rows, None, :] - x[None, :, :]) ** 2, axis=2)
     diag = rows[:, None] == np.arange(x.shape[0])[None, :]
     pattern = diag | ((d2 < p["r_s"] ** 2) & ((mask[rows, None] & mask[None, :]) != 0))
@@ -224,9 +225,10 @@ def assemble_csr(x, h, dim, n1, n2, beta=1.0, chunk=512):
     n = x.shape[0]
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     cols, vals = [], []
+    table = bump_table(x, h, dim, n1, n2, beta)
     for start in range(0, n, chunk):
         rows = np.arange(start, min(n, start + chunk))
-        pat, v = pair_rows(x, h, dim, n1, n2, rows, beta)
+        pat, v = pair_rows(x, h, dim, n1, n2, rows, beta, table)
         r_idx, c_idx = np.nonzero(pat)
         cols.append(c_idx.astype(np.int64))
         vals.append(v[r_idx, c_idx])

@@ -1,0 +1,513 @@
+// C ABI of libgpsparse (see include/gpsparse.h): argument checks, host/device
+// staging, buffer management and the order of the pipeline stages.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "gp_internal.cuh"
+
+namespace gp {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return GP_ERR_OOM;
+  }
+  return GP_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure(gp_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return GP_OK;
+  if (b.p) {
+    GP_CUDA(cudaStreamSynchronize(c->stream));
+    GP_CUDA(cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  size_t want = bytes + bytes / 8 + 256;
+  GP_CUDA(cudaMalloc(&b.p, want));
+  b.cap = want;
+  return GP_OK;
+}
+
+int ensure_pinned(gp_ctx* c, size_t bytes) {
+  if (c->pinned_cap >= bytes) return GP_OK;
+  if (c->pinned) {
+    GP_CUDA(cudaStreamSynchronize(c->stream));
+    GP_CUDA(cudaFreeHost(c->pinned));
+    c->pinned = nullptr;
+    c->pinned_cap = 0;
+  }
+  size_t want = bytes < 4096 ? 4096 : bytes;
+  GP_CUDA(cudaMallocHost(&c->pinned, want));
+  c->pinned_cap = want;
+  return GP_OK;
+}
+
+int kernel_events(gp_ctx* c) {
+  if (c->kev_ready) return GP_OK;
+  for (int i = 0; i < (int)(sizeof(c->kev) / sizeof(c->kev[0])); ++i) GP_CUDA(cudaEventCreate(&c->kev[i]));
+  c->kev_ready = true;
+  return GP_OK;
+}
+
+double event_ms(cudaEvent_t a, cudaEvent_t b) {
+  float t = 0.f;
+  if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return t;
+}
+
+}  // namespace gp
+
+namespace {
+
+void reset_counters(gp_ctx* c, int flags) {
+  c->flags = flags;
+  c->launches = 0;
+  c->t_spmm = c->t_fill = c->t_adj = 0.0;
+  c->n_spmm = 0;
+  c->bad_col = -1;
+}
+
+void fill_counters(const gp_ctx* c, gp_info* info) {
+  info->launches = c->launches;
+  info->status_detail = c->bad_col;
+  info->n_spmm = c->n_spmm;
+  info->t_spmm_kernel_ms = c->t_spmm;
+  info->t_fill_kernel_ms = c->t_fill;
+  info->t_adjoint_kernel_ms = c->t_adj;
+}
+
+int check_desc(const gp_kernel_desc* d) {
+  if (!d) return GP_ERR_INVALID_ARG;
+  if (d->dim < 1 || d->n_funcs < 1 || d->n_bumps < 1 || !(d->beta > 0.0) || !isfinite(d->beta))
+    return GP_ERR_INVALID_ARG;
+  if (d->dim > gp::kMaxDim || d->n_funcs > gp::kMaxFuncs || (int64_t)d->n_funcs * d->n_bumps > gp::kMaxBumps)
+    return GP_ERR_UNSUPPORTED;
+  return GP_OK;
+}
+
+int check_h(const gp_ctx* c, const double* h) {
+  if (!h) return GP_ERR_INVALID_ARG;
+  const int np = c->dim + 2;
+  for (int b = 0; b < c->nb; ++b) {
+    for (int t = 0; t < np; ++t)
+      if (!isfinite(h[b * np + t])) return GP_ERR_INVALID_ARG;
+    if (!(h[b * np + c->dim] > 0.0)) return GP_ERR_INVALID_ARG;  // radius
+  }
+  const double rs = h[c->nb * np], A = h[c->nb * np + 1], s2 = h[c->nb * np + 2];
+  if (!isfinite(rs) || !isfinite(A) || !isfinite(s2)) return GP_ERR_INVALID_ARG;
+  if (!(rs > 0.0) || !(A >= 0.0) || !(s2 > 0.0)) return GP_ERR_INVALID_ARG;
+  return GP_OK;
+}
+
+int check_opts(const gp_opts* o, bool need_probes) {
+  if (!o) return GP_ERR_INVALID_ARG;
+  if (o->precision != GP_FP64 && o->precision != GP_FP32_MIXED) return GP_ERR_INVALID_ARG;
+  if (o->max_iter < 1 || !(o->cg_rtol > 0.0) || !isfinite(o->cg_rtol)) return GP_ERR_INVALID_ARG;
+  if (need_probes) {
+    if (o->n_probes < 1 || o->n_probes > gp::kMaxProbes) return GP_ERR_INVALID_ARG;
+    if (o->lanczos_steps < 1 || o->lanczos_steps > gp::kMaxLanczos) return GP_ERR_INVALID_ARG;
+  }
+  return GP_OK;
+}
+
+// Make a device-resident copy of a caller array if it lives on the host.
+int stage_in(gp_ctx* c, gp::DevBuf& buf, const double* src, size_t count, const double** out) {
+  if (count == 0) {
+    *out = src;
+    return GP_OK;
+  }
+  if (gp::is_device_ptr(src)) {
+    *out = src;
+    return GP_OK;
+  }
+  GP_CHECK(gp::ensure(c, buf, count * sizeof(double)));
+  GP_CUDA(cudaMemcpyAsync(buf.p, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  *out = (const double*)buf.p;
+  return GP_OK;
+}
+
+int copy_out(gp_ctx* c, void* dst, const void* src_dev, size_t bytes) {
+  if (bytes == 0) return GP_OK;
+  GP_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, gp::is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                                       : cudaMemcpyDeviceToHost,
+                          c->stream));
+  return GP_OK;
+}
+
+struct Timer {
+  gp_ctx* c;
+  explicit Timer(gp_ctx* cc) : c(cc) {}
+  void mark(int i) { cudaEventRecord(c->ev[i], c->stream); }
+  double ms(int a, int b) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->ev[a], c->ev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      return 0.0;
+    }
+    return t;
+  }
+};
+
+int read_scalars(gp_ctx* c, gp::AsmScalars* hs) {
+  GP_CHECK(gp::ensure_pinned(c, sizeof(gp::AsmScalars)));
+  GP_CUDA(cudaMemcpyAsync(c->pinned, c->asm_s.p, sizeof(gp::AsmScalars), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(hs, c->pinned, sizeof(gp::AsmScalars));
+  return GP_OK;
+}
+
+// Assemble, solve [y, probes], SLQ, optional adjoint.
+int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const double* h, const gp_opts* o,
+             double* lml, double* grad, gp_info* info) {
+  if (!c || !lml || n < 0 || (n > 0 && (!x || !y))) return GP_ERR_INVALID_ARG;
+  GP_CHECK(check_h(c, h));
+  GP_CHECK(check_opts(o, true));
+  GP_CUDA(cudaSetDevice(c->device));
+  reset_counters(c, o->flags);
+  Timer tm(c);
+  tm.mark(0);
+  const double *xd = nullptr, *yd = nullptr;
+  GP_CHECK(stage_in(c, c->x_in, x, (size_t)n * c->dim, &xd));
+  GP_CHECK(stage_in(c, c->y_in, y, (size_t)n, &yd));
+  GP_CHECK(gp::assemble(c, xd, n, h, o->precision));
+  tm.mark(1);
+  GP_CHECK(gp::inactive_terms(c, yd));
+  const int nv = o->n_probes;
+  const int k = 1 + nv;
+  const int kp = (k + 3) / 4 * 4;
+  int iters = 0;
+  double max_rel = 0.0;
+  int cg_status;
+  if (o->precision == GP_FP64)
+    cg_status = gp::cg_run_fp64(c, k, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
+                                &iters, &max_rel);
+  else
+    cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
+                           &iters, &max_rel);
+  if (cg_status != GP_OK && cg_status != GP_ERR_NOT_CONVERGED) return cg_status;
+  GP_CHECK(gp::quad_form(c, yd, kp));
+  GP_CHECK(gp::slq(c, nv, kp));
+  tm.mark(2);
+  if (grad) GP_CHECK(gp::adjoint(c, nv, kp));
+  tm.mark(3);
+  gp::AsmScalars hs;
+  GP_CHECK(read_scalars(c, &hs));
+  if (c->n_act > 0 && hs.status != GP_OK) return hs.status;
+  const double s2 = c->sigma2;
+  const double n_in = (double)(n - c->n_act);
+  const double logdet = hs.sum_log_d * (c->n_act > 0) + hs.slq_mean + n_in * log(s2);
+  const double quad = hs.quad_form + hs.inact_y2 / s2;
+  *lml = -0.5 * quad - 0.5 * logdet;
+  if (grad) {
+    const int np = c->dim + 2;
+    const size_t nbp = (size_t)c->nb * np;
+    std::vector<double> gb(nbp, 0.0);
+    if (c->n_act > 0) {
+      GP_CHECK(gp::ensure_pinned(c, nbp * sizeof(double)));
+      GP_CUDA(cudaMemcpyAsync(c->pinned, c->grad_bump.p, nbp * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      GP_CUDA(cudaStreamSynchronize(c->stream));
+      memcpy(gb.data(), c->pinned, nbp * sizeof(double));
+    }
+    std::vector<double> out(nbp + 3);
+    for (size_t q = 0; q < nbp; ++q) out[q] = gb[q];
+    const bool act = c->n_act > 0;
+    out[nbp] = act ? hs.grad_rs : 0.0;
+    out[nbp + 1] = act ? hs.grad_A : 0.0;
+    out[nbp + 2] = (act ? hs.grad_s2 : 0.0) + 0.5 * hs.inact_y2 / (s2 * s2) - 0.5 * n_in / s2;
+    if (gp::is_device_ptr(grad)) {
+      GP_CHECK(gp::ensure_pinned(c, out.size() * sizeof(double)));
+      memcpy(c->pinned, out.data(), out.size() * sizeof(double));
+      GP_CUDA(cudaMemcpyAsync(grad, c->pinned, out.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      GP_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+      memcpy(grad, out.data(), out.size() * sizeof(double));
+    }
+  }
+  if (info) {
+    info->n = n;
+    info->n_active = c->n_act;
+    info->nnz = c->nnz;
+    info->iters = iters;
+    info->status_detail = -1;
+    info->max_rel_resid = max_rel;
+    info->quad_form = quad;
+    info->logdet = logdet;
+    info->logdet_stderr = nv > 1 ? sqrt(hs.slq_var / nv) : 0.0;
+    info->t_assemble_ms = tm.ms(0, 1);
+    info->t_solve_ms = tm.ms(1, 2);
+    info->t_grad_ms = grad ? tm.ms(2, 3) : 0.0;
+    info->cell_size = c->grid.h;
+    info->n_cells = c->grid.ncells;
+    info->kp = o->precision == GP_FP64 ? k : kp;
+    fill_counters(c, info);
+  }
+  return cg_status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gp_n_params(const gp_kernel_desc* d) {
+  if (!d) return -1;
+  return (int64_t)d->n_funcs * d->n_bumps * (d->dim + 2) + 3;
+}
+
+void gp_default_opts(gp_opts* o) {
+  if (!o) return;
+  o->precision = GP_FP32_MIXED;
+  o->n_probes = 32;
+  o->lanczos_steps = 50;
+  o->max_iter = 10000;
+  o->cg_rtol = 1e-6;
+  o->seed = 0x5eedull;
+  o->check_every = 16;
+  o->flags = 0;
+}
+
+int gp_create(gp_ctx** out, const gp_kernel_desc* desc, int device, void* stream) {
+  if (!out) return GP_ERR_INVALID_ARG;
+  *out = nullptr;
+  GP_CHECK(check_desc(desc));
+  GP_CUDA(cudaSetDevice(device));
+  gp_ctx* c = new (std::nothrow) gp_ctx();
+  if (!c) return GP_ERR_OOM;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  c->dim = desc->dim;
+  c->n1 = desc->n_funcs;
+  c->n2 = desc->n_bumps;
+  c->nb = desc->n_funcs * desc->n_bumps;
+  c->beta = desc->beta;
+  int st = GP_OK;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) st = GP_ERR_CUDA;
+  if (st == GP_OK) c->num_sms = prop.multiProcessorCount;
+  if (st == GP_OK) st = gp::ensure(c, c->cg, sizeof(gp::CgState));
+  if (st == GP_OK) st = gp::ensure(c, c->asm_s, sizeof(gp::AsmScalars));
+  if (st == GP_OK && cudaMemsetAsync(c->cg.p, 0, sizeof(gp::CgState), c->stream) != cudaSuccess) st = GP_ERR_CUDA;
+  if (st == GP_OK && cudaMemsetAsync(c->asm_s.p, 0, sizeof(gp::AsmScalars), c->stream) != cudaSuccess)
+    st = GP_ERR_CUDA;
+  for (int i = 0; i < 8 && st == GP_OK; ++i)
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) st = GP_ERR_CUDA;
+  if (st == GP_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = GP_ERR_CUDA;
+  if (st != GP_OK) {
+    gp_destroy(c);
+    return st;
+  }
+  *out = c;
+  return GP_OK;
+}
+
+int gp_destroy(gp_ctx* c) {
+  if (!c) return GP_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  gp::DevBuf* bufs[] = {&c->x_in,   &c->y_in,   &c->out_tmp,    &c->bump,      &c->mask0,     &c->F0,
+                        &c->pos,    &c->keys,   &c->vals,       &c->keys2,     &c->vals2,     &c->hist,
+                        &c->hist_scan, &c->scan_part, &c->cells, &c->perm,     &c->skey,      &c->cellc,
+                        &c->xr,     &c->xs,     &c->Fs,         &c->smask,     &c->dinv,      &c->dinv64,
+                        &c->cnt,    &c->row_ptr, &c->col,       &c->val,       &c->X,         &c->R,
+                        &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
+                        &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
+                        &c->asm_s,  &c->csr_tmp};
+  for (gp::DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  for (int i = 0; i < 8; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->kev_ready)
+    for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
+  delete c;
+  return GP_OK;
+}
+
+int gp_set_stream(gp_ctx* c, void* stream) {
+  if (!c) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  c->stream = (cudaStream_t)stream;
+  return GP_OK;
+}
+
+int gp_assemble(gp_ctx* c, const double* x, int64_t n, const double* h, const gp_opts* o, gp_info* info) {
+  if (!c || n < 0 || (n > 0 && !x) || !o) return GP_ERR_INVALID_ARG;
+  if (o->precision != GP_FP64 && o->precision != GP_FP32_MIXED) return GP_ERR_INVALID_ARG;
+  GP_CHECK(check_h(c, h));
+  GP_CUDA(cudaSetDevice(c->device));
+  reset_counters(c, o->flags);
+  Timer tm(c);
+  tm.mark(0);
+  const double* xd = nullptr;
+  GP_CHECK(stage_in(c, c->x_in, x, (size_t)n * c->dim, &xd));
+  GP_CHECK(gp::assemble(c, xd, n, h, o->precision));
+  tm.mark(1);
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->n = n;
+    info->n_active = c->n_act;
+    info->nnz = c->nnz;
+    info->status_detail = -1;
+    info->t_assemble_ms = tm.ms(0, 1);
+    info->cell_size = c->grid.h;
+    info->n_cells = c->grid.ncells;
+    fill_counters(c, info);
+  }
+  return GP_OK;
+}
+
+int gp_get_csr(gp_ctx* c, int64_t* row_ptr, int32_t* col, double* val, int32_t* perm, int64_t sizes[2]) {
+  if (!c || !sizes) return GP_ERR_INVALID_ARG;
+  if (!c->assembled) return GP_ERR_NOT_ASSEMBLED;
+  GP_CUDA(cudaSetDevice(c->device));
+  sizes[0] = c->n_act;
+  sizes[1] = c->nnz;
+  if (c->n_act == 0) {
+    if (row_ptr) {
+      int64_t z = 0;
+      if (gp::is_device_ptr(row_ptr)) GP_CUDA(cudaMemcpy(row_ptr, &z, sizeof(z), cudaMemcpyHostToDevice));
+      else *row_ptr = 0;
+    }
+    return GP_OK;
+  }
+  if (row_ptr) GP_CHECK(copy_out(c, row_ptr, c->row_ptr.p, (size_t)(c->n_act + 1) * sizeof(int64_t)));
+  if (col) GP_CHECK(copy_out(c, col, c->col.p, (size_t)c->nnz * sizeof(int32_t)));
+  if (perm) GP_CHECK(copy_out(c, perm, c->vals.p, (size_t)c->n_act * sizeof(int32_t)));
+  if (val) {
+    GP_CHECK(gp::ensure(c, c->csr_tmp, (size_t)c->nnz * sizeof(double)));
+    GP_CHECK(gp::csr_unscaled(c, (double*)c->csr_tmp.p));
+    GP_CHECK(copy_out(c, val, c->csr_tmp.p, (size_t)c->nnz * sizeof(double)));
+  }
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  return GP_OK;
+}
+
+int gp_solve(gp_ctx* c, const double* y, double* alpha, const gp_opts* o, gp_info* info) {
+  if (!c || !alpha || !o) return GP_ERR_INVALID_ARG;
+  if (!c->assembled) return GP_ERR_NOT_ASSEMBLED;
+  GP_CHECK(check_opts(o, false));
+  if (c->n > 0 && !y) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  reset_counters(c, o->flags);
+  Timer tm(c);
+  tm.mark(0);
+  const double* yd = nullptr;
+  GP_CHECK(stage_in(c, c->y_in, y, (size_t)c->n, &yd));
+  int iters = 0;
+  double max_rel = 0.0;
+  int st;
+  if (c->precision == GP_FP64)
+    st = gp::cg_run_fp64(c, 1, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel);
+  else
+    st = gp::cg_run(c, 1, 4, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel);
+  if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
+  double* out = alpha;
+  const bool dev = gp::is_device_ptr(alpha);
+  if (!dev) {
+    GP_CHECK(gp::ensure(c, c->out_tmp, (size_t)c->n * sizeof(double)));
+    out = (double*)c->out_tmp.p;
+  }
+  if (c->n > 0) GP_CHECK(gp::alpha_out(c, yd, out, 4));
+  if (!dev && c->n > 0)
+    GP_CUDA(cudaMemcpyAsync(alpha, out, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  tm.mark(1);
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->n = c->n;
+    info->n_active = c->n_act;
+    info->nnz = c->nnz;
+    info->iters = iters;
+    info->status_detail = -1;
+    info->max_rel_resid = max_rel;
+    info->t_solve_ms = tm.ms(0, 1);
+    info->cell_size = c->grid.h;
+    info->n_cells = c->grid.ncells;
+    info->kp = 4;
+    fill_counters(c, info);
+  }
+  return st;
+}
+
+int gp_lml(gp_ctx* c, const double* x, const double* y, int64_t n, const double* h, const gp_opts* o, double* lml,
+           gp_info* info) {
+  return evaluate(c, x, y, n, h, o, lml, nullptr, info);
+}
+
+int gp_lml_grad(gp_ctx* c, const double* x, const double* y, int64_t n, const double* h, const gp_opts* o,
+                double* lml, double* grad, gp_info* info) {
+  if (!grad) return GP_ERR_INVALID_ARG;
+  return evaluate(c, x, y, n, h, o, lml, grad, info);
+}
+
+int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const double* x, const double* y,
+                        const double* h, const gp_opts* o, double* lml, double* grad, gp_info* info) {
+  if (!c || n_inst < 0 || (n_inst > 0 && (!offsets || !h || !lml))) return GP_ERR_INVALID_ARG;
+  if (info) memset(info, 0, sizeof(*info));
+  const int64_t P = (int64_t)c->nb * (c->dim + 2) + 3;
+  const bool lml_dev = gp::is_device_ptr(lml), grad_dev = grad && gp::is_device_ptr(grad);
+  std::vector<double> g(P);
+  int status = GP_OK;
+  for (int32_t q = 0; q < n_inst; ++q) {
+    const int64_t a = offsets[q], b = offsets[q + 1];
+    if (b < a) return GP_ERR_INVALID_ARG;
+    double l = 0.0;
+    gp_info inf;
+    int st = evaluate(c, x ? x + a * c->dim : nullptr, y ? y + a : nullptr, b - a, h + q * P, o, &l,
+                      grad ? g.data() : nullptr, &inf);
+    if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
+    if (st != GP_OK) status = st;
+    if (lml_dev) GP_CUDA(cudaMemcpy(lml + q, &l, sizeof(double), cudaMemcpyHostToDevice));
+    else lml[q] = l;
+    if (grad) {
+      if (grad_dev) GP_CUDA(cudaMemcpy(grad + q * P, g.data(), P * sizeof(double), cudaMemcpyHostToDevice));
+      else memcpy(grad + q * P, g.data(), P * sizeof(double));
+    }
+    if (info) {
+      info->n += inf.n;
+      info->n_active += inf.n_active;
+      info->nnz += inf.nnz;
+      info->iters = inf.iters > info->iters ? inf.iters : info->iters;
+      info->t_assemble_ms += inf.t_assemble_ms;
+      info->t_solve_ms += inf.t_solve_ms;
+      info->t_grad_ms += inf.t_grad_ms;
+    }
+  }
+  return status;
+}
+
+const char* gp_status_string(int s) {
+  switch (s) {
+    case GP_OK: return "ok";
+    case GP_ERR_INVALID_ARG: return "invalid argument";
+    case GP_ERR_CUDA: return "CUDA runtime error";
+    case GP_ERR_OOM: return "device out of memory";
+    case GP_ERR_NOT_CONVERGED: return "CG did not converge within max_iter";
+    case GP_ERR_NOT_SPD: return "CG breakdown: matrix not positive definite";
+    case GP_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GP_ERR_NOT_ASSEMBLED: return "no assembled matrix";
+    case GP_ERR_UNSUPPORTED: return "size above a compiled limit";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

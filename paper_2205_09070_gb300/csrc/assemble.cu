@@ -1,0 +1,761 @@
+// Sparse assembly of K (Sec. 2.2, Eq. eq:bump_kernel with Eq. eq:bump and
+// Eq. eq:kstat) on one GPU:
+//   bbox -> bump table (F, support mask) -> active compaction -> Morton keys
+//   -> LSD radix sort -> cell table -> per-row pair count -> scan -> fill.
+// The stored matrix is the Jacobi-scaled active block
+//   Khat = D^-1/2 K_act D^-1/2,  D = diag(K_act) = A C sum_m F_m^2 + sigma_n^2,
+// in CSR with rows and columns in Morton order and ascending columns.
+#include <math.h>
+
+#include <algorithm>
+#include <climits>
+#include <utility>
+#include <vector>
+
+#include "gp_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kPrefactor = 0.26596152026762182;  // sqrt(2) / (3 sqrt(pi)), Eq. eq:kstat
+
+// ------------------------------------------------------------------ bbox
+__global__ void __launch_bounds__(kThreads) k_bbox(const double* __restrict__ x, int64_t n, int dim,
+                                                   double* __restrict__ part, gp::AsmScalars* s) {
+  double lo[gp::kMaxDim], hi[gp::kMaxDim];
+  for (int k = 0; k < gp::kMaxDim; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < dim; ++k) {
+      double v = x[i * dim + k];
+      lo[k] = fmin(lo[k], v);
+      hi[k] = fmax(hi[k], v);
+    }
+  }
+  __shared__ double sh[kThreads];
+  __shared__ bool last;
+  for (int k = 0; k < dim; ++k) {
+    for (int side = 0; side < 2; ++side) {
+      sh[threadIdx.x] = side ? hi[k] : lo[k];
+      __syncthreads();
+      for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+          double a = sh[threadIdx.x], b = sh[threadIdx.x + o];
+          sh[threadIdx.x] = side ? fmax(a, b) : fmin(a, b);
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) part[(blockIdx.x * gp::kMaxDim + k) * 2 + side] = sh[0];
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicInc(&s->ticket0, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    for (int k = 0; k < dim; ++k) {
+      double a = INFINITY, b = -INFINITY;
+      for (unsigned g = 0; g < gridDim.x; ++g) {
+        a = fmin(a, __ldcg(part + (g * gp::kMaxDim + k) * 2));
+        b = fmax(b, __ldcg(part + (g * gp::kMaxDim + k) * 2 + 1));
+      }
+      s->bbox_lo[k] = a;
+      s->bbox_hi[k] = b;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ bump table
+// F0[i, m] = f_m(x_i) (Eq. eq:bump, support |x - c| < r), mask0[i] bit m set
+// iff x_i lies inside some bump of f_m; flag[i] = (mask0[i] != 0).
+// An FP32 pre-filter (coordinates relative to the bounding box) rejects bumps
+// far from the point; every accepted bump is re-tested and evaluated in FP64
+// with the same operation order as the plain definition.
+__global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restrict__ x, int64_t n, int dim,
+                                                         const gp::BumpParam* __restrict__ bumps, int n1,
+                                                         int n2, double beta, double lo0, double lo1,
+                                                         double lo2, double* __restrict__ F0,
+                                                         uint32_t* __restrict__ mask0,
+                                                         int32_t* __restrict__ flag) {
+  extern __shared__ gp::BumpParam sb[];
+  const int nb = n1 * n2;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) sb[b] = bumps[b];
+  __syncthreads();
+  const double lo[3] = {lo0, lo1, lo2};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double xi[gp::kMaxDim] = {0, 0, 0};
+    float x32[gp::kMaxDim] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+      xi[k] = x[i * dim + k];
+      x32[k] = (float)(xi[k] - lo[k]);
+    }
+    uint32_t mask = 0;
+    for (int m = 0; m < n1; ++m) {
+      double f = 0.0;
+      bool in_m = false;
+      for (int j = 0; j < n2; ++j) {
+        const gp::BumpParam& bp = sb[m * n2 + j];
+        float q32 = 0.0f;
+        for (int k = 0; k < dim; ++k) {
+          float t = x32[k] - bp.c32[k];
+          q32 = fmaf(t, t, q32);
+        }
+        q32 *= bp.inv_r2_32;
+        if (q32 < 1.0f + bp.margin) {
+          double d2 = 0.0;
+          for (int k = 0; k < dim; ++k) {
+            double t = __dsub_rn(xi[k], bp.c[k]);
+            d2 = __dadd_rn(d2, __dmul_rn(t, t));
+          }
+          double q = __ddiv_rn(d2, bp.r2);
+          if (q < 1.0) {
+            double u = 1.0 - q;
+            f += bp.a * exp(beta - beta / u);
+            in_m = true;
+          }
+        }
+      }
+      F0[i * n1 + m] = f;
+      if (in_m) mask |= 1u << m;
+    }
+    mask0[i] = mask;
+    flag[i] = mask != 0u;
+  }
+}
+
+// ------------------------------------------------------------------ cells
+__device__ inline void cell_of(const double* xi, const gp::Grid& g, int* c) {
+  for (int k = 0; k < gp::kMaxDim; ++k) c[k] = 0;
+  for (int k = 0; k < g.dim; ++k) {
+    double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h);
+    long long ci = (long long)floor(u);
+    ci = ci < 0 ? 0 : ci;
+    ci = ci > g.G[k] - 1 ? g.G[k] - 1 : ci;
+    c[k] = (int)ci;
+  }
+}
+
+__device__ inline uint32_t morton(const int* c, const gp::Grid& g) {
+  uint32_t key = 0;
+  int pos = 0;
+  for (int t = 0; t < 32 && pos < g.keybits; ++t)
+    for (int k = 0; k < g.dim; ++k)
+      if (t < g.bits[k]) key |= (uint32_t)((c[k] >> t) & 1) << pos++;
+  return key;
+}
+
+__global__ void __launch_bounds__(kThreads) k_keys(const double* __restrict__ x, int64_t n,
+                                                   const int64_t* __restrict__ pos,
+                                                   const uint32_t* __restrict__ mask0, gp::Grid g,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (mask0[i] == 0u) continue;
+    double xi[gp::kMaxDim] = {0, 0, 0};
+    for (int k = 0; k < g.dim; ++k) xi[k] = x[i * g.dim + k];
+    int c[gp::kMaxDim];
+    cell_of(xi, g, c);
+    int64_t a = pos[i];
+    keys[a] = morton(c, g);
+    vals[a] = (uint32_t)i;
+  }
+}
+
+// ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits.  A tile of
+// kRsTile items is ranked in kRsRounds rounds of 256 items (item order within
+// the tile = round, then thread), each item's rank among equal digits in its
+// warp comes from __match_any_sync, and per-warp digit counts are prefixed in
+// shared memory, so equal keys keep their input order.
+constexpr int kRsRounds = 8;
+constexpr int kRsTile = kThreads * kRsRounds;
+
+__global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                      int ntiles, int32_t* __restrict__ hist) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  for (int r = 0; r < kRsRounds; ++r) {
+    int64_t idx = base + r * kThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin, int64_t n, int shift,
+                                                         int ntiles, const int64_t* __restrict__ offs,
+                                                         uint32_t* __restrict__ kout,
+                                                         uint32_t* __restrict__ vout) {
+  __shared__ long long run[256];
+  __shared__ long long wcnt[kWarps][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  for (int r = 0; r < kRsRounds; ++r) {
+    for (int t = threadIdx.x; t < kWarps * 256; t += kThreads) (&wcnt[0][0])[t] = 0;
+    __syncthreads();
+    const int64_t idx = base + r * kThreads + threadIdx.x;
+    const bool valid = idx < n;
+    uint32_t k = valid ? kin[idx] : 0u;
+    uint32_t v = valid ? vin[idx] : 0u;
+    unsigned d = valid ? ((k >> shift) & 255u) : 256u + lane;  // invalid items match nobody
+    unsigned peers = __match_any_sync(kFull, d);
+    unsigned below = peers & gpd::lanemask_lt();
+    int rank = __popc(below);
+    if (valid && below == 0u) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {
+      const int dig = threadIdx.x;  // 256 threads = 256 digits
+      long long acc = run[dig];
+      for (int ww = 0; ww < kWarps; ++ww) {
+        long long cnum = wcnt[ww][dig];
+        wcnt[ww][dig] = acc;
+        acc += cnum;
+      }
+      run[dig] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      long long p = wcnt[w][d] + rank;
+      kout[p] = k;
+      vout[p] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ sorted points
+// For sorted position p: original index, cell coordinates, FP32 coordinates
+// relative to the own cell (units of h), FP64 coordinates, F and mask in
+// Morton order, D^-1/2, cell table boundaries, and sum ln D.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ x, int64_t n_act,
+                                                     const uint32_t* __restrict__ skey,
+                                                     const uint32_t* __restrict__ perm, gp::Grid g,
+                                                     const double* __restrict__ F0,
+                                                     const uint32_t* __restrict__ mask0, int n1, double AC,
+                                                     double sigma2, int4* __restrict__ cellc,
+                                                     float4* __restrict__ xr, double* __restrict__ xs,
+                                                     T* __restrict__ Fs, uint32_t* __restrict__ smask,
+                                                     T* __restrict__ dinv, double* __restrict__ dinv64,
+                                                     int2* __restrict__ cells, double* __restrict__ part,
+                                                     gp::AsmScalars* s) {
+  double acc = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_act; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = perm[p];
+    double xi[gp::kMaxDim] = {0, 0, 0};
+    for (int k = 0; k < g.dim; ++k) xi[k] = x[(int64_t)i * g.dim + k];
+    int c[gp::kMaxDim];
+    cell_of(xi, g, c);
+    cellc[p] = make_int4(c[0], c[1], c[2], 0);
+    float r[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < g.dim; ++k) {
+      double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h);
+      r[k] = (float)(u - (double)c[k]);
+      xs[p * g.dim + k] = xi[k];
+    }
+    xr[p] = make_float4(r[0], r[1], r[2], 0.f);
+    double sF = 0.0;
+    for (int m = 0; m < n1; ++m) {
+      double f = F0[(int64_t)i * n1 + m];
+      Fs[p * n1 + m] = (T)f;
+      sF += f * f;
+    }
+    smask[p] = mask0[i];
+    const double D = AC * sF + sigma2;
+    const double di = 1.0 / sqrt(D);
+    dinv64[p] = di;
+    dinv[p] = (T)di;
+    acc += log(D);
+    const int64_t lin = (int64_t)c[0] + (int64_t)g.G[0] * ((int64_t)c[1] + (int64_t)g.G[1] * c[2]);
+    const uint32_t kk = skey[p];
+    if (p == 0 || skey[p - 1] != kk) cells[lin].x = (int)p;
+    if (p == n_act - 1 || skey[p + 1] != kk) cells[lin].y = (int)(p + 1);
+  }
+  __shared__ double sh[kThreads];
+  __shared__ bool last;
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sh[0];
+    __threadfence();
+    last = atomicInc(&s->ticket1, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
+    s->sum_log_d = t;
+  }
+}
+
+// ------------------------------------------------------------------ pair search
+struct PairArgs {
+  int64_t n;
+  int dim, nstencil, n1;
+  int G0, G1, G2;
+  const int2* cells;
+  const int4* cellc;
+  const uint32_t* mask;
+  const float4* xr;
+  const double* xs;
+  const void* Fs;
+  const void* dinv;
+  const int64_t* row_ptr;
+  int32_t* cnt;
+  int32_t* col;
+  void* val;
+  float scale;   // (h / r_s)^2
+  float guard;   // |rho^2 - 1| below this: decide in FP64
+  double rs2;    // r_s^2
+  double AC;     // A * C
+  double sigma2;
+};
+
+__device__ inline int warp_incl_scan_int(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+__device__ inline double dist2_fp64(const double* __restrict__ xs, int dim, int64_t p, int64_t j) {
+  double d2 = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    double t = __dsub_rn(xs[p * dim + k], xs[j * dim + k]);
+    d2 = __dadd_rn(d2, __dmul_rn(t, t));
+  }
+  return d2;
+}
+
+// One warp per active row p.  The 3^dim neighbour cells of p's cell are
+// ordered by their first sorted index, so visiting their point ranges in that
+// order yields ascending column indices; the ranges are flattened and 32
+// candidates are tested per step.  Predicate of row p, column j:
+//   mask_p & mask_j != 0  and  |x_p - x_j|^2 < r_s^2   (j == p always passes).
+// COUNT writes the number of hits per row; FILL writes columns and the
+// Jacobi-scaled values  D_p^-1/2 (A C k~ sum_m F_pm F_jm + sigma_n^2 [p==j]) D_j^-1/2.
+template <typename T, bool FILL>
+__global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
+  __shared__ int sh_start[kWarps][32];
+  __shared__ int sh_pre[kWarps][32];
+  __shared__ int sh_off[kWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const T* Fs = (const T*)a.Fs;
+  const T* dinv = (const T*)a.dinv;
+  T* val = (T*)a.val;
+  const int G[3] = {a.G0, a.G1, a.G2};
+  for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < a.n; p += (int64_t)gridDim.x * kWarps) {
+    const int4 ci4 = a.cellc[p];
+    const int ci[3] = {ci4.x, ci4.y, ci4.z};
+    const uint32_t mi = a.mask[p];
+    // 2-bit offset code per axis (offset + 1); axes beyond dim keep offset 0
+    int start = 0, len = 0, offpack = 0x15;
+    if (lane < a.nstencil) {
+      int t = lane;
+      bool ok = true;
+      int64_t lin = 0, mult = 1;
+      for (int k = 0; k < a.dim; ++k) {
+        int o = t % 3 - 1;
+        t /= 3;
+        int cc = ci[k] + o;
+        ok = ok && cc >= 0 && cc < G[k];
+        lin += (int64_t)cc * mult;
+        mult *= G[k];
+        offpack = (offpack & ~(3 << (2 * k))) | ((o + 1) << (2 * k));
+      }
+      if (ok) {
+        int2 se = a.cells[lin];
+        start = se.x;
+        len = se.y - se.x;
+      }
+    }
+    const int key = len > 0 ? start : INT_MAX;
+    int rank = 0;
+    for (int l2 = 0; l2 < a.nstencil; ++l2) {
+      int k2 = __shfl_sync(kFull, key, l2);
+      rank += (k2 < key) || (k2 == key && l2 < lane);
+    }
+    const unsigned nonempty = __ballot_sync(kFull, lane < a.nstencil && len > 0);
+    const int nseg = __popc(nonempty);
+    __syncwarp();
+    if (lane < a.nstencil && len > 0) {
+      sh_start[w][rank] = start;
+      sh_pre[w][rank] = len;
+      sh_off[w][rank] = offpack;
+    }
+    __syncwarp();
+    const int L = lane < nseg ? sh_pre[w][lane] : 0;
+    const int inc = warp_incl_scan_int(L);
+    __syncwarp();
+    if (lane < nseg) sh_pre[w][lane] = inc - L;
+    const int total = __shfl_sync(kFull, inc, 31);
+    __syncwarp();
+
+    const float4 xi = a.xr[p];
+    int64_t out = 0;
+    T di = 0;
+    if (FILL) {
+      out = a.row_ptr[p];
+      di = dinv[p];
+    }
+    int count = 0;
+    for (int base = 0; base < total; base += 32) {
+      const int f = base + lane;
+      bool hit = false;
+      int j = 0;
+      T v = 0;
+      if (f < total) {
+        int r = 0;
+        for (int step = 16; step > 0; step >>= 1)
+          if (r + step < nseg && sh_pre[w][r + step] <= f) r += step;
+        j = sh_start[w][r] + (f - sh_pre[w][r]);
+        const uint32_t mj = a.mask[j];
+        if ((mi & mj) != 0u) {
+          T rho2, s2;
+          if (sizeof(T) == 4) {
+            const float4 xj = a.xr[j];
+            const int op = sh_off[w][r];
+            const float dx = (xj.x + (float)((op & 3) - 1)) - xi.x;
+            const float dy = (xj.y + (float)(((op >> 2) & 3) - 1)) - xi.y;
+            const float dz = (xj.z + (float)(((op >> 4) & 3) - 1)) - xi.z;
+            float r2 = (dx * dx + dy * dy + dz * dz) * a.scale;
+            if (fabsf(r2 - 1.0f) < a.guard) {
+              const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+              hit = e2 < a.rs2;
+              rho2 = (T)(e2 / a.rs2);
+              s2 = (T)((a.rs2 - e2) / a.rs2);
+            } else {
+              hit = r2 < 1.0f;
+              rho2 = (T)r2;
+              s2 = (T)(1.0f - r2);
+              if (FILL && hit && s2 < (T)0.1) {
+                // near the support edge 1 - rho^2 cancels: take it from FP64
+                const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+                rho2 = (T)(e2 / a.rs2);
+                s2 = (T)((a.rs2 - e2) / a.rs2);
+              }
+            }
+          } else {
+            const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+            hit = e2 < a.rs2;
+            rho2 = (T)(e2 / a.rs2);
+            s2 = (T)((a.rs2 - e2) / a.rs2);
+          }
+          if (FILL && hit) {
+            T S = 0;
+            uint32_t common = mi & mj;
+            while (common) {
+              const int m = __ffs(common) - 1;
+              common &= common - 1u;
+              S += Fs[p * a.n1 + m] * Fs[(int64_t)j * a.n1 + m];
+            }
+            v = (T)a.AC * gpd::Real<T>::kstat(rho2, s2) * S;
+            if (j == p) v += (T)a.sigma2;
+            v = v * di * dinv[j];
+          }
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, hit);
+      if (FILL && hit) {
+        const int64_t q = out + count + __popc(bal & gpd::lanemask_lt());
+        a.col[q] = j;
+        val[q] = v;
+      }
+      count += __popc(bal);
+    }
+    if (!FILL && lane == 0) a.cnt[p] = count;
+  }
+}
+
+// Unscaled values of the stored block (for gp_get_csr): K = D^1/2 Khat D^1/2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_unscale(int64_t n, const int64_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                      const double* __restrict__ dinv64, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < n; p += (int64_t)gridDim.x * kWarps) {
+    const double dp = dinv64[p];
+    for (int64_t e = rp[p] + lane; e < rp[p + 1]; e += 32) out[e] = (double)val[e] / (dp * dinv64[col[e]]);
+  }
+}
+
+unsigned grid_for(int64_t items, int per_block, int max_blocks) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (unsigned)g;
+}
+
+template <typename T>
+int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
+  const int dim = c->dim, n1 = c->n1, n2 = c->n2, nb = c->nb;
+  const int maxb = c->num_sms * 16;
+  gp::AsmScalars* s = (gp::AsmScalars*)c->asm_s.p;
+
+  // --- bounding box (one small device->host read)
+  GP_CHECK(gp::ensure(c, c->part_a, (size_t)maxb * gp::kMaxDim * 2 * sizeof(double)));
+  {
+    unsigned gb = grid_for(n, kThreads, maxb);
+    k_bbox<<<gb, kThreads, 0, c->stream>>>(x, n, dim, (double*)c->part_a.p, s);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+  }
+  GP_CHECK(gp::ensure_pinned(c, sizeof(gp::AsmScalars)));
+  GP_CUDA(cudaMemcpyAsync(c->pinned, s, sizeof(gp::AsmScalars), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  gp::AsmScalars hs = *(gp::AsmScalars*)c->pinned;
+  for (int k = 0; k < dim; ++k)
+    if (!isfinite(hs.bbox_lo[k]) || !isfinite(hs.bbox_hi[k])) return GP_ERR_INVALID_ARG;
+
+  // --- grid: cells of edge h >= r_s (slightly enlarged so that rounding in
+  // the cell index can never separate two points closer than r_s by two cells)
+  gp::Grid g{};
+  g.dim = dim;
+  double h_cell = c->r_s * (1.0 + 1e-9);
+  double ext[3] = {0, 0, 0};
+  for (int k = 0; k < dim; ++k) {
+    g.lo[k] = hs.bbox_lo[k];
+    ext[k] = hs.bbox_hi[k] - hs.bbox_lo[k];
+  }
+  const double max_cells = (double)(1 << 25);
+  for (;;) {
+    double tot = 1.0;
+    for (int k = 0; k < dim; ++k) tot *= floor(ext[k] / h_cell) + 1.0;
+    if (tot <= max_cells) break;
+    h_cell *= 1.25;
+  }
+  g.h = h_cell;
+  g.ncells = 1;
+  g.keybits = 0;
+  for (int k = 0; k < gp::kMaxDim; ++k) {
+    g.G[k] = k < dim ? (int)(floor(ext[k] / h_cell) + 1.0) : 1;
+    int b = 0;
+    while (((int64_t)1 << b) < g.G[k]) ++b;
+    g.bits[k] = b;
+    g.keybits += b;
+    g.ncells *= g.G[k];
+  }
+  if (g.keybits > 32) return GP_ERR_UNSUPPORTED;
+  c->grid = g;
+
+  // --- bump parameters with FP32 pre-filter margins
+  {
+    double L = 0.0;
+    for (int k = 0; k < dim; ++k) L = fmax(L, ext[k]);
+    std::vector<gp::BumpParam> hb(nb);
+    for (int m = 0; m < n1; ++m)
+      for (int j = 0; j < n2; ++j) {
+        const double* q = h + (size_t)(m * n2 + j) * (dim + 2);
+        gp::BumpParam& bp = hb[m * n2 + j];
+        double cmax = 0.0;
+        for (int k = 0; k < gp::kMaxDim; ++k) {
+          bp.c[k] = k < dim ? q[k] : 0.0;
+          bp.c32[k] = k < dim ? (float)(q[k] - g.lo[k]) : 0.f;
+          if (k < dim) cmax = fmax(cmax, fabs(q[k] - g.lo[k]));
+        }
+        const double r = q[dim];
+        bp.r = r;
+        bp.r2 = r * r;
+        bp.a = q[dim + 1];
+        bp.m = m;
+        bp.inv_r2_32 = (float)(1.0 / (r * r));
+        // FP32 coordinate error per axis <= 2^-24 (L + cmax) each for x and c,
+        // plus rounding of the difference; q moves by at most about
+        // 2 sqrt(dim) err / r near q = 1.  Keep a 16x safety factor.
+        const double err = 2.0 * 6.0e-8 * (L + cmax + r);
+        double margin = 16.0 * (2.0 * sqrt((double)dim) * err / r + 4e-7);
+        bp.margin = margin > 0.5 ? 1e30f : (float)margin;
+      }
+    GP_CHECK(gp::ensure(c, c->bump, sizeof(gp::BumpParam) * nb));
+    GP_CHECK(gp::ensure_pinned(c, sizeof(gp::BumpParam) * nb));
+    memcpy(c->pinned, hb.data(), sizeof(gp::BumpParam) * nb);
+    GP_CUDA(cudaMemcpyAsync(c->bump.p, c->pinned, sizeof(gp::BumpParam) * nb, cudaMemcpyHostToDevice, c->stream));
+  }
+
+  // --- bump table over all points
+  GP_CHECK(gp::ensure(c, c->F0, (size_t)n * n1 * sizeof(double)));
+  GP_CHECK(gp::ensure(c, c->mask0, (size_t)n * sizeof(uint32_t)));
+  GP_CHECK(gp::ensure(c, c->cnt, (size_t)n * sizeof(int32_t)));
+  GP_CHECK(gp::ensure(c, c->pos, (size_t)(n + 1) * sizeof(int64_t)));
+  {
+    unsigned gb = grid_for(n, kThreads, maxb);
+    size_t smem = sizeof(gp::BumpParam) * nb;
+    k_bump_table<<<gb, kThreads, smem, c->stream>>>(x, n, dim, (const gp::BumpParam*)c->bump.p, n1, n2, c->beta,
+                                                    g.lo[0], dim > 1 ? g.lo[1] : 0.0, dim > 2 ? g.lo[2] : 0.0,
+                                                    (double*)c->F0.p, (uint32_t*)c->mask0.p,
+                                                    (int32_t*)c->cnt.p);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+  }
+  GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->cnt.p, (int64_t*)c->pos.p, n));
+  int64_t n_act = 0;
+  GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->pos.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  n_act = *(int64_t*)c->pinned;
+  c->n_act = n_act;
+  c->nnz = 0;
+  if (n_act == 0) return GP_OK;
+
+  // --- Morton keys of the active points, stable radix sort
+  GP_CHECK(gp::ensure(c, c->keys, (size_t)n_act * 4));
+  GP_CHECK(gp::ensure(c, c->vals, (size_t)n_act * 4));
+  GP_CHECK(gp::ensure(c, c->keys2, (size_t)n_act * 4));
+  GP_CHECK(gp::ensure(c, c->vals2, (size_t)n_act * 4));
+  {
+    unsigned gb = grid_for(n, kThreads, maxb);
+    k_keys<<<gb, kThreads, 0, c->stream>>>(x, n, (const int64_t*)c->pos.p, (const uint32_t*)c->mask0.p, g,
+                                           (uint32_t*)c->keys.p, (uint32_t*)c->vals.p);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+  }
+  const int passes = (g.keybits + 7) / 8;
+  const int ntiles = (int)((n_act + kRsTile - 1) / kRsTile);
+  GP_CHECK(gp::ensure(c, c->hist, (size_t)256 * ntiles * sizeof(int32_t)));
+  GP_CHECK(gp::ensure(c, c->hist_scan, (size_t)(256 * ntiles + 1) * sizeof(int64_t)));
+  for (int ps = 0; ps < passes; ++ps) {
+    const int shift = 8 * ps;
+    k_rs_hist<<<ntiles, kThreads, 0, c->stream>>>((const uint32_t*)c->keys.p, n_act, shift, ntiles,
+                                                  (int32_t*)c->hist.p);
+    GP_LAUNCH_CHECK();
+    GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->hist.p, (int64_t*)c->hist_scan.p, (int64_t)256 * ntiles));
+    k_rs_scatter<<<ntiles, kThreads, 0, c->stream>>>((const uint32_t*)c->keys.p, (const uint32_t*)c->vals.p, n_act,
+                                                     shift, ntiles, (const int64_t*)c->hist_scan.p,
+                                                     (uint32_t*)c->keys2.p, (uint32_t*)c->vals2.p);
+    GP_LAUNCH_CHECK();
+    c->launches += 2;
+    std::swap(c->keys, c->keys2);
+    std::swap(c->vals, c->vals2);
+  }
+
+  // --- sorted point data, cell table, sum ln D
+  GP_CHECK(gp::ensure(c, c->cells, (size_t)g.ncells * sizeof(int2)));
+  GP_CUDA(cudaMemsetAsync(c->cells.p, 0, (size_t)g.ncells * sizeof(int2), c->stream));
+  GP_CHECK(gp::ensure(c, c->cellc, (size_t)n_act * sizeof(int4)));
+  GP_CHECK(gp::ensure(c, c->xr, (size_t)n_act * sizeof(float4)));
+  GP_CHECK(gp::ensure(c, c->xs, (size_t)n_act * dim * sizeof(double)));
+  GP_CHECK(gp::ensure(c, c->Fs, (size_t)n_act * n1 * sizeof(T)));
+  GP_CHECK(gp::ensure(c, c->smask, (size_t)n_act * sizeof(uint32_t)));
+  GP_CHECK(gp::ensure(c, c->dinv, (size_t)n_act * sizeof(T)));
+  GP_CHECK(gp::ensure(c, c->dinv64, (size_t)n_act * sizeof(double)));
+  GP_CHECK(gp::ensure(c, c->part_b, (size_t)maxb * sizeof(double)));
+  const double AC = c->A * kPrefactor;
+  {
+    unsigned gb = grid_for(n_act, kThreads, maxb);
+    k_sorted<T><<<gb, kThreads, 0, c->stream>>>(x, n_act, (const uint32_t*)c->keys.p, (const uint32_t*)c->vals.p, g,
+                                                (const double*)c->F0.p, (const uint32_t*)c->mask0.p, n1, AC,
+                                                c->sigma2, (int4*)c->cellc.p, (float4*)c->xr.p, (double*)c->xs.p,
+                                                (T*)c->Fs.p, (uint32_t*)c->smask.p, (T*)c->dinv.p,
+                                                (double*)c->dinv64.p, (int2*)c->cells.p, (double*)c->part_b.p, s);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+  }
+
+  // --- two-pass CSR: count, scan, fill
+  PairArgs pa{};
+  pa.n = n_act;
+  pa.dim = dim;
+  pa.nstencil = dim == 1 ? 3 : (dim == 2 ? 9 : 27);
+  pa.n1 = n1;
+  pa.G0 = g.G[0];
+  pa.G1 = g.G[1];
+  pa.G2 = g.G[2];
+  pa.cells = (const int2*)c->cells.p;
+  pa.cellc = (const int4*)c->cellc.p;
+  pa.mask = (const uint32_t*)c->smask.p;
+  pa.xr = (const float4*)c->xr.p;
+  pa.xs = (const double*)c->xs.p;
+  pa.Fs = c->Fs.p;
+  pa.dinv = c->dinv.p;
+  pa.cnt = (int32_t*)c->cnt.p;
+  const double sc = (g.h / c->r_s) * (g.h / c->r_s);
+  pa.scale = (float)sc;
+  pa.guard = (float)(1e-4 * sc);
+  pa.rs2 = c->r_s * c->r_s;
+  pa.AC = AC;
+  pa.sigma2 = c->sigma2;
+  const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
+  k_pair<T, false><<<gw, kThreads, 0, c->stream>>>(pa);
+  GP_LAUNCH_CHECK();
+  c->launches += 1;
+  GP_CHECK(gp::ensure(c, c->row_ptr, (size_t)(n_act + 1) * sizeof(int64_t)));
+  GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->cnt.p, (int64_t*)c->row_ptr.p, n_act));
+  GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->row_ptr.p + n_act, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t nnz = *(int64_t*)c->pinned;
+  c->nnz = nnz;
+  GP_CHECK(gp::ensure(c, c->col, (size_t)nnz * sizeof(int32_t)));
+  GP_CHECK(gp::ensure(c, c->val, (size_t)nnz * sizeof(T)));
+  pa.row_ptr = (const int64_t*)c->row_ptr.p;
+  pa.col = (int32_t*)c->col.p;
+  pa.val = c->val.p;
+  const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
+  if (timed) {
+    GP_CHECK(gp::kernel_events(c));
+    GP_CUDA(cudaEventRecord(c->kev[128], c->stream));
+  }
+  k_pair<T, true><<<gw, kThreads, 0, c->stream>>>(pa);
+  GP_LAUNCH_CHECK();
+  c->launches += 1;
+  if (timed) {
+    GP_CUDA(cudaEventRecord(c->kev[129], c->stream));
+    GP_CUDA(cudaEventSynchronize(c->kev[129]));
+    c->t_fill += gp::event_ms(c->kev[128], c->kev[129]);
+  }
+  return GP_OK;
+}
+
+}  // namespace
+
+namespace gp {
+
+int assemble(gp_ctx* c, const double* x, int64_t n, const double* h, int precision) {
+  c->assembled = false;
+  c->precision = precision;
+  c->n = n;
+  const size_t nbp = (size_t)c->nb * (c->dim + 2);
+  c->r_s = h[nbp];
+  c->A = h[nbp + 1];
+  c->sigma2 = h[nbp + 2];
+  if (n > (int64_t)INT32_MAX - 1) return GP_ERR_UNSUPPORTED;
+  c->n_act = 0;
+  c->nnz = 0;
+  if (n > 0) {
+    int st = precision == GP_FP64 ? assemble_t<double>(c, x, n, h) : assemble_t<float>(c, x, n, h);
+    if (st != GP_OK) return st;
+  }
+  c->assembled = true;
+  return GP_OK;
+}
+
+int csr_unscaled(gp_ctx* c, double* out) {
+  if (c->n_act == 0) return GP_OK;
+  const unsigned gw = grid_for(c->n_act, kWarps, c->num_sms * 8);
+  if (c->precision == GP_FP64)
+    k_unscale<double><<<gw, kThreads, 0, c->stream>>>(c->n_act, (const int64_t*)c->row_ptr.p,
+                                                     (const int32_t*)c->col.p, (const double*)c->val.p,
+                                                     (const double*)c->dinv64.p, out);
+  else
+    k_unscale<float><<<gw, kThreads, 0, c->stream>>>(c->n_act, (const int64_t*)c->row_ptr.p,
+                                                    (const int32_t*)c->col.p, (const float*)c->val.p,
+                                                    (const double*)c->dinv64.p, out);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+}  // namespace gp

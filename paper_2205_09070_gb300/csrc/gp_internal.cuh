@@ -1,0 +1,280 @@
+// Internal declarations shared by the translation units of libgpsparse.
+// Paper: arXiv 2205.09070 (sparse exact GPs with compactly supported,
+// non-stationary bump-sum kernels).  Section / equation references below are
+// to that paper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/gpsparse.h"
+
+namespace gp {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxFuncs = 32;      // support mask is one 32-bit word
+constexpr int kMaxBumps = 512;     // n_funcs * n_bumps
+constexpr int kMaxProbes = 64;     // probe sign bits: two 32-bit words per row
+constexpr int kMaxCols = 68;       // 1 + n_probes, padded to a multiple of 4
+constexpr int kMaxLanczos = 64;
+constexpr int kScanItems = 4096;   // elements per block of the 3-phase scan
+
+// One bump of Eq. eq:bump, in the layout the kernels read.
+struct BumpParam {
+  double c[kMaxDim];   // centre
+  double r2;           // radius^2
+  double a;            // amplitude
+  double r;            // radius
+  float c32[kMaxDim];  // centre - lo, FP32 (for the pre-filter)
+  float inv_r2_32;     // 1 / r^2, FP32
+  float margin;        // pre-filter accepts q32 < 1 + margin, then re-tests in FP64
+  int m;               // function index
+};
+
+// Uniform search grid (cells of edge h >= r_s, Morton-ordered).
+struct Grid {
+  double lo[kMaxDim];
+  double h;          // cell edge
+  int G[kMaxDim];    // cells per dimension
+  int bits[kMaxDim]; // Morton bits per dimension
+  int dim;
+  int keybits;
+  int64_t ncells;
+};
+
+// Scalars of one batched CG run, in device memory.
+struct CgState {
+  double rr[kMaxCols];
+  double rr0[kMaxCols];
+  double alpha[kMaxCols];
+  double beta[kMaxCols];
+  int done[kMaxCols];
+  int steps[kMaxCols];     // Lanczos steps recorded per column
+  int iter;                // iterations completed
+  int finished;            // set by the last kernel of an iteration: later kernels return at once
+  int pending;             // all columns converged / breakdown / cap, seen by the iteration's first update
+  int status;              // GP_OK or GP_ERR_NOT_SPD
+  int bad_col;
+  unsigned ticket_a;       // last-block tickets (reset by the last block)
+  unsigned ticket_b;
+  unsigned ticket_c;
+  int max_iter;
+  double tol2;             // cg_rtol^2
+};
+
+// Reductions produced by assembly / likelihood kernels.
+struct AsmScalars {
+  double bbox_lo[kMaxDim];
+  double bbox_hi[kMaxDim];
+  double sum_log_d;        // sum over active rows of ln K_ii
+  double inact_y2;         // sum over inactive rows of y_i^2
+  long long n_inactive;
+  double quad_form;        // y_act^T alpha_act
+  double slq_mean;         // mean over probes of the Lanczos quadrature (already x N_act)
+  double slq_var;          // sample variance of the probe terms
+  double grad_A;
+  double grad_rs;
+  double grad_s2;
+  unsigned ticket0;
+  unsigned ticket1;
+  unsigned ticket2;
+  unsigned ticket3;
+  int status;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace gp
+
+struct gp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int dim = 0, n1 = 0, n2 = 0, nb = 0;
+  double beta = 1.0;
+  int num_sms = 0;
+
+  // last assembly
+  bool assembled = false;
+  int precision = GP_FP32_MIXED;
+  int64_t n = 0, n_act = 0, nnz = 0;
+  double r_s = 0, A = 0, sigma2 = 0;
+  gp::Grid grid{};
+
+  // device buffers (grow-only)
+  gp::DevBuf x_in, y_in, out_tmp;
+  gp::DevBuf bump;
+  gp::DevBuf mask0, F0, pos;
+  gp::DevBuf keys, vals, keys2, vals2, hist, hist_scan, scan_part;
+  gp::DevBuf cells;
+  gp::DevBuf perm, skey, cellc, xr, xs, Fs, smask, dinv, dinv64;
+  gp::DevBuf cnt, row_ptr, col, val;
+  gp::DevBuf X, R, P, Q, zbits;
+  gp::DevBuf part_a, part_b, part_c, hist_alpha, hist_beta;
+  gp::DevBuf g, grad_part, grad_bump;
+  gp::DevBuf cg, asm_s;
+  gp::DevBuf csr_tmp;
+
+  // pinned host staging
+  void* pinned = nullptr;
+  size_t pinned_cap = 0;
+
+  cudaEvent_t ev[8] = {};
+
+  // instrumentation (GP_FLAG_TIME_KERNELS)
+  int flags = 0;
+  int64_t launches = 0;
+  cudaEvent_t kev[2 * 64 + 4] = {};
+  bool kev_ready = false;
+  double t_spmm = 0.0, t_fill = 0.0, t_adj = 0.0;
+  int n_spmm = 0;
+  int bad_col = -1, bad_iter = 0;   // where the last CG run stopped on a breakdown
+};
+
+namespace gp {
+
+// ---------------------------------------------------------------- host utils
+int ensure(gp_ctx* c, DevBuf& b, size_t bytes);
+int ensure_pinned(gp_ctx* c, size_t bytes);
+int kernel_events(gp_ctx* c);            // create the timing event pool once
+double event_ms(cudaEvent_t a, cudaEvent_t b);
+int cuda_status(cudaError_t e);
+bool is_device_ptr(const void* p);
+
+// ---------------------------------------------------------------- launchers
+// scan.cu: exclusive scan of n int32 values into int64 (out has n+1 entries,
+// out[n] = total).  Deterministic 3-phase scan.
+int scan_i32_to_i64(gp_ctx* c, const int32_t* in, int64_t* out, int64_t n);
+
+// assemble.cu
+int assemble(gp_ctx* c, const double* x_dev, int64_t n, const double* h, int precision);
+int csr_unscaled(gp_ctx* c, double* val_out_dev);
+
+// solve.cu
+int cg_run(gp_ctx* c, int k, int kp, const double* y_dev, int n_probes, uint64_t seed,
+           int lanczos_steps, int max_iter, double rtol, int check_every,
+           int* iters_out, double* max_rel_resid);
+int cg_run_fp64(gp_ctx* c, int k, const double* y_dev, int n_probes, uint64_t seed,
+                int lanczos_steps, int max_iter, double rtol, int check_every,
+                int* iters_out, double* max_rel_resid);
+int inactive_terms(gp_ctx* c, const double* y_dev);
+int quad_form(gp_ctx* c, const double* y_dev, int kp);
+int slq(gp_ctx* c, int n_probes, int kcols);
+int alpha_out(gp_ctx* c, const double* y_dev, double* alpha_dev, int kp);
+
+// adjoint.cu
+int adjoint(gp_ctx* c, int n_probes, int kp);
+
+}  // namespace gp
+
+// ---------------------------------------------------------------- device utils
+namespace gpd {
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the k-th output of the
+// stream whose state starts at `seed` is the finaliser applied to
+// seed + (k + 1) * 0x9E3779B97F4A7C15.
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Rademacher sign bit of probe l at original point index i: 1 means -1.
+__device__ inline unsigned probe_bit(uint64_t seed, int l, long long i) {
+  return (unsigned)(splitmix64(seed, ((uint64_t)l << 40) + (uint64_t)i) >> 63);
+}
+
+// Stationary kernel of Eq. eq:kstat divided by its prefactor C = sqrt(2)/(3 sqrt(pi)),
+// as a function of rho^2 = (d/r)^2 and s^2 = 1 - rho^2 (both given, s2 > 0).
+// With s = sqrt(1 - rho^2) the printed form is
+//   (1 + 2 rho^2) s - 3 rho^2 log((1 + s) / rho)
+// and, expanding atanh(s) = log((1+s)/rho), it equals the all-positive series
+//   s^5 * sum_{k>=0} 6 s^(2k) / ((2k+3)(2k+5)),
+// which is free of the cancellation the printed form suffers as rho -> 1.
+__device__ inline float kstat_unit_f(float rho2, float s2) {
+  float s = sqrtf(s2);
+  if (s <= 0.8f) {
+    float g = 0.0f;
+#pragma unroll
+    for (int k = 30; k >= 0; --k) g = fmaf(g, s2, 6.0f / (float)((2 * k + 3) * (2 * k + 5)));
+    return s2 * s2 * s * g;
+  }
+  if (rho2 <= 0.0f) return 1.0f;
+  float rho = sqrtf(rho2);
+  return (1.0f + 2.0f * rho2) * s - 3.0f * rho2 * logf((1.0f + s) / rho);
+}
+
+__device__ inline double kstat_unit_d(double rho2, double s2) {
+  double s = sqrt(s2);
+  if (s <= 0.5) {
+    double g = 0.0;
+#pragma unroll
+    for (int k = 26; k >= 0; --k) g = fma(g, s2, 6.0 / (double)((2 * k + 3) * (2 * k + 5)));
+    return s2 * s2 * s * g;
+  }
+  if (rho2 <= 0.0) return 1.0;
+  double rho = sqrt(rho2);
+  return (1.0 + 2.0 * rho2) * s - 3.0 * rho2 * log((1.0 + s) / rho);
+}
+
+// atanh(s) - s = s^3 sum_{k>=0} s^(2k) / (2k+3); used for
+// d k~/d r_s = (6 C / r_s) rho^2 (atanh(s) - s), from differentiating Eq. eq:kstat.
+__device__ inline float atanh_minus_s_f(float rho2, float s2) {
+  float s = sqrtf(s2);
+  if (s <= 0.5f) {
+    float g = 0.0f;
+#pragma unroll
+    for (int k = 12; k >= 0; --k) g = fmaf(g, s2, 1.0f / (float)(2 * k + 3));
+    return s2 * s * g;
+  }
+  if (rho2 <= 0.0f) return 0.0f;  // multiplied by rho^2 = 0 by the caller
+  return logf((1.0f + s) / sqrtf(rho2)) - s;
+}
+
+__device__ inline double atanh_minus_s_d(double rho2, double s2) {
+  double s = sqrt(s2);
+  if (s <= 0.3) {
+    double g = 0.0;
+#pragma unroll
+    for (int k = 18; k >= 0; --k) g = fma(g, s2, 1.0 / (double)(2 * k + 3));
+    return s2 * s * g;
+  }
+  if (rho2 <= 0.0) return 0.0;
+  return log((1.0 + s) / sqrt(rho2)) - s;
+}
+
+template <typename T> struct Real;
+template <> struct Real<float> {
+  __device__ static float kstat(float r2, float s2) { return kstat_unit_f(r2, s2); }
+  __device__ static float dk(float r2, float s2) { return atanh_minus_s_f(r2, s2); }
+};
+template <> struct Real<double> {
+  __device__ static double kstat(double r2, double s2) { return kstat_unit_d(r2, s2); }
+  __device__ static double dk(double r2, double s2) { return atanh_minus_s_d(r2, s2); }
+};
+
+__device__ inline unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace gpd
+
+#define GP_CHECK(call)                        \
+  do {                                        \
+    int _s = (call);                          \
+    if (_s != GP_OK) return _s;               \
+  } while (0)
+
+#define GP_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return gp::cuda_status(_e);  \
+  } while (0)
+
+#define GP_LAUNCH_CHECK() GP_CUDA(cudaGetLastError())

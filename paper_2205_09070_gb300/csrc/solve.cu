@@ -1,0 +1,900 @@
+// Conjugate gradients on the Jacobi-scaled active block Khat (Sec. 2.5: K x = y
+// by CG) and the stochastic Lanczos quadrature of ln|Khat| from the same CG
+// iterations (the Lanczos tridiagonal of a CG run started at x0 = 0 is fixed
+// by its step lengths alpha_t and direction updates beta_t).
+//
+// FP32_MIXED: one CG over the block [yhat, z_1 .. z_nv] (row-major, kp floats
+// per row).  Per iteration three kernels:
+//   A  Q = Khat P (SpMM) with p_c^T q_c per column in FP64 -> alpha_c
+//   B  R -= alpha Q, |r_c|^2 in FP64                        -> beta_c, convergence
+//   C  X += alpha P_old, P = R + beta P_old
+// The scalars of each kernel are finished by its last block (threadfence +
+// ticket), so the per-column reductions are deterministic and no kernel waits
+// on another.
+// FP64: one single-RHS CG per column, all in FP64 (the plain comparison path).
+#include <math.h>
+
+#include "gp_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Sum partials part[b * stride + t] over blocks b < nblk for t < width with all
+// threads of the block, in a fixed order; result in out[t] (shared).
+__device__ void block_sum_partials(const double* part, int nblk, int width, int stride, double* out,
+                                   double* scratch /* >= kThreads doubles */) {
+  const int groups = kThreads / width;  // width <= kMaxCols < kThreads
+  const int t = threadIdx.x % width, grp = threadIdx.x / width;
+  double acc = 0.0;
+  if (grp < groups)
+    for (int b = grp; b < nblk; b += groups) acc += __ldcg(part + (int64_t)b * stride + t);
+  scratch[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < width) {
+    double s = 0.0;
+    for (int g2 = 0; g2 < groups; ++g2) s += scratch[g2 * width + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ inline bool last_block(unsigned* ticket) {
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// alpha_c = rr_c / p_c^T q_c for columns still running (Saad, Alg. 6.18).
+__device__ void finish_alpha(gp::CgState* st, const double* pq, int k, int col0, double* hist_alpha, int m_hist) {
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double a = 0.0;
+    if (!st->done[c]) {
+      const double d = pq[c];
+      if (!(d > 0.0) || !isfinite(d)) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = col0 + c;
+      } else {
+        a = st->rr[c] / d;
+        const int it = st->iter;
+        if (it < m_hist) {
+          hist_alpha[it * gp::kMaxCols + col0 + c] = a;
+          st->steps[col0 + c] = it + 1;
+        }
+      }
+    }
+    st->alpha[c] = a;
+  }
+}
+
+// beta_c = |r_new|^2 / |r|^2, convergence |r_new|^2 <= tol^2 |r_0|^2.
+__device__ void finish_beta(gp::CgState* st, const double* rr_new, int k, int col0, double* hist_beta, int m_hist) {
+  __shared__ int any_running;
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  const int it = st->iter;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double b = 0.0;
+    if (!st->done[c]) {
+      const double r = rr_new[c];
+      b = r / st->rr[c];
+      if (it < m_hist) hist_beta[it * gp::kMaxCols + col0 + c] = b;
+      st->rr[c] = r;
+      if (r <= st->tol2 * st->rr0[c]) st->done[c] = 1;
+      else atomicOr(&any_running, 1);
+      if (!isfinite(r)) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = col0 + c;
+      }
+    }
+    st->beta[c] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->iter = it + 1;
+    st->pending = (!any_running) || st->status != GP_OK || st->iter >= st->max_iter;
+  }
+}
+
+// ---------------------------------------------------------------- FP32 batched
+// Initial block: R = P = [yhat, z_1..z_nv, 0 pad], X = 0, probe sign bits.
+__global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp, const double* __restrict__ y,
+                                                       const uint32_t* __restrict__ perm,
+                                                       const double* __restrict__ dinv64, uint64_t seed, int nv,
+                                                       float* __restrict__ X, float* __restrict__ R,
+                                                       float* __restrict__ P, uint32_t* __restrict__ zbits,
+                                                       double* __restrict__ part, gp::CgState* st, double tol2,
+                                                       int max_iter) {
+  double acc = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = perm[p];
+    const float yh = (float)(y[i] * dinv64[p]);
+    acc += (double)yh * (double)yh;
+    uint32_t zb[2] = {0u, 0u};
+    float* xr = X + p * kp;
+    float* rr = R + p * kp;
+    float* pr = P + p * kp;
+    xr[0] = 0.f;
+    rr[0] = yh;
+    pr[0] = yh;
+    for (int l = 0; l < nv; ++l) {
+      const unsigned b = gpd::probe_bit(seed, l, (long long)i);
+      zb[l >> 5] |= b << (l & 31);
+      const float z = b ? -1.f : 1.f;
+      xr[1 + l] = 0.f;
+      rr[1 + l] = z;
+      pr[1 + l] = z;
+    }
+    for (int c = 1 + nv; c < kp; ++c) {
+      xr[c] = 0.f;
+      rr[c] = 0.f;
+      pr[c] = 0.f;
+    }
+    zbits[2 * p] = zb[0];
+    zbits[2 * p + 1] = zb[1];
+  }
+  __shared__ double sh[kThreads];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (last_block(&st->ticket_c)) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
+      st->iter = 0;
+      st->status = GP_OK;
+      st->bad_col = -1;
+      st->max_iter = max_iter;
+      st->tol2 = tol2;
+      bool any = false;
+      for (int c = 0; c < gp::kMaxCols; ++c) {
+        double r0 = c == 0 ? t : (c < k ? (double)n : 0.0);
+        st->rr0[c] = r0;
+        st->rr[c] = r0;
+        st->alpha[c] = 0.0;
+        st->beta[c] = 0.0;
+        st->done[c] = !(r0 > 0.0);
+        st->steps[c] = 0;
+        any = any || (c < k && !st->done[c]);
+      }
+      st->pending = !any;
+      st->finished = !any;
+    }
+  }
+}
+
+// A: Q = Khat P with per-column p^T q.  One warp per row; the warp's lanes
+// form NG = 32/G groups of G lanes, a group takes every NG-th nonzero of the
+// row and each of its lanes owns one float4 of the kp = 4G columns.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_spmm_f32(int64_t n, int k, const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col,
+                                                       const float* __restrict__ val, const float4* __restrict__ P,
+                                                       float4* __restrict__ Q, double* __restrict__ part,
+                                                       gp::CgState* st, double* hist_alpha, int m_hist) {
+  if (st->finished) return;
+  constexpr int NG = 32 / G;
+  constexpr int KP = 4 * G;
+  __shared__ double sh[kWarps][KP];
+  __shared__ double scratch[kThreads];
+  __shared__ double tot[KP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane - grp * G;
+  const bool act = grp < NG;
+  double pq0 = 0, pq1 = 0, pq2 = 0, pq3 = 0;
+  for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < n; p += (int64_t)gridDim.x * kWarps) {
+    const int64_t s = rp[p], e = rp[p + 1];
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      for (int64_t idx = s + grp; idx < e; idx += NG) {
+        const int j = __ldg(col + idx);
+        const float v = __ldg(val + idx);
+        const float4 pj = __ldg(P + (int64_t)j * G + gl);
+        q.x = fmaf(v, pj.x, q.x);
+        q.y = fmaf(v, pj.y, q.y);
+        q.z = fmaf(v, pj.z, q.z);
+        q.w = fmaf(v, pj.w, q.w);
+      }
+    }
+    // group 0 adds the partial sums of groups 1..NG-1 (each read unmodified)
+    const float4 q0 = q;
+#pragma unroll
+    for (int g2 = 1; g2 < NG; ++g2) {
+      const int src = gl + g2 * G;
+      q.x += __shfl_sync(kFull, q0.x, src);
+      q.y += __shfl_sync(kFull, q0.y, src);
+      q.z += __shfl_sync(kFull, q0.z, src);
+      q.w += __shfl_sync(kFull, q0.w, src);
+    }
+    if (grp == 0) {
+      Q[p * G + gl] = q;
+      const float4 pp = __ldg(P + p * G + gl);
+      pq0 += (double)pp.x * q.x;
+      pq1 += (double)pp.y * q.y;
+      pq2 += (double)pp.z * q.z;
+      pq3 += (double)pp.w * q.w;
+    }
+  }
+  if (grp == 0) {
+    sh[w][4 * gl + 0] = pq0;
+    sh[w][4 * gl + 1] = pq1;
+    sh[w][4 * gl + 2] = pq2;
+    sh[w][4 * gl + 3] = pq3;
+  }
+  __syncthreads();
+  if (threadIdx.x < KP) {
+    double t = 0.0;
+    for (int ww = 0; ww < kWarps; ++ww) t += sh[ww][threadIdx.x];
+    part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
+    __threadfence();
+  }
+  if (last_block(&st->ticket_a)) {
+    block_sum_partials(part, gridDim.x, KP, KP, tot, scratch);
+    finish_alpha(st, tot, k, 0, hist_alpha, m_hist);
+  }
+}
+
+// B: R -= alpha Q and |r_c|^2.  Block = (KQ float4 columns) x (rows).
+__global__ void k_upd_r_f32(int64_t n, int k, int kq, const float4* __restrict__ Q, float4* __restrict__ R,
+                            double* __restrict__ part, gp::CgState* st, double* hist_beta, int m_hist) {
+  if (st->finished) return;
+  __shared__ double scratch[kThreads];
+  __shared__ double red[kThreads * 4];
+  __shared__ double tot[gp::kMaxCols];
+  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq, ny = blockDim.x / kq;
+  const bool act = ty < ny;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (act) a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1], (float)st->alpha[4 * tx + 2],
+                           (float)st->alpha[4 * tx + 3]);
+  double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+  if (act) {
+    for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += (int64_t)gridDim.x * ny) {
+      float4 r = R[p * kq + tx];
+      const float4 q = Q[p * kq + tx];
+      r.x = fmaf(-a.x, q.x, r.x);
+      r.y = fmaf(-a.y, q.y, r.y);
+      r.z = fmaf(-a.z, q.z, r.z);
+      r.w = fmaf(-a.w, q.w, r.w);
+      R[p * kq + tx] = r;
+      r0 += (double)r.x * r.x;
+      r1 += (double)r.y * r.y;
+      r2 += (double)r.z * r.z;
+      r3 += (double)r.w * r.w;
+    }
+  }
+  red[threadIdx.x * 4 + 0] = r0;
+  red[threadIdx.x * 4 + 1] = r1;
+  red[threadIdx.x * 4 + 2] = r2;
+  red[threadIdx.x * 4 + 3] = r3;
+  __syncthreads();
+  const int kp = 4 * kq;
+  if (threadIdx.x < kp) {
+    const int cx = threadIdx.x / 4, cc = threadIdx.x % 4;
+    double t = 0.0;
+    for (int yy = 0; yy < ny; ++yy) t += red[(yy * kq + cx) * 4 + cc];
+    part[(int64_t)blockIdx.x * kp + threadIdx.x] = t;
+    __threadfence();
+  }
+  if (last_block(&st->ticket_b)) {
+    block_sum_partials(part, gridDim.x, kp, kp, tot, scratch);
+    finish_beta(st, tot, k, 0, hist_beta, m_hist);
+  }
+}
+
+// C: X += alpha P_old, P = R + beta P_old.
+__global__ void k_upd_xp_f32(int64_t n, int kq, float4* __restrict__ X, const float4* __restrict__ R,
+                             float4* __restrict__ P, gp::CgState* st) {
+  if (st->finished) return;
+  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq, ny = blockDim.x / kq;
+  if (ty < ny) {
+    const float4 a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1],
+                                 (float)st->alpha[4 * tx + 2], (float)st->alpha[4 * tx + 3]);
+    const float4 b = make_float4((float)st->beta[4 * tx], (float)st->beta[4 * tx + 1], (float)st->beta[4 * tx + 2],
+                                 (float)st->beta[4 * tx + 3]);
+    for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += (int64_t)gridDim.x * ny) {
+      const int64_t o = p * kq + tx;
+      const float4 po = P[o];
+      const float4 r = R[o];
+      float4 x = X[o];
+      x.x = fmaf(a.x, po.x, x.x);
+      x.y = fmaf(a.y, po.y, x.y);
+      x.z = fmaf(a.z, po.z, x.z);
+      x.w = fmaf(a.w, po.w, x.w);
+      X[o] = x;
+      P[o] = make_float4(fmaf(b.x, po.x, r.x), fmaf(b.y, po.y, r.y), fmaf(b.z, po.z, r.z), fmaf(b.w, po.w, r.w));
+    }
+  }
+  if (last_block(&st->ticket_c)) {
+    if (threadIdx.x == 0) st->finished = st->pending;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 single RHS
+__global__ void __launch_bounds__(kThreads) k_init_f64(int64_t n, int col0, int nv, const double* __restrict__ y,
+                                                       const uint32_t* __restrict__ perm,
+                                                       const double* __restrict__ dinv64, uint64_t seed,
+                                                       double* __restrict__ X, double* __restrict__ R,
+                                                       double* __restrict__ P, uint32_t* __restrict__ zbits,
+                                                       double* __restrict__ part, gp::CgState* st, double tol2,
+                                                       int max_iter) {
+  double acc = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = perm[p];
+    double v;
+    if (col0 == 0) {
+      v = y[i] * dinv64[p];
+      uint32_t zb[2] = {0u, 0u};
+      for (int l = 0; l < nv; ++l) zb[l >> 5] |= gpd::probe_bit(seed, l, (long long)i) << (l & 31);
+      zbits[2 * p] = zb[0];
+      zbits[2 * p + 1] = zb[1];
+    } else {
+      v = gpd::probe_bit(seed, col0 - 1, (long long)i) ? -1.0 : 1.0;
+    }
+    X[p] = 0.0;
+    R[p] = v;
+    P[p] = v;
+    acc += v * v;
+  }
+  __shared__ double sh[kThreads];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (last_block(&st->ticket_c)) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
+      st->iter = 0;
+      st->status = GP_OK;
+      st->bad_col = -1;
+      st->max_iter = max_iter;
+      st->tol2 = tol2;
+      st->rr0[0] = t;
+      st->rr[0] = t;
+      st->alpha[0] = 0.0;
+      st->beta[0] = 0.0;
+      st->done[0] = !(t > 0.0);
+      st->steps[col0] = 0;
+      st->pending = st->done[0];
+      st->finished = st->done[0];
+    }
+  }
+}
+
+// A (FP64): q = Khat p, one warp per row, lanes over the row's nonzeros.
+__global__ void __launch_bounds__(kThreads) k_spmv_f64(int64_t n, const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col,
+                                                       const double* __restrict__ val, const double* __restrict__ P,
+                                                       double* __restrict__ Q, double* __restrict__ part,
+                                                       gp::CgState* st, int col0, double* hist_alpha, int m_hist) {
+  if (st->finished) return;
+  __shared__ double sh[kWarps];
+  __shared__ double tot[1];
+  __shared__ double scratch[kThreads];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double pq = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < n; p += (int64_t)gridDim.x * kWarps) {
+    double q = 0.0;
+    for (int64_t e = rp[p] + lane; e < rp[p + 1]; e += 32) q = fma(__ldg(val + e), __ldg(P + __ldg(col + e)), q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(kFull, q, o);
+    if (lane == 0) {
+      Q[p] = q;
+      pq += P[p] * q;
+    }
+  }
+  if (lane == 0) sh[w] = pq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int ww = 0; ww < kWarps; ++ww) t += sh[ww];
+    part[blockIdx.x] = t;
+  }
+  if (last_block(&st->ticket_a)) {
+    block_sum_partials(part, gridDim.x, 1, 1, tot, scratch);
+    finish_alpha(st, tot, 1, col0, hist_alpha, m_hist);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_upd_r_f64(int64_t n, const double* __restrict__ Q,
+                                                        double* __restrict__ R, double* __restrict__ part,
+                                                        gp::CgState* st, int col0, double* hist_beta, int m_hist) {
+  if (st->finished) return;
+  __shared__ double sh[kThreads];
+  __shared__ double tot[1];
+  const double a = st->alpha[0];
+  double acc = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double r = fma(-a, Q[p], R[p]);
+    R[p] = r;
+    acc += r * r;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (last_block(&st->ticket_b)) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
+      tot[0] = t;
+    }
+    __syncthreads();
+    finish_beta(st, tot, 1, col0, hist_beta, m_hist);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_upd_xp_f64(int64_t n, double* __restrict__ X,
+                                                         const double* __restrict__ R, double* __restrict__ P,
+                                                         gp::CgState* st) {
+  if (st->finished) return;
+  const double a = st->alpha[0], b = st->beta[0];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double po = P[p];
+    X[p] = fma(a, po, X[p]);
+    P[p] = fma(b, po, R[p]);
+  }
+  if (last_block(&st->ticket_c)) {
+    if (threadIdx.x == 0) st->finished = st->pending;
+  }
+}
+
+// ---------------------------------------------------------------- LML pieces
+// Inactive rows (outside every bump): K_ii = sigma_n^2 only; sum y_i^2 there.
+__global__ void __launch_bounds__(kThreads) k_inactive(int64_t n, const double* __restrict__ y,
+                                                       const uint32_t* __restrict__ mask0, double* part,
+                                                       gp::AsmScalars* s) {
+  double acc = 0.0;
+  long long cnt = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (mask0[i] == 0u) {
+      acc += y[i] * y[i];
+      ++cnt;
+    }
+  }
+  __shared__ double sh[kThreads];
+  __shared__ long long shc[kThreads];
+  sh[threadIdx.x] = acc;
+  shc[threadIdx.x] = cnt;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[threadIdx.x] += sh[threadIdx.x + o];
+      shc[threadIdx.x] += shc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sh[0];
+    ((long long*)part)[2 * blockIdx.x + 1] = shc[0];
+  }
+  if (last_block(&s->ticket2)) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      long long c = 0;
+      for (unsigned b = 0; b < gridDim.x; ++b) {
+        t += __ldcg(part + 2 * b);
+        c += __ldcg((const long long*)part + 2 * b + 1);
+      }
+      s->inact_y2 = t;
+      s->n_inactive = c;
+    }
+  }
+}
+
+// y_act^T K_act^-1 y_act = yhat^T alphahat with yhat = D^-1/2 y.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_quad(int64_t n, const double* __restrict__ y,
+                                                   const uint32_t* __restrict__ perm,
+                                                   const double* __restrict__ dinv64, const T* __restrict__ X,
+                                                   int64_t ld, double* part, gp::AsmScalars* s) {
+  double acc = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    acc += y[perm[p]] * dinv64[p] * (double)X[p * ld];
+  __shared__ double sh[kThreads];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (last_block(&s->ticket3)) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
+      s->quad_form = t;
+    }
+  }
+}
+
+// Eigenvalues and first eigenvector components of the symmetric tridiagonal
+// T (diagonal d[0..m), off-diagonal e[0..m-1)) by the implicit QL method with
+// Wilkinson-type shifts (Wilkinson & Reinsch; Golub & Van Loan Sec. 8.3),
+// accumulating only the first row z of the eigenvector matrix (Golub & Welsch).
+// Returns false if it fails to converge.
+__device__ bool tridiag_ql(double* d, double* e, double* z, int m) {
+  for (int i = 0; i < m; ++i) z[i] = i == 0 ? 1.0 : 0.0;
+  if (m > 0) e[m - 1] = 0.0;
+  for (int l = 0; l < m; ++l) {
+    int iter = 0;
+    for (;;) {
+      int mm = l;
+      for (; mm < m - 1; ++mm) {
+        const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
+        if (fabs(e[mm]) <= 1e-16 * dd) break;
+      }
+      if (mm == l) break;
+      if (++iter > 60) return false;
+      // shift from the leading 2x2 block
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = hypot(g, 1.0);
+      g = d[mm] - d[l] + e[l] / (g + (g >= 0.0 ? fabs(r) : -fabs(r)));
+      double s = 1.0, c = 1.0, p = 0.0;
+      int i = mm - 1;
+      bool deflated = false;
+      for (; i >= l; --i) {
+        const double f = s * e[i];
+        const double b = c * e[i];
+        r = hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= p;
+          e[mm] = 0.0;
+          deflated = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+        const double zf = z[i + 1];
+        z[i + 1] = s * z[i] + c * zf;
+        z[i] = c * z[i] - s * zf;
+      }
+      if (deflated) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[mm] = 0.0;
+    }
+  }
+  return true;
+}
+
+// One thread per probe: Lanczos T from the CG coefficients of column 1+l
+// (Saad, Sec. 6.7.3): T_tt = 1/alpha_t + beta_{t-1}/alpha_{t-1},
+// T_t,t+1 = sqrt(beta_t)/alpha_t; Gamma_l = |z|^2 sum_k tau_k^2 ln theta_k.
+__global__ void k_slq(int nv, int64_t n_act, const double* __restrict__ ha, const double* __restrict__ hb,
+                      const gp::CgState* st, gp::AsmScalars* s) {
+  __shared__ double gam[gp::kMaxProbes];
+  __shared__ int bad[gp::kMaxProbes];
+  const int l = threadIdx.x;
+  if (l < nv) {
+    const int c = 1 + l;
+    const int m = st->steps[c];
+    double d[gp::kMaxLanczos], e[gp::kMaxLanczos], z[gp::kMaxLanczos];
+    for (int t = 0; t < m; ++t) {
+      const double at = ha[t * gp::kMaxCols + c];
+      d[t] = 1.0 / at + (t > 0 ? hb[(t - 1) * gp::kMaxCols + c] / ha[(t - 1) * gp::kMaxCols + c] : 0.0);
+      e[t] = t + 1 < m ? sqrt(hb[t * gp::kMaxCols + c]) / at : 0.0;
+    }
+    bool ok = m > 0 && tridiag_ql(d, e, z, m);
+    double g = 0.0;
+    for (int t = 0; t < m && ok; ++t) {
+      if (!(d[t] > 0.0)) ok = false;
+      else g += z[t] * z[t] * log(d[t]);
+    }
+    gam[l] = g * (double)n_act;
+    bad[l] = !ok;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mean = 0.0;
+    int nbad = 0;
+    for (int q = 0; q < nv; ++q) {
+      mean += gam[q];
+      nbad += bad[q];
+    }
+    mean /= nv;
+    double var = 0.0;
+    for (int q = 0; q < nv; ++q) var += (gam[q] - mean) * (gam[q] - mean);
+    var = nv > 1 ? var / (nv - 1) : 0.0;
+    s->slq_mean = mean;
+    s->slq_var = var;
+    s->status = nbad ? GP_ERR_NOT_SPD : GP_OK;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_alpha_active(int64_t n, const uint32_t* __restrict__ perm,
+                                                           const double* __restrict__ dinv64,
+                                                           const T* __restrict__ X, int64_t ld,
+                                                           double* __restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    out[perm[p]] = dinv64[p] * (double)X[p * ld];
+}
+
+__global__ void __launch_bounds__(kThreads) k_alpha_inactive(int64_t n, const uint32_t* __restrict__ mask0,
+                                                             const double* __restrict__ y, double inv_s2,
+                                                             double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (mask0[i] == 0u) out[i] = y[i] * inv_s2;
+}
+
+unsigned grid_for(int64_t items, int per_block, int max_blocks) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (unsigned)g;
+}
+
+typedef void (*SpmmFn)(int64_t, int, const int64_t*, const int32_t*, const float*, const float4*, float4*, double*,
+                       gp::CgState*, double*, int);
+
+SpmmFn spmm_for(int G) {
+  switch (G) {
+    case 1: return k_spmm_f32<1>;
+    case 2: return k_spmm_f32<2>;
+    case 3: return k_spmm_f32<3>;
+    case 4: return k_spmm_f32<4>;
+    case 5: return k_spmm_f32<5>;
+    case 6: return k_spmm_f32<6>;
+    case 7: return k_spmm_f32<7>;
+    case 8: return k_spmm_f32<8>;
+    case 9: return k_spmm_f32<9>;
+    case 10: return k_spmm_f32<10>;
+    case 11: return k_spmm_f32<11>;
+    case 12: return k_spmm_f32<12>;
+    case 13: return k_spmm_f32<13>;
+    case 14: return k_spmm_f32<14>;
+    case 15: return k_spmm_f32<15>;
+    case 16: return k_spmm_f32<16>;
+    case 17: return k_spmm_f32<17>;
+    default: return nullptr;
+  }
+}
+
+int read_state(gp_ctx* c, gp::CgState* host) {
+  GP_CHECK(gp::ensure_pinned(c, sizeof(gp::CgState)));
+  GP_CUDA(cudaMemcpyAsync(c->pinned, c->cg.p, sizeof(gp::CgState), cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(host, c->pinned, sizeof(gp::CgState));
+  return GP_OK;
+}
+
+}  // namespace
+
+namespace gp {
+
+int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
+           int check_every, int* iters_out, double* max_rel) {
+  const int64_t n = c->n_act;
+  *iters_out = 0;
+  *max_rel = 0.0;
+  if (n == 0) return GP_OK;
+  const int G = kp / 4;
+  SpmmFn spmm = spmm_for(G);
+  if (!spmm || kp % 4) return GP_ERR_UNSUPPORTED;
+  GP_CHECK(ensure(c, c->X, (size_t)n * kp * sizeof(float)));
+  GP_CHECK(ensure(c, c->R, (size_t)n * kp * sizeof(float)));
+  GP_CHECK(ensure(c, c->P, (size_t)n * kp * sizeof(float)));
+  GP_CHECK(ensure(c, c->Q, (size_t)n * kp * sizeof(float)));
+  GP_CHECK(ensure(c, c->zbits, (size_t)n * 2 * sizeof(uint32_t)));
+  const int maxb = c->num_sms * 4;
+  GP_CHECK(ensure(c, c->part_a, (size_t)maxb * 4 * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->part_b, (size_t)maxb * 4 * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->hist_alpha, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->hist_beta, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
+  CgState* st = (CgState*)c->cg.p;
+  {
+    unsigned gb = grid_for(n, kThreads, maxb);
+    k_init_f32<<<gb, kThreads, 0, c->stream>>>(n, k, kp, y, (const uint32_t*)c->vals.p, (const double*)c->dinv64.p,
+                                               seed, nv, (float*)c->X.p, (float*)c->R.p, (float*)c->P.p,
+                                               (uint32_t*)c->zbits.p, (double*)c->part_a.p, st, rtol * rtol,
+                                               max_iter);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+  }
+  const unsigned g_spmm = grid_for(n, kWarps, c->num_sms * 4);
+  const int kq = kp / 4;
+  const int ny = kThreads / kq;
+  const unsigned g_upd = grid_for(n, ny, c->num_sms * 4);
+  if (check_every <= 0) check_every = 16;
+  if (check_every > 64) check_every = 64;
+  const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
+  if (timed) GP_CHECK(kernel_events(c));
+  CgState hs;
+  int iter_before = 0;
+  for (int it = 0; it < max_iter; it += check_every) {
+    for (int t = 0; t < check_every; ++t) {
+      if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t], c->stream));
+      spmm<<<g_spmm, kThreads, 0, c->stream>>>(n, k, (const int64_t*)c->row_ptr.p, (const int32_t*)c->col.p,
+                                               (const float*)c->val.p, (const float4*)c->P.p, (float4*)c->Q.p,
+                                               (double*)c->part_a.p, st, (double*)c->hist_alpha.p, m_hist);
+      if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t + 1], c->stream));
+      k_upd_r_f32<<<g_upd, kThreads, 0, c->stream>>>(n, k, kq, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                     (double*)c->part_b.p, st, (double*)c->hist_beta.p, m_hist);
+      k_upd_xp_f32<<<g_upd, kThreads, 0, c->stream>>>(n, kq, (float4*)c->X.p, (const float4*)c->R.p,
+                                                      (float4*)c->P.p, st);
+    }
+    GP_LAUNCH_CHECK();
+    c->launches += 3 * check_every;
+    GP_CHECK(read_state(c, &hs));
+    if (timed) {
+      // launches after convergence return at once: time only the ones that worked
+      const int worked = hs.iter - iter_before;
+      for (int t = 0; t < worked && t < check_every; ++t) c->t_spmm += event_ms(c->kev[2 * t], c->kev[2 * t + 1]);
+      c->n_spmm += worked < check_every ? worked : check_every;
+    }
+    iter_before = hs.iter;
+    if (hs.finished) break;
+  }
+  GP_CHECK(read_state(c, &hs));
+  *iters_out = hs.iter;
+  double mr = 0.0;
+  bool all_done = true;
+  for (int q = 0; q < k; ++q) {
+    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.rr[q] / hs.rr0[q]));
+    all_done = all_done && hs.done[q];
+  }
+  *max_rel = mr;
+  c->bad_col = hs.bad_col;
+  c->bad_iter = hs.iter;
+  if (hs.status != GP_OK) return hs.status;
+  if (!all_done) return GP_ERR_NOT_CONVERGED;
+  return GP_OK;
+}
+
+int cg_run_fp64(gp_ctx* c, int k, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
+                int check_every, int* iters_out, double* max_rel) {
+  const int64_t n = c->n_act;
+  *iters_out = 0;
+  *max_rel = 0.0;
+  if (n == 0) return GP_OK;
+  GP_CHECK(ensure(c, c->X, (size_t)n * k * sizeof(double)));
+  GP_CHECK(ensure(c, c->R, (size_t)n * sizeof(double)));
+  GP_CHECK(ensure(c, c->P, (size_t)n * sizeof(double)));
+  GP_CHECK(ensure(c, c->Q, (size_t)n * sizeof(double)));
+  GP_CHECK(ensure(c, c->zbits, (size_t)n * 2 * sizeof(uint32_t)));
+  const int maxb = c->num_sms * 4;
+  GP_CHECK(ensure(c, c->part_a, (size_t)maxb * 4 * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->part_b, (size_t)maxb * 4 * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->hist_alpha, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->hist_beta, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
+  CgState* st = (CgState*)c->cg.p;
+  if (check_every <= 0) check_every = 16;
+  if (check_every > 64) check_every = 64;
+  const unsigned gb = grid_for(n, kThreads, maxb);
+  const unsigned gw = grid_for(n, kWarps, c->num_sms * 4);
+  int status = GP_OK;
+  double mr = 0.0;
+  int itmax = 0;
+  for (int col = 0; col < k; ++col) {
+    double* X = (double*)c->X.p + (int64_t)col * n;
+    k_init_f64<<<gb, kThreads, 0, c->stream>>>(n, col, nv, y, (const uint32_t*)c->vals.p,
+                                               (const double*)c->dinv64.p, seed, X, (double*)c->R.p,
+                                               (double*)c->P.p, (uint32_t*)c->zbits.p, (double*)c->part_a.p, st,
+                                               rtol * rtol, max_iter);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+    CgState hs;
+    for (int it = 0; it < max_iter; it += check_every) {
+      for (int t = 0; t < check_every; ++t) {
+        k_spmv_f64<<<gw, kThreads, 0, c->stream>>>(n, (const int64_t*)c->row_ptr.p, (const int32_t*)c->col.p,
+                                                   (const double*)c->val.p, (const double*)c->P.p, (double*)c->Q.p,
+                                                   (double*)c->part_a.p, st, col, (double*)c->hist_alpha.p, m_hist);
+        k_upd_r_f64<<<gb, kThreads, 0, c->stream>>>(n, (const double*)c->Q.p, (double*)c->R.p,
+                                                    (double*)c->part_b.p, st, col, (double*)c->hist_beta.p, m_hist);
+        k_upd_xp_f64<<<gb, kThreads, 0, c->stream>>>(n, X, (const double*)c->R.p, (double*)c->P.p, st);
+      }
+      GP_LAUNCH_CHECK();
+      c->launches += 3 * check_every;
+      GP_CHECK(read_state(c, &hs));
+      if (hs.finished) break;
+    }
+    GP_CHECK(read_state(c, &hs));
+    itmax = hs.iter > itmax ? hs.iter : itmax;
+    if (hs.rr0[0] > 0) mr = fmax(mr, sqrt(hs.rr[0] / hs.rr0[0]));
+    if (hs.status != GP_OK && status == GP_OK) status = hs.status;
+    if (!hs.done[0] && status == GP_OK) status = GP_ERR_NOT_CONVERGED;
+  }
+  *iters_out = itmax;
+  *max_rel = mr;
+  return status;
+}
+
+int inactive_terms(gp_ctx* c, const double* y) {
+  AsmScalars* s = (AsmScalars*)c->asm_s.p;
+  const int maxb = c->num_sms * 4;
+  GP_CHECK(ensure(c, c->part_c, (size_t)maxb * 2 * sizeof(double)));
+  if (c->n == 0) {
+    GP_CUDA(cudaMemsetAsync(&s->inact_y2, 0, sizeof(double), c->stream));
+    GP_CUDA(cudaMemsetAsync(&s->n_inactive, 0, sizeof(long long), c->stream));
+    return GP_OK;
+  }
+  k_inactive<<<grid_for(c->n, kThreads, maxb), kThreads, 0, c->stream>>>(c->n, y, (const uint32_t*)c->mask0.p,
+                                                                         (double*)c->part_c.p, s);
+  GP_LAUNCH_CHECK();
+  c->launches += 1;
+  return GP_OK;
+}
+
+int quad_form(gp_ctx* c, const double* y, int kp) {
+  AsmScalars* s = (AsmScalars*)c->asm_s.p;
+  if (c->n_act == 0) {
+    GP_CUDA(cudaMemsetAsync(&s->quad_form, 0, sizeof(double), c->stream));
+    return GP_OK;
+  }
+  const int maxb = c->num_sms * 4;
+  GP_CHECK(ensure(c, c->part_c, (size_t)maxb * 2 * sizeof(double)));
+  const unsigned gb = grid_for(c->n_act, kThreads, maxb);
+  if (c->precision == GP_FP64)
+    k_quad<double><<<gb, kThreads, 0, c->stream>>>(c->n_act, y, (const uint32_t*)c->vals.p,
+                                                   (const double*)c->dinv64.p, (const double*)c->X.p, 1,
+                                                   (double*)c->part_c.p, s);
+  else
+    k_quad<float><<<gb, kThreads, 0, c->stream>>>(c->n_act, y, (const uint32_t*)c->vals.p,
+                                                  (const double*)c->dinv64.p, (const float*)c->X.p, kp,
+                                                  (double*)c->part_c.p, s);
+  GP_LAUNCH_CHECK();
+  c->launches += 1;
+  return GP_OK;
+}
+
+int slq(gp_ctx* c, int nv, int kcols) {
+  (void)kcols;
+  AsmScalars* s = (AsmScalars*)c->asm_s.p;
+  if (c->n_act == 0) {
+    GP_CUDA(cudaMemsetAsync(&s->slq_mean, 0, 2 * sizeof(double), c->stream));
+    return GP_OK;
+  }
+  k_slq<<<1, kMaxProbes, 0, c->stream>>>(nv, c->n_act, (const double*)c->hist_alpha.p,
+                                         (const double*)c->hist_beta.p, (const CgState*)c->cg.p, s);
+  GP_LAUNCH_CHECK();
+  c->launches += 1;
+  return GP_OK;
+}
+
+int alpha_out(gp_ctx* c, const double* y, double* out, int kp) {
+  const int maxb = c->num_sms * 4;
+  if (c->n > 0)
+    k_alpha_inactive<<<grid_for(c->n, kThreads, maxb), kThreads, 0, c->stream>>>(
+        c->n, (const uint32_t*)c->mask0.p, y, 1.0 / c->sigma2, out);
+  if (c->n_act > 0) {
+    const unsigned gb = grid_for(c->n_act, kThreads, maxb);
+    if (c->precision == GP_FP64)
+      k_alpha_active<double><<<gb, kThreads, 0, c->stream>>>(c->n_act, (const uint32_t*)c->vals.p,
+                                                             (const double*)c->dinv64.p, (const double*)c->X.p, 1,
+                                                             out);
+    else
+      k_alpha_active<float><<<gb, kThreads, 0, c->stream>>>(c->n_act, (const uint32_t*)c->vals.p,
+                                                            (const double*)c->dinv64.p, (const float*)c->X.p, kp,
+                                                            out);
+  }
+  GP_LAUNCH_CHECK();
+  c->launches += (c->n > 0) + (c->n_act > 0);
+  return GP_OK;
+}
+
+}  // namespace gp
