@@ -328,7 +328,8 @@ int gp_destroy(gp_ctx* c) {
                         &c->cnt,    &c->row_ptr, &c->col,       &c->val,       &c->X,         &c->R,
                         &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
-                        &c->asm_s,  &c->csr_tmp};
+                        &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
+                        &c->bval};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);

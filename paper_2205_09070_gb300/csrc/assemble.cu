@@ -148,6 +148,27 @@ __device__ inline uint32_t morton(const int* c, const gp::Grid& g) {
   return key;
 }
 
+// Sort key: the cell's Morton code in the high bits (points of a cell stay
+// contiguous and cells follow the Z-curve), then the Morton code of the
+// point's sub-cell (2^subbits per axis) so that consecutive rows inside a
+// cell are also close in space.
+__device__ inline uint32_t sort_key(const double* xi, const int* c, const gp::Grid& g) {
+  uint32_t sub = 0;
+  if (g.subbits > 0) {
+    const int ns = 1 << g.subbits;
+    int sc[gp::kMaxDim] = {0, 0, 0};
+    for (int k = 0; k < g.dim; ++k) {
+      double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h) - (double)c[k];
+      int v = (int)floor(u * ns);
+      sc[k] = v < 0 ? 0 : (v > ns - 1 ? ns - 1 : v);
+    }
+    int pos = 0;
+    for (int t = 0; t < g.subbits; ++t)
+      for (int k = 0; k < g.dim; ++k) sub |= (uint32_t)((sc[k] >> t) & 1) << pos++;
+  }
+  return (morton(c, g) << (g.subbits * g.dim)) | sub;
+}
+
 __global__ void __launch_bounds__(kThreads) k_keys(const double* __restrict__ x, int64_t n,
                                                    const int64_t* __restrict__ pos,
                                                    const uint32_t* __restrict__ mask0, gp::Grid g,
@@ -159,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double* __restrict__ x,
     int c[gp::kMaxDim];
     cell_of(xi, g, c);
     int64_t a = pos[i];
-    keys[a] = morton(c, g);
+    keys[a] = sort_key(xi, c, g);
     vals[a] = (uint32_t)i;
   }
 }
@@ -274,9 +295,10 @@ __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ 
     dinv[p] = (T)di;
     acc += log(D);
     const int64_t lin = (int64_t)c[0] + (int64_t)g.G[0] * ((int64_t)c[1] + (int64_t)g.G[1] * c[2]);
-    const uint32_t kk = skey[p];
-    if (p == 0 || skey[p - 1] != kk) cells[lin].x = (int)p;
-    if (p == n_act - 1 || skey[p + 1] != kk) cells[lin].y = (int)(p + 1);
+    const int sh = g.subbits * g.dim;  // the cell code sits above the sub-cell bits
+    const uint32_t kk = skey[p] >> sh;
+    if (p == 0 || (skey[p - 1] >> sh) != kk) cells[lin].x = (int)p;
+    if (p == n_act - 1 || (skey[p + 1] >> sh) != kk) cells[lin].y = (int)(p + 1);
   }
   __shared__ double sh[kThreads];
   __shared__ bool last;
@@ -482,6 +504,185 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ 8x1 block CSR
+// The FP32 SpMM reads K in CSR of 8x1 blocks: block row b holds the rows
+// 8b..8b+7 (consecutive in Morton / sub-cell order, so close in space); each
+// stored block is one column j with the 8 values K_(8b+r),j (0 where (8b+r, j)
+// is outside the pattern) and an 8-bit mask of the pattern entries.  One
+// column index and one gathered P row then serve up to 8 rows.
+// The support predicate is evaluated exactly as in k_pair (same FP32
+// expression, same FP64 guard band), so the block pattern and the scalar CSR
+// pattern are identical.
+constexpr int kBR = 8;
+constexpr int kBWarps = 4;
+constexpr int kMaxCand = kBR * 27;  // distinct neighbour cells of one block row
+
+template <bool FILL>
+__global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk, const int64_t* __restrict__ brp,
+                                                        int32_t* __restrict__ bcnt, int32_t* __restrict__ bcol,
+                                                        uint8_t* __restrict__ bmask, float* __restrict__ bval) {
+  __shared__ float4 s_rx[kBWarps][kBR];
+  __shared__ int4 s_rc[kBWarps][kBR];
+  __shared__ uint32_t s_rm[kBWarps][kBR];
+  __shared__ float s_rd[kBWarps][kBR];
+  __shared__ int s_start[kBWarps][kMaxCand];
+  __shared__ int s_pre[kBWarps][kMaxCand];
+  __shared__ int4 s_cc[kBWarps][kMaxCand];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float* Fs = (const float*)a.Fs;
+  const float* dinv = (const float*)a.dinv;
+  const int G[3] = {a.G0, a.G1, a.G2};
+  for (int64_t bb = (int64_t)blockIdx.x * kBWarps + w; bb < nblk; bb += (int64_t)gridDim.x * kBWarps) {
+    const int64_t r0 = bb * kBR;
+    const int nr = (int)min((int64_t)kBR, a.n - r0);
+    int4 myc = make_int4(-1, -1, -1, 0);
+    if (lane < nr) {
+      myc = a.cellc[r0 + lane];
+      s_rx[w][lane] = a.xr[r0 + lane];
+      s_rc[w][lane] = myc;
+      s_rm[w][lane] = a.mask[r0 + lane];
+      s_rd[w][lane] = FILL ? dinv[r0 + lane] : 0.f;
+    }
+    // one representative lane per distinct row cell
+    bool rep = lane < nr;
+    for (int q = 0; q < kBR; ++q) {
+      const int ox = __shfl_sync(kFull, myc.x, q), oy = __shfl_sync(kFull, myc.y, q),
+                oz = __shfl_sync(kFull, myc.z, q);
+      if (q < lane && ox == myc.x && oy == myc.y && oz == myc.z) rep = false;
+    }
+    unsigned reps = __ballot_sync(kFull, rep);
+    // neighbour cells of all row cells, non-empty ones once each
+    int L = 0;
+    while (reps) {
+      const int q = __ffs(reps) - 1;
+      reps &= reps - 1u;
+      const int c3[3] = {__shfl_sync(kFull, myc.x, q), __shfl_sync(kFull, myc.y, q), __shfl_sync(kFull, myc.z, q)};
+      bool ok = false;
+      int start = 0, len = 0;
+      int nc[3] = {0, 0, 0};
+      if (lane < a.nstencil) {
+        int t = lane;
+        ok = true;
+        int64_t lin = 0, mult = 1;
+        for (int k = 0; k < a.dim; ++k) {
+          const int o = t % 3 - 1;
+          t /= 3;
+          nc[k] = c3[k] + o;
+          ok = ok && nc[k] >= 0 && nc[k] < G[k];
+          lin += (int64_t)nc[k] * mult;
+          mult *= G[k];
+        }
+        if (ok) {
+          const int2 se = a.cells[lin];
+          start = se.x;
+          len = se.y - se.x;
+          ok = len > 0;
+        }
+        for (int t2 = 0; ok && t2 < L; ++t2)
+          if (s_start[w][t2] == start) ok = false;
+      }
+      const unsigned bal = __ballot_sync(kFull, ok);
+      if (ok) {
+        const int pos = L + __popc(bal & gpd::lanemask_lt());
+        s_start[w][pos] = start;
+        s_pre[w][pos] = len;
+        s_cc[w][pos] = make_int4(nc[0], nc[1], nc[2], 0);
+      }
+      L += __popc(bal);
+      __syncwarp();
+    }
+    // exclusive prefix of the range lengths
+    int run = 0;
+    for (int c0 = 0; c0 < L; c0 += 32) {
+      const int v = c0 + lane < L ? s_pre[w][c0 + lane] : 0;
+      const int inc = warp_incl_scan_int(v);
+      __syncwarp();
+      if (c0 + lane < L) s_pre[w][c0 + lane] = run + inc - v;
+      run += __shfl_sync(kFull, inc, 31);
+      __syncwarp();
+    }
+    const int total = run;
+    int64_t out = FILL ? brp[bb] : 0;
+    int count = 0;
+    for (int base = 0; base < total; base += 32) {
+      const int f = base + lane;
+      uint32_t bits = 0u;
+      int j = 0;
+      float v[kBR];
+#pragma unroll
+      for (int rr = 0; rr < kBR; ++rr) v[rr] = 0.f;
+      if (f < total) {
+        int r = 0;
+        for (int step = 128; step > 0; step >>= 1)
+          if (r + step < L && s_pre[w][r + step] <= f) r += step;
+        j = s_start[w][r] + (f - s_pre[w][r]);
+        const int4 cj = s_cc[w][r];
+        const uint32_t mj = a.mask[j];
+        const float4 xj = a.xr[j];
+        const float dj = FILL ? dinv[j] : 0.f;
+#pragma unroll
+        for (int rr = 0; rr < kBR; ++rr) {
+          if (rr >= nr) break;
+          const uint32_t mi = s_rm[w][rr];
+          if ((mi & mj) == 0u) continue;
+          const int4 ci = s_rc[w][rr];
+          const int ox = cj.x - ci.x, oy = cj.y - ci.y, oz = cj.z - ci.z;
+          if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) continue;
+          const float4 xi = s_rx[w][rr];
+          const int64_t p = r0 + rr;
+          const float dx = (xj.x + (float)ox) - xi.x;
+          const float dy = (xj.y + (float)oy) - xi.y;
+          const float dz = (xj.z + (float)oz) - xi.z;
+          const float r2 = (dx * dx + dy * dy + dz * dz) * a.scale;
+          bool hit;
+          float rho2, s2;
+          if (fabsf(r2 - 1.0f) < a.guard) {
+            const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+            hit = e2 < a.rs2;
+            rho2 = (float)(e2 / a.rs2);
+            s2 = (float)((a.rs2 - e2) / a.rs2);
+          } else {
+            hit = r2 < 1.0f;
+            rho2 = r2;
+            s2 = 1.0f - r2;
+            if (FILL && hit && s2 < 0.1f) {
+              const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+              rho2 = (float)(e2 / a.rs2);
+              s2 = (float)((a.rs2 - e2) / a.rs2);
+            }
+          }
+          if (!hit) continue;
+          bits |= 1u << rr;
+          if (FILL) {
+            float S = 0.f;
+            uint32_t common = mi & mj;
+            while (common) {
+              const int m = __ffs(common) - 1;
+              common &= common - 1u;
+              S += Fs[p * a.n1 + m] * Fs[(int64_t)j * a.n1 + m];
+            }
+            float val = (float)a.AC * gpd::kstat_unit_f(rho2, s2) * S;
+            if (j == p) val += (float)a.sigma2;
+            v[rr] = val * s_rd[w][rr] * dj;
+          }
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, bits != 0u);
+      if (FILL && bits != 0u) {
+        const int64_t q = out + count + __popc(bal & gpd::lanemask_lt());
+        bcol[q] = j;
+        bmask[q] = (uint8_t)bits;
+        float4* dst = (float4*)(bval + q * kBR);
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+      count += __popc(bal);
+    }
+    if (!FILL && lane == 0) bcnt[bb] = count;
+    __syncwarp();
+  }
+}
+
 // Unscaled values of the stored block (for gp_get_csr): K = D^1/2 Khat D^1/2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_unscale(int64_t n, const int64_t* __restrict__ rp,
@@ -551,6 +752,8 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     g.ncells *= g.G[k];
   }
   if (g.keybits > 32) return GP_ERR_UNSUPPORTED;
+  g.subbits = 0;
+  while (g.subbits < 2 && g.keybits + (g.subbits + 1) * dim <= 32) ++g.subbits;
   c->grid = g;
 
   // --- bump parameters with FP32 pre-filter margins
@@ -623,7 +826,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     GP_LAUNCH_CHECK();
     c->launches += 1;
   }
-  const int passes = (g.keybits + 7) / 8;
+  const int passes = (g.keybits + g.subbits * dim + 7) / 8;
   const int ntiles = (int)((n_act + kRsTile - 1) / kRsTile);
   GP_CHECK(gp::ensure(c, c->hist, (size_t)256 * ntiles * sizeof(int32_t)));
   GP_CHECK(gp::ensure(c, c->hist_scan, (size_t)(256 * ntiles + 1) * sizeof(int64_t)));
@@ -716,6 +919,32 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     GP_CUDA(cudaEventRecord(c->kev[129], c->stream));
     GP_CUDA(cudaEventSynchronize(c->kev[129]));
     c->t_fill += gp::event_ms(c->kev[128], c->kev[129]);
+  }
+  if (sizeof(T) == 4) {
+    // 8x1 block CSR for the FP32 SpMM: count, scan, fill
+    const int64_t nblk = (n_act + kBR - 1) / kBR;
+    c->nblk = nblk;
+    GP_CHECK(gp::ensure(c, c->bcnt, (size_t)nblk * sizeof(int32_t)));
+    GP_CHECK(gp::ensure(c, c->brp, (size_t)(nblk + 1) * sizeof(int64_t)));
+    const unsigned gbk = grid_for(nblk, kBWarps, c->num_sms * 16);
+    k_bpair<false><<<gbk, kBWarps * 32, 0, c->stream>>>(pa, nblk, nullptr, (int32_t*)c->bcnt.p, nullptr, nullptr,
+                                                         nullptr);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+    GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->bcnt.p, (int64_t*)c->brp.p, nblk));
+    GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->brp.p + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            c->stream));
+    GP_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t nbe = *(int64_t*)c->pinned;
+    c->nbent = nbe;
+    GP_CHECK(gp::ensure(c, c->bcol, (size_t)nbe * sizeof(int32_t)));
+    GP_CHECK(gp::ensure(c, c->bmask, (size_t)nbe));
+    GP_CHECK(gp::ensure(c, c->bval, (size_t)nbe * kBR * sizeof(float)));
+    k_bpair<true><<<gbk, kBWarps * 32, 0, c->stream>>>(pa, nblk, (const int64_t*)c->brp.p, nullptr,
+                                                        (int32_t*)c->bcol.p, (uint8_t*)c->bmask.p,
+                                                        (float*)c->bval.p);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
   }
   return GP_OK;
 }

@@ -39,7 +39,8 @@ struct Grid {
   int G[kMaxDim];    // cells per dimension
   int bits[kMaxDim]; // Morton bits per dimension
   int dim;
-  int keybits;
+  int keybits;       // bits of the cell Morton code
+  int subbits;       // bits per axis of the sub-cell order inside a cell
   int64_t ncells;
 };
 
@@ -61,6 +62,11 @@ struct CgState {
   unsigned ticket_c;
   int max_iter;
   double tol2;             // cg_rtol^2
+  // FP32 batched path: iteration-parity copies, so that one block of a
+  // kernel can publish iteration t+1 while the others still read iteration t
+  double rrp[2][kMaxCols];
+  int donep[2][kMaxCols];
+  int fin[2];
 };
 
 // Reductions produced by assembly / likelihood kernels.
@@ -112,6 +118,9 @@ struct gp_ctx {
   gp::DevBuf cells;
   gp::DevBuf perm, skey, cellc, xr, xs, Fs, smask, dinv, dinv64;
   gp::DevBuf cnt, row_ptr, col, val;
+  // 8x1 block CSR of the FP32 path (rows 8b..8b+7 per block row)
+  gp::DevBuf bcnt, brp, bcol, bmask, bval;
+  int64_t nblk = 0, nbent = 0;
   gp::DevBuf X, R, P, Q, zbits;
   gp::DevBuf part_a, part_b, part_c, hist_alpha, hist_beta;
   gp::DevBuf g, grad_part, grad_bump;
@@ -153,7 +162,7 @@ int scan_i32_to_i64(gp_ctx* c, const int32_t* in, int64_t* out, int64_t n);
 int assemble(gp_ctx* c, const double* x_dev, int64_t n, const double* h, int precision);
 int csr_unscaled(gp_ctx* c, double* val_out_dev);
 
-// solve.cu
+// solve.cu (cg_run: FP32 batched CG on the 8x1 block CSR)
 int cg_run(gp_ctx* c, int k, int kp, const double* y_dev, int n_probes, uint64_t seed,
            int lanczos_steps, int max_iter, double rtol, int check_every,
            int* iters_out, double* max_rel_resid);

@@ -4,14 +4,17 @@
 // by its step lengths alpha_t and direction updates beta_t).
 //
 // FP32_MIXED: one CG over the block [yhat, z_1 .. z_nv] (row-major, kp floats
-// per row).  Per iteration three kernels:
-//   A  Q = Khat P (SpMM) with p_c^T q_c per column in FP64 -> alpha_c
-//   B  R -= alpha Q, |r_c|^2 in FP64                        -> beta_c, convergence
-//   C  X += alpha P_old, P = R + beta P_old
-// The scalars of each kernel are finished by its last block (threadfence +
-// ticket), so the per-column reductions are deterministic and no kernel waits
-// on another.
-// FP64: one single-RHS CG per column, all in FP64 (the plain comparison path).
+// per row).  Per iteration t three kernels:
+//   A  Q = Khat P on the 8x1 block CSR; per-block partial sums of p_c^T q_c
+//   B  every block reduces A's partials (fixed order) -> alpha_c;
+//      R -= alpha Q; per-block partial sums of |r_c|^2
+//   C  every block reduces A's and B's partials -> alpha_c, beta_c;
+//      X += alpha P_old, P = R + beta P_old; block 0 publishes the
+//      iteration-(t+1) residual norms, convergence flags and the stop flag
+// Scalars of iteration t live in parity slot t&1, so no kernel waits on
+// another and no block runs a serial tail; all reductions are deterministic.
+// FP64: one single-RHS CG per column, all in FP64 (the plain comparison path),
+// with its scalars finished by the last block of each kernel.
 #include <math.h>
 
 #include "gp_internal.cuh"
@@ -23,15 +26,24 @@ constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sum partials part[b * stride + t] over blocks b < nblk for t < width with all
-// threads of the block, in a fixed order; result in out[t] (shared).
+// threads of the block, in a fixed order; result in out[t] (shared).  Four
+// independent accumulators keep several L2 loads in flight per thread.
 __device__ void block_sum_partials(const double* part, int nblk, int width, int stride, double* out,
-                                   double* scratch /* >= kThreads doubles */) {
-  const int groups = kThreads / width;  // width <= kMaxCols < kThreads
+                                   double* scratch /* >= blockDim.x doubles */) {
+  const int groups = blockDim.x / width;  // width <= kMaxCols < blockDim.x
   const int t = threadIdx.x % width, grp = threadIdx.x / width;
-  double acc = 0.0;
-  if (grp < groups)
-    for (int b = grp; b < nblk; b += groups) acc += __ldcg(part + (int64_t)b * stride + t);
-  scratch[threadIdx.x] = acc;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (grp < groups) {
+    int b = grp;
+    for (; b + 3 * groups < nblk; b += 4 * groups) {
+      a0 += __ldcg(part + (int64_t)b * stride + t);
+      a1 += __ldcg(part + (int64_t)(b + groups) * stride + t);
+      a2 += __ldcg(part + (int64_t)(b + 2 * groups) * stride + t);
+      a3 += __ldcg(part + (int64_t)(b + 3 * groups) * stride + t);
+    }
+    for (; b < nblk; b += groups) a0 += __ldcg(part + (int64_t)b * stride + t);
+  }
+  scratch[threadIdx.x] = (a0 + a1) + (a2 + a3);
   __syncthreads();
   if (threadIdx.x < width) {
     double s = 0.0;
@@ -119,24 +131,24 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
     const float yh = (float)(y[i] * dinv64[p]);
     acc += (double)yh * (double)yh;
     uint32_t zb[2] = {0u, 0u};
-    float* xr = X + p * kp;
-    float* rr = R + p * kp;
-    float* pr = P + p * kp;
-    xr[0] = 0.f;
-    rr[0] = yh;
-    pr[0] = yh;
+    float* xrow = X + p * kp;
+    float* rrow = R + p * kp;
+    float* prow = P + p * kp;
+    xrow[0] = 0.f;
+    rrow[0] = yh;
+    prow[0] = yh;
     for (int l = 0; l < nv; ++l) {
       const unsigned b = gpd::probe_bit(seed, l, (long long)i);
       zb[l >> 5] |= b << (l & 31);
       const float z = b ? -1.f : 1.f;
-      xr[1 + l] = 0.f;
-      rr[1 + l] = z;
-      pr[1 + l] = z;
+      xrow[1 + l] = 0.f;
+      rrow[1 + l] = z;
+      prow[1 + l] = z;
     }
     for (int c = 1 + nv; c < kp; ++c) {
-      xr[c] = 0.f;
-      rr[c] = 0.f;
-      pr[c] = 0.f;
+      xrow[c] = 0.f;
+      rrow[c] = 0.f;
+      prow[c] = 0.f;
     }
     zbits[2 * p] = zb[0];
     zbits[2 * p + 1] = zb[1];
@@ -148,7 +160,10 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sh[0];
+    __threadfence();
+  }
   if (last_block(&st->ticket_c)) {
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -160,72 +175,191 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
       st->tol2 = tol2;
       bool any = false;
       for (int c = 0; c < gp::kMaxCols; ++c) {
-        double r0 = c == 0 ? t : (c < k ? (double)n : 0.0);
+        const double r0 = c == 0 ? t : (c < k ? (double)n : 0.0);
         st->rr0[c] = r0;
-        st->rr[c] = r0;
-        st->alpha[c] = 0.0;
-        st->beta[c] = 0.0;
-        st->done[c] = !(r0 > 0.0);
+        st->rrp[0][c] = r0;
+        st->rrp[1][c] = r0;
+        st->donep[0][c] = !(r0 > 0.0);
+        st->donep[1][c] = st->donep[0][c];
         st->steps[c] = 0;
-        any = any || (c < k && !st->done[c]);
+        any = any || (c < k && !st->donep[0][c]);
       }
-      st->pending = !any;
+      st->fin[0] = !any;
+      st->fin[1] = !any;
       st->finished = !any;
     }
   }
 }
 
-// A: Q = Khat P with per-column p^T q.  One warp per row; the warp's lanes
-// form NG = 32/G groups of G lanes, a group takes every NG-th nonzero of the
-// row and each of its lanes owns one float4 of the kp = 4G columns.
+// A: Q = Khat P on the 8x1 block CSR.  Each warp owns a contiguous run of
+// block rows holding an equal share of the stored blocks and streams them in
+// chunks of 32 blocks through a double-buffered shared-memory stage: while the
+// warp computes chunk c, cp.async copies the P rows (kp floats) and the 8
+// values of chunk c+1 into the other buffer, and the column indices of chunk
+// c+2 are already being loaded.  Compute: the warp's lanes form NG = 32/G
+// groups of G lanes (one float4 of the kp = 4G columns per lane); a group
+// takes every NG-th block of the chunk and applies its P row to the 8 rows
+// of the block row (8 float4 accumulators per lane).
+// Smallest block row b in [0, nblk] whose first stored block is >= target
+// (brp ascending, brp[nblk] = total).  Every block row then belongs to
+// exactly one warp's share.
+__device__ inline int64_t first_row_at_or_after(const int64_t* __restrict__ brp, int64_t nblk, int64_t target) {
+  int64_t lo = 0, hi = nblk;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(brp + mid) < target) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kSpmmThreads = 128;
+constexpr int kSpmmWarps = kSpmmThreads / 32;
+constexpr int kBR = 8;
+constexpr int kChunk = 32;
+
+__device__ inline void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Position of a chunk in the warp's stream: block row bb, first block base.
+struct ChunkPos {
+  int64_t bb, base;
+};
+
+__device__ inline ChunkPos next_chunk(ChunkPos c, const int64_t* __restrict__ brp) {
+  const int64_t e = __ldg(brp + c.bb + 1);
+  if (c.base + kChunk < e) return {c.bb, c.base + kChunk};
+  return {c.bb + 1, e};
+}
+
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_spmm_f32(int64_t n, int k, const int64_t* __restrict__ rp,
-                                                       const int32_t* __restrict__ col,
-                                                       const float* __restrict__ val, const float4* __restrict__ P,
-                                                       float4* __restrict__ Q, double* __restrict__ part,
-                                                       gp::CgState* st, double* hist_alpha, int m_hist) {
-  if (st->finished) return;
+__global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t nblk, int it,
+                                                            const int64_t* __restrict__ brp,
+                                                            const int32_t* __restrict__ bcol,
+                                                            const float4* __restrict__ bval,
+                                                            const float4* __restrict__ P, float4* __restrict__ Q,
+                                                            double* __restrict__ part, const gp::CgState* st) {
+  if (st->fin[it & 1]) return;
   constexpr int NG = 32 / G;
   constexpr int KP = 4 * G;
-  __shared__ double sh[kWarps][KP];
-  __shared__ double scratch[kThreads];
-  __shared__ double tot[KP];
+  constexpr int kStage = kChunk * (KP + kBR);  // floats per stage buffer
+  extern __shared__ float4 smem_f4[];
+  float* stage = (float*)smem_f4 + (size_t)(threadIdx.x >> 5) * 2 * kStage;
+  __shared__ double sh[kSpmmWarps][KP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane - grp * G;
   const bool act = grp < NG;
   double pq0 = 0, pq1 = 0, pq2 = 0, pq3 = 0;
-  for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < n; p += (int64_t)gridDim.x * kWarps) {
-    const int64_t s = rp[p], e = rp[p + 1];
-    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (act) {
-      for (int64_t idx = s + grp; idx < e; idx += NG) {
-        const int j = __ldg(col + idx);
-        const float v = __ldg(val + idx);
-        const float4 pj = __ldg(P + (int64_t)j * G + gl);
-        q.x = fmaf(v, pj.x, q.x);
-        q.y = fmaf(v, pj.y, q.y);
-        q.z = fmaf(v, pj.z, q.z);
-        q.w = fmaf(v, pj.w, q.w);
-      }
-    }
-    // group 0 adds the partial sums of groups 1..NG-1 (each read unmodified)
-    const float4 q0 = q;
+  // Work split by stored blocks, not by block rows (cluster cores hold many
+  // times more blocks per row than the background).
+  const int64_t nent = brp[nblk];
+  const int64_t nw = (int64_t)gridDim.x * kSpmmWarps;
+  const int64_t wid = (int64_t)blockIdx.x * kSpmmWarps + w;
+  const int64_t b0 = first_row_at_or_after(brp, nblk, nent * wid / nw);
+  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (wid + 1) / nw);
+  if (b0 < b1) {
+    const int64_t e_end = __ldg(brp + b1);
+    // stage a chunk: lane l copies block (base + l): its P row and its 8 values
+    auto issue = [&](ChunkPos c, int jl, int buf) {
+      if (c.bb < b1) {
+        const int64_t e = __ldg(brp + c.bb + 1);
+        const int cnt = (int)min((int64_t)kChunk, e - c.base);
+        if (lane < cnt) {
+          float* dp = stage + buf * kStage + lane * KP;
+          const float4* sp = P + (int64_t)jl * G;
 #pragma unroll
-    for (int g2 = 1; g2 < NG; ++g2) {
-      const int src = gl + g2 * G;
-      q.x += __shfl_sync(kFull, q0.x, src);
-      q.y += __shfl_sync(kFull, q0.y, src);
-      q.z += __shfl_sync(kFull, q0.z, src);
-      q.w += __shfl_sync(kFull, q0.w, src);
+          for (int q = 0; q < G; ++q) cp_async16(dp + 4 * q, sp + q);
+          float* dv = stage + buf * kStage + kChunk * KP + lane * kBR;
+          cp_async16(dv, bval + 2 * (c.base + lane));
+          cp_async16(dv + 4, bval + 2 * (c.base + lane) + 1);
+        }
+      }
+      cp_async_commit();
+    };
+    auto col_of = [&](ChunkPos c) -> int {
+      if (c.bb >= b1) return 0;
+      const int64_t idx = c.base + lane;
+      return idx < min(e_end, __ldg(brp + c.bb + 1)) ? __ldg(bcol + idx) : 0;
+    };
+    ChunkPos cur{b0, __ldg(brp + b0)};
+    ChunkPos nx1 = next_chunk(cur, brp);
+    issue(cur, col_of(cur), 0);
+    int j1 = col_of(nx1);
+    float4 acc[kBR];
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int buf = 0;
+    while (cur.bb < b1) {
+      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp) : nx1;
+      issue(nx1, j1, buf ^ 1);            // copies of chunk c+1 in flight
+      const int j2 = col_of(nx2);          // indices of chunk c+2 in flight
+      cp_async_wait<1>();                  // chunk c has landed
+      __syncwarp();
+      const int64_t e = __ldg(brp + cur.bb + 1);
+      const int cnt = (int)min((int64_t)kChunk, e - cur.base);
+      const float* sp = stage + buf * kStage;
+      const float* sv = sp + kChunk * KP;
+      constexpr int kSteps = (kChunk + NG - 1) / NG;
+#pragma unroll 2
+      for (int t = 0; t < kSteps; ++t) {
+        const int src = t * NG + grp;
+        if (act && src < cnt) {
+          const float4 pj = *(const float4*)(sp + src * KP + 4 * gl);
+          const float4 v0 = *(const float4*)(sv + src * kBR);
+          const float4 v1 = *(const float4*)(sv + src * kBR + 4);
+          const float vv[kBR] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) {
+            acc[r].x = fmaf(vv[r], pj.x, acc[r].x);
+            acc[r].y = fmaf(vv[r], pj.y, acc[r].y);
+            acc[r].z = fmaf(vv[r], pj.z, acc[r].z);
+            acc[r].w = fmaf(vv[r], pj.w, acc[r].w);
+          }
+        }
+      }
+      __syncwarp();  // buffer `buf` may be refilled from the next iteration on
+      if (cur.base + kChunk >= e) {
+        // last chunk of block row cur.bb: group 0 adds the other groups' sums
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) {
+          const float4 q0 = acc[r];
+#pragma unroll
+          for (int g2 = 1; g2 < NG; ++g2) {
+            const int src = gl + g2 * G;
+            acc[r].x += __shfl_sync(kFull, q0.x, src);
+            acc[r].y += __shfl_sync(kFull, q0.y, src);
+            acc[r].z += __shfl_sync(kFull, q0.z, src);
+            acc[r].w += __shfl_sync(kFull, q0.w, src);
+          }
+        }
+        if (grp == 0) {
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) {
+            const int64_t row = cur.bb * kBR + r;
+            if (row < n) {
+              Q[row * G + gl] = acc[r];
+              const float4 pp = __ldg(P + row * G + gl);
+              pq0 += (double)pp.x * acc[r].x;
+              pq1 += (double)pp.y * acc[r].y;
+              pq2 += (double)pp.z * acc[r].z;
+              pq3 += (double)pp.w * acc[r].w;
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kBR; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      cur = nx1;
+      nx1 = nx2;
+      j1 = j2;
+      buf ^= 1;
     }
-    if (grp == 0) {
-      Q[p * G + gl] = q;
-      const float4 pp = __ldg(P + p * G + gl);
-      pq0 += (double)pp.x * q.x;
-      pq1 += (double)pp.y * q.y;
-      pq2 += (double)pp.z * q.z;
-      pq3 += (double)pp.w * q.w;
-    }
+    cp_async_wait<0>();
   }
   if (grp == 0) {
     sh[w][4 * gl + 0] = pq0;
@@ -236,28 +370,60 @@ __global__ void __launch_bounds__(kThreads) k_spmm_f32(int64_t n, int k, const i
   __syncthreads();
   if (threadIdx.x < KP) {
     double t = 0.0;
-    for (int ww = 0; ww < kWarps; ++ww) t += sh[ww][threadIdx.x];
+    for (int ww = 0; ww < kSpmmWarps; ++ww) t += sh[ww][threadIdx.x];
     part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
-    __threadfence();
-  }
-  if (last_block(&st->ticket_a)) {
-    block_sum_partials(part, gridDim.x, KP, KP, tot, scratch);
-    finish_alpha(st, tot, k, 0, hist_alpha, m_hist);
   }
 }
 
-// B: R -= alpha Q and |r_c|^2.  Block = (KQ float4 columns) x (rows).
-__global__ void k_upd_r_f32(int64_t n, int k, int kq, const float4* __restrict__ Q, float4* __restrict__ R,
-                            double* __restrict__ part, gp::CgState* st, double* hist_beta, int m_hist) {
-  if (st->finished) return;
-  __shared__ double scratch[kThreads];
-  __shared__ double red[kThreads * 4];
-  __shared__ double tot[gp::kMaxCols];
+constexpr int kUpdThreads = 1024;
+
+// alpha_c of iteration it from the SpMM partials (every block, same order).
+__device__ void alpha_from_partials(const double* part_pq, int npq, int k, int kp, int it, const gp::CgState* st,
+                                    double* alpha /* shared, kp */, double* pq /* shared, kp */, double* scratch,
+                                    int* bad) {
+  block_sum_partials(part_pq, npq, kp, kp, pq, scratch);
+  if (threadIdx.x < kp) {
+    const int c = threadIdx.x;
+    double a = 0.0;
+    bad[c] = 0;
+    if (c < k && !st->donep[it & 1][c]) {
+      const double d = pq[c];
+      if (!(d > 0.0) || !isfinite(d)) bad[c] = 1;
+      else a = st->rrp[it & 1][c] / d;
+    }
+    alpha[c] = a;
+  }
+  __syncthreads();
+}
+
+// B: R -= alpha Q, per-block |r_c|^2.  Block = (kq float4 columns) x rows.
+__global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int k, int kq, int it,
+                                                           const float4* __restrict__ Q, float4* __restrict__ R,
+                                                           const double* __restrict__ part_pq, int npq,
+                                                           double* __restrict__ part_rr, gp::CgState* st,
+                                                           double* hist_alpha, int m_hist) {
+  if (st->fin[it & 1]) return;
+  __shared__ double scratch[kUpdThreads];
+  __shared__ double red[kUpdThreads * 4];
+  __shared__ double alpha[gp::kMaxCols], pq[gp::kMaxCols];
+  __shared__ int bad[gp::kMaxCols];
+  const int kp = 4 * kq;
+  alpha_from_partials(part_pq, npq, k, kp, it, st, alpha, pq, scratch, bad);
+  if (blockIdx.x == 0 && threadIdx.x < k) {
+    const int c = threadIdx.x;
+    if (bad[c]) {
+      st->status = GP_ERR_NOT_SPD;
+      st->bad_col = c;
+    } else if (!st->donep[it & 1][c] && it < m_hist) {
+      hist_alpha[it * gp::kMaxCols + c] = alpha[c];
+      st->steps[c] = it + 1;
+    }
+  }
   const int tx = threadIdx.x % kq, ty = threadIdx.x / kq, ny = blockDim.x / kq;
   const bool act = ty < ny;
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (act) a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1], (float)st->alpha[4 * tx + 2],
-                           (float)st->alpha[4 * tx + 3]);
+  if (act) a = make_float4((float)alpha[4 * tx], (float)alpha[4 * tx + 1], (float)alpha[4 * tx + 2],
+                           (float)alpha[4 * tx + 3]);
   double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
   if (act) {
     for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += (int64_t)gridDim.x * ny) {
@@ -279,30 +445,69 @@ __global__ void k_upd_r_f32(int64_t n, int k, int kq, const float4* __restrict__
   red[threadIdx.x * 4 + 2] = r2;
   red[threadIdx.x * 4 + 3] = r3;
   __syncthreads();
-  const int kp = 4 * kq;
   if (threadIdx.x < kp) {
     const int cx = threadIdx.x / 4, cc = threadIdx.x % 4;
     double t = 0.0;
     for (int yy = 0; yy < ny; ++yy) t += red[(yy * kq + cx) * 4 + cc];
-    part[(int64_t)blockIdx.x * kp + threadIdx.x] = t;
-    __threadfence();
-  }
-  if (last_block(&st->ticket_b)) {
-    block_sum_partials(part, gridDim.x, kp, kp, tot, scratch);
-    finish_beta(st, tot, k, 0, hist_beta, m_hist);
+    part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = t;
   }
 }
 
-// C: X += alpha P_old, P = R + beta P_old.
-__global__ void k_upd_xp_f32(int64_t n, int kq, float4* __restrict__ X, const float4* __restrict__ R,
-                             float4* __restrict__ P, gp::CgState* st) {
-  if (st->finished) return;
+// C: X += alpha P_old, P = R + beta P_old; block 0 publishes iteration it+1.
+__global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int k, int kq, int it,
+                                                            float4* __restrict__ X, const float4* __restrict__ R,
+                                                            float4* __restrict__ P,
+                                                            const double* __restrict__ part_pq, int npq,
+                                                            const double* __restrict__ part_rr, int nrr,
+                                                            gp::CgState* st, double* hist_beta, int m_hist) {
+  const int cur = it & 1, nxt = (it + 1) & 1;
+  if (st->fin[cur]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->fin[nxt] = 1;
+    return;
+  }
+  __shared__ double scratch[kUpdThreads];
+  __shared__ double alpha[gp::kMaxCols], pq[gp::kMaxCols], rrn[gp::kMaxCols], beta[gp::kMaxCols];
+  __shared__ int bad[gp::kMaxCols];
+  __shared__ int any_running;
+  const int kp = 4 * kq;
+  alpha_from_partials(part_pq, npq, k, kp, it, st, alpha, pq, scratch, bad);
+  block_sum_partials(part_rr, nrr, kp, kp, rrn, scratch);
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  if (threadIdx.x < kp) {
+    const int c = threadIdx.x;
+    double b = 0.0;
+    const bool was_done = c >= k || st->donep[cur][c];
+    if (!was_done) b = rrn[c] / st->rrp[cur][c];
+    beta[c] = b;
+    if (blockIdx.x == 0) {
+      bool done = was_done;
+      if (!was_done) {
+        if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
+        done = rrn[c] <= st->tol2 * st->rr0[c];
+        if (!isfinite(rrn[c])) {
+          st->status = GP_ERR_NOT_SPD;
+          st->bad_col = c;
+        }
+      }
+      st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn[c];
+      st->donep[nxt][c] = done;
+      if (c < k && !done) atomicOr(&any_running, 1);
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->iter = it + 1;
+    const int f = !any_running || st->status != GP_OK || it + 1 >= st->max_iter;
+    st->fin[nxt] = f;
+    st->finished = f;
+  }
   const int tx = threadIdx.x % kq, ty = threadIdx.x / kq, ny = blockDim.x / kq;
   if (ty < ny) {
-    const float4 a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1],
-                                 (float)st->alpha[4 * tx + 2], (float)st->alpha[4 * tx + 3]);
-    const float4 b = make_float4((float)st->beta[4 * tx], (float)st->beta[4 * tx + 1], (float)st->beta[4 * tx + 2],
-                                 (float)st->beta[4 * tx + 3]);
+    const float4 a = make_float4((float)alpha[4 * tx], (float)alpha[4 * tx + 1], (float)alpha[4 * tx + 2],
+                                 (float)alpha[4 * tx + 3]);
+    const float4 b = make_float4((float)beta[4 * tx], (float)beta[4 * tx + 1], (float)beta[4 * tx + 2],
+                                 (float)beta[4 * tx + 3]);
     for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += (int64_t)gridDim.x * ny) {
       const int64_t o = p * kq + tx;
       const float4 po = P[o];
@@ -315,9 +520,6 @@ __global__ void k_upd_xp_f32(int64_t n, int kq, float4* __restrict__ X, const fl
       X[o] = x;
       P[o] = make_float4(fmaf(b.x, po.x, r.x), fmaf(b.y, po.y, r.y), fmaf(b.z, po.z, r.z), fmaf(b.w, po.w, r.w));
     }
-  }
-  if (last_block(&st->ticket_c)) {
-    if (threadIdx.x == 0) st->finished = st->pending;
   }
 }
 
@@ -649,28 +851,28 @@ unsigned grid_for(int64_t items, int per_block, int max_blocks) {
   return (unsigned)g;
 }
 
-typedef void (*SpmmFn)(int64_t, int, const int64_t*, const int32_t*, const float*, const float4*, float4*, double*,
-                       gp::CgState*, double*, int);
+typedef void (*SpmmFn)(int64_t, int64_t, int, const int64_t*, const int32_t*, const float4*, const float4*,
+                       float4*, double*, const gp::CgState*);
 
 SpmmFn spmm_for(int G) {
   switch (G) {
-    case 1: return k_spmm_f32<1>;
-    case 2: return k_spmm_f32<2>;
-    case 3: return k_spmm_f32<3>;
-    case 4: return k_spmm_f32<4>;
-    case 5: return k_spmm_f32<5>;
-    case 6: return k_spmm_f32<6>;
-    case 7: return k_spmm_f32<7>;
-    case 8: return k_spmm_f32<8>;
-    case 9: return k_spmm_f32<9>;
-    case 10: return k_spmm_f32<10>;
-    case 11: return k_spmm_f32<11>;
-    case 12: return k_spmm_f32<12>;
-    case 13: return k_spmm_f32<13>;
-    case 14: return k_spmm_f32<14>;
-    case 15: return k_spmm_f32<15>;
-    case 16: return k_spmm_f32<16>;
-    case 17: return k_spmm_f32<17>;
+    case 1: return k_bspmm_f32<1>;
+    case 2: return k_bspmm_f32<2>;
+    case 3: return k_bspmm_f32<3>;
+    case 4: return k_bspmm_f32<4>;
+    case 5: return k_bspmm_f32<5>;
+    case 6: return k_bspmm_f32<6>;
+    case 7: return k_bspmm_f32<7>;
+    case 8: return k_bspmm_f32<8>;
+    case 9: return k_bspmm_f32<9>;
+    case 10: return k_bspmm_f32<10>;
+    case 11: return k_bspmm_f32<11>;
+    case 12: return k_bspmm_f32<12>;
+    case 13: return k_bspmm_f32<13>;
+    case 14: return k_bspmm_f32<14>;
+    case 15: return k_bspmm_f32<15>;
+    case 16: return k_bspmm_f32<16>;
+    case 17: return k_bspmm_f32<17>;
     default: return nullptr;
   }
 }
@@ -716,27 +918,37 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     GP_LAUNCH_CHECK();
     c->launches += 1;
   }
-  const unsigned g_spmm = grid_for(n, kWarps, c->num_sms * 4);
+  const int64_t nblk = c->nblk;
+  const size_t spmm_smem = (size_t)kSpmmWarps * 2 * kChunk * (kp + kBR) * sizeof(float);
+  GP_CUDA(cudaFuncSetAttribute(spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmm_smem));
+  int spmm_per_sm = 0;
+  GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spmm_per_sm, spmm, kSpmmThreads, spmm_smem));
+  if (spmm_per_sm < 1) spmm_per_sm = 1;
+  const unsigned g_spmm = grid_for(nblk, kSpmmWarps, c->num_sms * spmm_per_sm);
   const int kq = kp / 4;
-  const int ny = kThreads / kq;
-  const unsigned g_upd = grid_for(n, ny, c->num_sms * 4);
+  const int ny = kUpdThreads / kq;
+  const unsigned g_upd = grid_for(n, ny, c->num_sms);
   if (check_every <= 0) check_every = 16;
   if (check_every > 64) check_every = 64;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
   if (timed) GP_CHECK(kernel_events(c));
   CgState hs;
   int iter_before = 0;
-  for (int it = 0; it < max_iter; it += check_every) {
+  for (int it0 = 0; it0 < max_iter; it0 += check_every) {
     for (int t = 0; t < check_every; ++t) {
+      const int it = it0 + t;
       if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t], c->stream));
-      spmm<<<g_spmm, kThreads, 0, c->stream>>>(n, k, (const int64_t*)c->row_ptr.p, (const int32_t*)c->col.p,
-                                               (const float*)c->val.p, (const float4*)c->P.p, (float4*)c->Q.p,
-                                               (double*)c->part_a.p, st, (double*)c->hist_alpha.p, m_hist);
+      spmm<<<g_spmm, kSpmmThreads, spmm_smem, c->stream>>>(n, nblk, it, (const int64_t*)c->brp.p, (const int32_t*)c->bcol.p,
+                                                   (const float4*)c->bval.p, (const float4*)c->P.p,
+                                                   (float4*)c->Q.p, (double*)c->part_a.p, st);
       if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t + 1], c->stream));
-      k_upd_r_f32<<<g_upd, kThreads, 0, c->stream>>>(n, k, kq, (const float4*)c->Q.p, (float4*)c->R.p,
-                                                     (double*)c->part_b.p, st, (double*)c->hist_beta.p, m_hist);
-      k_upd_xp_f32<<<g_upd, kThreads, 0, c->stream>>>(n, kq, (float4*)c->X.p, (const float4*)c->R.p,
-                                                      (float4*)c->P.p, st);
+      k_upd_r_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, k, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                        (const double*)c->part_a.p, (int)g_spmm,
+                                                        (double*)c->part_b.p, st, (double*)c->hist_alpha.p, m_hist);
+      k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, k, kq, it, (float4*)c->X.p, (const float4*)c->R.p,
+                                                         (float4*)c->P.p, (const double*)c->part_a.p, (int)g_spmm,
+                                                         (const double*)c->part_b.p, (int)g_upd, st,
+                                                         (double*)c->hist_beta.p, m_hist);
     }
     GP_LAUNCH_CHECK();
     c->launches += 3 * check_every;
@@ -754,9 +966,10 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   *iters_out = hs.iter;
   double mr = 0.0;
   bool all_done = true;
+  const int par = hs.iter & 1;
   for (int q = 0; q < k; ++q) {
-    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.rr[q] / hs.rr0[q]));
-    all_done = all_done && hs.done[q];
+    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.rrp[par][q] / hs.rr0[q]));
+    all_done = all_done && hs.donep[par][q];
   }
   *max_rel = mr;
   c->bad_col = hs.bad_col;
