@@ -264,19 +264,25 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (wid + 1) / nw);
   if (b0 < b1) {
     const int64_t e_end = __ldg(brp + b1);
-    // stage a chunk: lane l copies block (base + l): its P row and its 8 values
+    // stage a chunk: consecutive lanes copy consecutive 16-byte pieces of the
+    // same P row (G pieces per row, so one copy instruction covers about 32/G
+    // rows), then the chunk's block values (2 float4 each, contiguous)
     auto issue = [&](ChunkPos c, int jl, int buf) {
       if (c.bb < b1) {
         const int64_t e = __ldg(brp + c.bb + 1);
         const int cnt = (int)min((int64_t)kChunk, e - c.base);
-        if (lane < cnt) {
-          float* dp = stage + buf * kStage + lane * KP;
-          const float4* sp = P + (int64_t)jl * G;
+        float* dst = stage + buf * kStage;
 #pragma unroll
-          for (int q = 0; q < G; ++q) cp_async16(dp + 4 * q, sp + q);
-          float* dv = stage + buf * kStage + kChunk * KP + lane * kBR;
-          cp_async16(dv, bval + 2 * (c.base + lane));
-          cp_async16(dv + 4, bval + 2 * (c.base + lane) + 1);
+        for (int i = 0; i < G; ++i) {
+          const int q = lane + 32 * i;  // piece q: entry q / G, slot q % G
+          const int ent = q / G;
+          const int j = __shfl_sync(kFull, jl, ent < 32 ? ent : 31);
+          if (ent < cnt) cp_async16(dst + ent * KP + 4 * (q - ent * G), P + (int64_t)j * G + (q - ent * G));
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int q = lane + 32 * i;
+          if (q < 2 * cnt) cp_async16(dst + kChunk * KP + 4 * q, bval + 2 * c.base + q);
         }
       }
       cp_async_commit();
