@@ -381,58 +381,75 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   }
 }
 
-constexpr int kUpdThreads = 1024;
+constexpr int kUpdThreads = 256;
+constexpr int kRedThreads = 1024;
 
-// alpha_c of iteration it from the SpMM partials (every block, same order).
-__device__ void alpha_from_partials(const double* part_pq, int npq, int k, int kp, int it, const gp::CgState* st,
-                                    double* alpha /* shared, kp */, double* pq /* shared, kp */, double* scratch,
-                                    int* bad) {
+// alpha of iteration it (one block): p_c^T q_c from the SpMM partials in a
+// fixed order; alpha_c = |r_c|^2 / p_c^T q_c for columns still running.
+__global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restrict__ part_pq, int npq, int k,
+                                                          int kp, int it, gp::CgState* st, double* hist_alpha,
+                                                          int m_hist) {
+  if (st->fin[it & 1]) return;
+  __shared__ double scratch[kRedThreads];
+  __shared__ double pq[gp::kMaxCols];
   block_sum_partials(part_pq, npq, kp, kp, pq, scratch);
   if (threadIdx.x < kp) {
     const int c = threadIdx.x;
     double a = 0.0;
-    bad[c] = 0;
     if (c < k && !st->donep[it & 1][c]) {
       const double d = pq[c];
-      if (!(d > 0.0) || !isfinite(d)) bad[c] = 1;
-      else a = st->rrp[it & 1][c] / d;
+      if (!(d > 0.0) || !isfinite(d)) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = c;
+      } else {
+        a = st->rrp[it & 1][c] / d;
+        if (it < m_hist) {
+          hist_alpha[it * gp::kMaxCols + c] = a;
+          st->steps[c] = it + 1;
+        }
+      }
     }
-    alpha[c] = a;
+    st->alpha[c] = a;
   }
-  __syncthreads();
 }
 
-// B: R -= alpha Q, per-block |r_c|^2.  Block = (kq float4 columns) x rows.
-__global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int k, int kq, int it,
-                                                           const float4* __restrict__ Q, float4* __restrict__ R,
-                                                           const double* __restrict__ part_pq, int npq,
-                                                           double* __restrict__ part_rr, gp::CgState* st,
-                                                           double* hist_alpha, int m_hist) {
+// B: R -= alpha Q with per-block partial sums of |r_c|^2.  A thread owns one
+// float4 column slot (fixed, since the grid stride is a multiple of kq) and
+// walks rows four at a time so that several loads are in flight.
+__global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int kq, int it, const float4* __restrict__ Q,
+                                                           float4* __restrict__ R, double* __restrict__ part_rr,
+                                                           const gp::CgState* st) {
   if (st->fin[it & 1]) return;
-  __shared__ double scratch[kUpdThreads];
-  __shared__ double red[kUpdThreads * 4];
-  __shared__ double alpha[gp::kMaxCols], pq[gp::kMaxCols];
-  __shared__ int bad[gp::kMaxCols];
-  const int kp = 4 * kq;
-  alpha_from_partials(part_pq, npq, k, kp, it, st, alpha, pq, scratch, bad);
-  if (blockIdx.x == 0 && threadIdx.x < k) {
-    const int c = threadIdx.x;
-    if (bad[c]) {
-      st->status = GP_ERR_NOT_SPD;
-      st->bad_col = c;
-    } else if (!st->donep[it & 1][c] && it < m_hist) {
-      hist_alpha[it * gp::kMaxCols + c] = alpha[c];
-      st->steps[c] = it + 1;
-    }
-  }
-  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq, ny = blockDim.x / kq;
-  const bool act = ty < ny;
-  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (act) a = make_float4((float)alpha[4 * tx], (float)alpha[4 * tx + 1], (float)alpha[4 * tx + 2],
-                           (float)alpha[4 * tx + 3]);
+  __shared__ double red[kUpdThreads][4];
+  const int ny = kUpdThreads / kq;
+  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq;
   double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-  if (act) {
-    for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += (int64_t)gridDim.x * ny) {
+  if (ty < ny) {
+    const float4 a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1],
+                                 (float)st->alpha[4 * tx + 2], (float)st->alpha[4 * tx + 3]);
+    const int64_t stride = (int64_t)gridDim.x * ny;
+    int64_t p = (int64_t)blockIdx.x * ny + ty;
+    for (; p + 3 * stride < n; p += 4 * stride) {
+      float4 r[4], q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        r[u] = R[(p + u * stride) * kq + tx];
+        q[u] = Q[(p + u * stride) * kq + tx];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        r[u].x = fmaf(-a.x, q[u].x, r[u].x);
+        r[u].y = fmaf(-a.y, q[u].y, r[u].y);
+        r[u].z = fmaf(-a.z, q[u].z, r[u].z);
+        r[u].w = fmaf(-a.w, q[u].w, r[u].w);
+        R[(p + u * stride) * kq + tx] = r[u];
+        r0 += (double)r[u].x * r[u].x;
+        r1 += (double)r[u].y * r[u].y;
+        r2 += (double)r[u].z * r[u].z;
+        r3 += (double)r[u].w * r[u].w;
+      }
+    }
+    for (; p < n; p += stride) {
       float4 r = R[p * kq + tx];
       const float4 q = Q[p * kq + tx];
       r.x = fmaf(-a.x, q.x, r.x);
@@ -446,86 +463,110 @@ __global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int k, int
       r3 += (double)r.w * r.w;
     }
   }
-  red[threadIdx.x * 4 + 0] = r0;
-  red[threadIdx.x * 4 + 1] = r1;
-  red[threadIdx.x * 4 + 2] = r2;
-  red[threadIdx.x * 4 + 3] = r3;
+  red[threadIdx.x][0] = r0;
+  red[threadIdx.x][1] = r1;
+  red[threadIdx.x][2] = r2;
+  red[threadIdx.x][3] = r3;
   __syncthreads();
+  const int kp = 4 * kq;
   if (threadIdx.x < kp) {
     const int cx = threadIdx.x / 4, cc = threadIdx.x % 4;
     double t = 0.0;
-    for (int yy = 0; yy < ny; ++yy) t += red[(yy * kq + cx) * 4 + cc];
+    for (int yy = 0; yy < ny; ++yy) t += red[yy * kq + cx][cc];
     part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = t;
   }
 }
 
-// C: X += alpha P_old, P = R + beta P_old; block 0 publishes iteration it+1.
-__global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int k, int kq, int it,
-                                                            float4* __restrict__ X, const float4* __restrict__ R,
-                                                            float4* __restrict__ P,
-                                                            const double* __restrict__ part_pq, int npq,
-                                                            const double* __restrict__ part_rr, int nrr,
-                                                            gp::CgState* st, double* hist_beta, int m_hist) {
+// beta of iteration it (one block): |r_new|^2 from the partials, convergence,
+// and the iteration-(it+1) scalars in parity slot (it+1)&1.
+__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part_rr, int nrr, int k, int kp,
+                                                         int it, gp::CgState* st, double* hist_beta, int m_hist) {
   const int cur = it & 1, nxt = (it + 1) & 1;
   if (st->fin[cur]) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->fin[nxt] = 1;
+    if (threadIdx.x == 0) st->fin[nxt] = 1;
     return;
   }
-  __shared__ double scratch[kUpdThreads];
-  __shared__ double alpha[gp::kMaxCols], pq[gp::kMaxCols], rrn[gp::kMaxCols], beta[gp::kMaxCols];
-  __shared__ int bad[gp::kMaxCols];
+  __shared__ double scratch[kRedThreads];
+  __shared__ double rrn[gp::kMaxCols];
   __shared__ int any_running;
-  const int kp = 4 * kq;
-  alpha_from_partials(part_pq, npq, k, kp, it, st, alpha, pq, scratch, bad);
   block_sum_partials(part_rr, nrr, kp, kp, rrn, scratch);
   if (threadIdx.x == 0) any_running = 0;
   __syncthreads();
   if (threadIdx.x < kp) {
     const int c = threadIdx.x;
-    double b = 0.0;
     const bool was_done = c >= k || st->donep[cur][c];
-    if (!was_done) b = rrn[c] / st->rrp[cur][c];
-    beta[c] = b;
-    if (blockIdx.x == 0) {
-      bool done = was_done;
-      if (!was_done) {
-        if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
-        done = rrn[c] <= st->tol2 * st->rr0[c];
-        if (!isfinite(rrn[c])) {
-          st->status = GP_ERR_NOT_SPD;
-          st->bad_col = c;
-        }
+    double b = 0.0;
+    bool done = was_done;
+    if (!was_done) {
+      b = rrn[c] / st->rrp[cur][c];
+      if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
+      done = rrn[c] <= st->tol2 * st->rr0[c];
+      if (!isfinite(rrn[c])) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = c;
       }
-      st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn[c];
-      st->donep[nxt][c] = done;
-      if (c < k && !done) atomicOr(&any_running, 1);
     }
+    st->beta[c] = b;
+    st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn[c];
+    st->donep[nxt][c] = done;
+    if (c < k && !done) atomicOr(&any_running, 1);
   }
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
     st->iter = it + 1;
     const int f = !any_running || st->status != GP_OK || it + 1 >= st->max_iter;
     st->fin[nxt] = f;
     st->finished = f;
   }
-  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq, ny = blockDim.x / kq;
-  if (ty < ny) {
-    const float4 a = make_float4((float)alpha[4 * tx], (float)alpha[4 * tx + 1], (float)alpha[4 * tx + 2],
-                                 (float)alpha[4 * tx + 3]);
-    const float4 b = make_float4((float)beta[4 * tx], (float)beta[4 * tx + 1], (float)beta[4 * tx + 2],
-                                 (float)beta[4 * tx + 3]);
-    for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += (int64_t)gridDim.x * ny) {
-      const int64_t o = p * kq + tx;
-      const float4 po = P[o];
-      const float4 r = R[o];
-      float4 x = X[o];
-      x.x = fmaf(a.x, po.x, x.x);
-      x.y = fmaf(a.y, po.y, x.y);
-      x.z = fmaf(a.z, po.z, x.z);
-      x.w = fmaf(a.w, po.w, x.w);
-      X[o] = x;
-      P[o] = make_float4(fmaf(b.x, po.x, r.x), fmaf(b.y, po.y, r.y), fmaf(b.z, po.z, r.z), fmaf(b.w, po.w, r.w));
+}
+
+// C: X += alpha P_old, P = R + beta P_old (runs for iteration it unless the
+// run had already finished before it).
+__global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, int it, float4* __restrict__ X,
+                                                            const float4* __restrict__ R, float4* __restrict__ P,
+                                                            const gp::CgState* st) {
+  if (st->fin[it & 1]) return;
+  const int ny = kUpdThreads / kq;
+  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq;
+  if (ty >= ny) return;
+  const float4 a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1], (float)st->alpha[4 * tx + 2],
+                               (float)st->alpha[4 * tx + 3]);
+  const float4 b = make_float4((float)st->beta[4 * tx], (float)st->beta[4 * tx + 1], (float)st->beta[4 * tx + 2],
+                               (float)st->beta[4 * tx + 3]);
+  const int64_t stride = (int64_t)gridDim.x * ny;
+  int64_t p = (int64_t)blockIdx.x * ny + ty;
+  for (; p + stride < n; p += 2 * stride) {
+    float4 po[2], r[2], x[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t o = (p + u * stride) * kq + tx;
+      po[u] = P[o];
+      r[u] = R[o];
+      x[u] = X[o];
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t o = (p + u * stride) * kq + tx;
+      x[u].x = fmaf(a.x, po[u].x, x[u].x);
+      x[u].y = fmaf(a.y, po[u].y, x[u].y);
+      x[u].z = fmaf(a.z, po[u].z, x[u].z);
+      x[u].w = fmaf(a.w, po[u].w, x[u].w);
+      X[o] = x[u];
+      P[o] = make_float4(fmaf(b.x, po[u].x, r[u].x), fmaf(b.y, po[u].y, r[u].y), fmaf(b.z, po[u].z, r[u].z),
+                         fmaf(b.w, po[u].w, r[u].w));
+    }
+  }
+  for (; p < n; p += stride) {
+    const int64_t o = p * kq + tx;
+    const float4 po = P[o];
+    const float4 r = R[o];
+    float4 x = X[o];
+    x.x = fmaf(a.x, po.x, x.x);
+    x.y = fmaf(a.y, po.y, x.y);
+    x.z = fmaf(a.z, po.z, x.z);
+    x.w = fmaf(a.w, po.w, x.w);
+    X[o] = x;
+    P[o] = make_float4(fmaf(b.x, po.x, r.x), fmaf(b.y, po.y, r.y), fmaf(b.z, po.z, r.z), fmaf(b.w, po.w, r.w));
   }
 }
 
@@ -911,7 +952,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   GP_CHECK(ensure(c, c->zbits, (size_t)n * 2 * sizeof(uint32_t)));
   const int maxb = c->num_sms * 4;
   GP_CHECK(ensure(c, c->part_a, (size_t)maxb * 4 * kMaxCols * sizeof(double)));
-  GP_CHECK(ensure(c, c->part_b, (size_t)maxb * 4 * kMaxCols * sizeof(double)));
+  GP_CHECK(ensure(c, c->part_b, (size_t)c->num_sms * 8 * kMaxCols * sizeof(double)));
   GP_CHECK(ensure(c, c->hist_alpha, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
   GP_CHECK(ensure(c, c->hist_beta, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
   CgState* st = (CgState*)c->cg.p;
@@ -933,7 +974,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   const unsigned g_spmm = grid_for(nblk, kSpmmWarps, c->num_sms * spmm_per_sm);
   const int kq = kp / 4;
   const int ny = kUpdThreads / kq;
-  const unsigned g_upd = grid_for(n, ny, c->num_sms);
+  const unsigned g_upd = grid_for(n, ny, c->num_sms * 8);
   if (check_every <= 0) check_every = 16;
   if (check_every > 64) check_every = 64;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
@@ -944,20 +985,22 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     for (int t = 0; t < check_every; ++t) {
       const int it = it0 + t;
       if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t], c->stream));
-      spmm<<<g_spmm, kSpmmThreads, spmm_smem, c->stream>>>(n, nblk, it, (const int64_t*)c->brp.p, (const int32_t*)c->bcol.p,
-                                                   (const float4*)c->bval.p, (const float4*)c->P.p,
-                                                   (float4*)c->Q.p, (double*)c->part_a.p, st);
+      spmm<<<g_spmm, kSpmmThreads, spmm_smem, c->stream>>>(n, nblk, it, (const int64_t*)c->brp.p,
+                                                           (const int32_t*)c->bcol.p, (const float4*)c->bval.p,
+                                                           (const float4*)c->P.p, (float4*)c->Q.p,
+                                                           (double*)c->part_a.p, st);
       if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t + 1], c->stream));
-      k_upd_r_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, k, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
-                                                        (const double*)c->part_a.p, (int)g_spmm,
-                                                        (double*)c->part_b.p, st, (double*)c->hist_alpha.p, m_hist);
-      k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, k, kq, it, (float4*)c->X.p, (const float4*)c->R.p,
-                                                         (float4*)c->P.p, (const double*)c->part_a.p, (int)g_spmm,
-                                                         (const double*)c->part_b.p, (int)g_upd, st,
-                                                         (double*)c->hist_beta.p, m_hist);
+      k_cg_alpha<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, it, st,
+                                                   (double*)c->hist_alpha.p, m_hist);
+      k_upd_r_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                        (double*)c->part_b.p, st);
+      k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_upd, k, kp, it, st,
+                                                  (double*)c->hist_beta.p, m_hist);
+      k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (float4*)c->X.p, (const float4*)c->R.p,
+                                                         (float4*)c->P.p, st);
     }
     GP_LAUNCH_CHECK();
-    c->launches += 3 * check_every;
+    c->launches += 5 * check_every;
     GP_CHECK(read_state(c, &hs));
     if (timed) {
       // launches after convergence return at once: time only the ones that worked
