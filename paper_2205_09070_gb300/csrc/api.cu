@@ -329,7 +329,7 @@ int gp_destroy(gp_ctx* c) {
                         &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
                         &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
-                        &c->bval};
+                        &c->bval,   &c->slq_g};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);

@@ -511,8 +511,10 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
 // is outside the pattern) and an 8-bit mask of the pattern entries.  One
 // column index and one gathered P row then serve up to 8 rows.
 // The support predicate is evaluated exactly as in k_pair (same FP32
-// expression, same FP64 guard band), so the block pattern and the scalar CSR
-// pattern are identical.
+// expression, same FP64 guard band), so the two patterns are identical, and
+// candidate columns are visited in ascending order, so the hits of each row
+// arrive in the order of its scalar-CSR row: the fill copies the values
+// already computed there.
 constexpr int kBR = 8;
 constexpr int kBWarps = 4;
 constexpr int kMaxCand = kBR * 27;  // distinct neighbour cells of one block row
@@ -524,24 +526,26 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
   __shared__ float4 s_rx[kBWarps][kBR];
   __shared__ int4 s_rc[kBWarps][kBR];
   __shared__ uint32_t s_rm[kBWarps][kBR];
-  __shared__ float s_rd[kBWarps][kBR];
   __shared__ int s_start[kBWarps][kMaxCand];
-  __shared__ int s_pre[kBWarps][kMaxCand];
+  __shared__ int s_len[kBWarps][kMaxCand];
   __shared__ int4 s_cc[kBWarps][kMaxCand];
+  __shared__ int s_start2[kBWarps][kMaxCand];
+  __shared__ int s_pre[kBWarps][kMaxCand];
+  __shared__ int4 s_cc2[kBWarps][kMaxCand];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const float* Fs = (const float*)a.Fs;
-  const float* dinv = (const float*)a.dinv;
+  const float* csr_val = (const float*)a.val;
   const int G[3] = {a.G0, a.G1, a.G2};
   for (int64_t bb = (int64_t)blockIdx.x * kBWarps + w; bb < nblk; bb += (int64_t)gridDim.x * kBWarps) {
     const int64_t r0 = bb * kBR;
     const int nr = (int)min((int64_t)kBR, a.n - r0);
     int4 myc = make_int4(-1, -1, -1, 0);
+    int64_t myrow = 0;  // next unread scalar-CSR entry of row r0 + lane
     if (lane < nr) {
       myc = a.cellc[r0 + lane];
       s_rx[w][lane] = a.xr[r0 + lane];
       s_rc[w][lane] = myc;
       s_rm[w][lane] = a.mask[r0 + lane];
-      s_rd[w][lane] = FILL ? dinv[r0 + lane] : 0.f;
+      if (FILL) myrow = a.row_ptr[r0 + lane];
     }
     // one representative lane per distinct row cell
     bool rep = lane < nr;
@@ -585,12 +589,23 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
       if (ok) {
         const int pos = L + __popc(bal & gpd::lanemask_lt());
         s_start[w][pos] = start;
-        s_pre[w][pos] = len;
+        s_len[w][pos] = len;
         s_cc[w][pos] = make_int4(nc[0], nc[1], nc[2], 0);
       }
       L += __popc(bal);
       __syncwarp();
     }
+    // order the cells by first sorted index (distinct for non-empty cells),
+    // which orders the candidate columns ascending
+    for (int e = lane; e < L; e += 32) {
+      const int st0 = s_start[w][e];
+      int rank = 0;
+      for (int t2 = 0; t2 < L; ++t2) rank += s_start[w][t2] < st0;
+      s_start2[w][rank] = st0;
+      s_pre[w][rank] = s_len[w][e];
+      s_cc2[w][rank] = s_cc[w][e];
+    }
+    __syncwarp();
     // exclusive prefix of the range lengths
     int run = 0;
     for (int c0 = 0; c0 < L; c0 += 32) {
@@ -608,18 +623,14 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
       const int f = base + lane;
       uint32_t bits = 0u;
       int j = 0;
-      float v[kBR];
-#pragma unroll
-      for (int rr = 0; rr < kBR; ++rr) v[rr] = 0.f;
       if (f < total) {
         int r = 0;
         for (int step = 128; step > 0; step >>= 1)
           if (r + step < L && s_pre[w][r + step] <= f) r += step;
-        j = s_start[w][r] + (f - s_pre[w][r]);
-        const int4 cj = s_cc[w][r];
+        j = s_start2[w][r] + (f - s_pre[w][r]);
+        const int4 cj = s_cc2[w][r];
         const uint32_t mj = a.mask[j];
         const float4 xj = a.xr[j];
-        const float dj = FILL ? dinv[j] : 0.f;
 #pragma unroll
         for (int rr = 0; rr < kBR; ++rr) {
           if (rr >= nr) break;
@@ -629,52 +640,34 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
           const int ox = cj.x - ci.x, oy = cj.y - ci.y, oz = cj.z - ci.z;
           if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) continue;
           const float4 xi = s_rx[w][rr];
-          const int64_t p = r0 + rr;
           const float dx = (xj.x + (float)ox) - xi.x;
           const float dy = (xj.y + (float)oy) - xi.y;
           const float dz = (xj.z + (float)oz) - xi.z;
           const float r2 = (dx * dx + dy * dy + dz * dz) * a.scale;
           bool hit;
-          float rho2, s2;
-          if (fabsf(r2 - 1.0f) < a.guard) {
-            const double e2 = dist2_fp64(a.xs, a.dim, p, j);
-            hit = e2 < a.rs2;
-            rho2 = (float)(e2 / a.rs2);
-            s2 = (float)((a.rs2 - e2) / a.rs2);
-          } else {
-            hit = r2 < 1.0f;
-            rho2 = r2;
-            s2 = 1.0f - r2;
-            if (FILL && hit && s2 < 0.1f) {
-              const double e2 = dist2_fp64(a.xs, a.dim, p, j);
-              rho2 = (float)(e2 / a.rs2);
-              s2 = (float)((a.rs2 - e2) / a.rs2);
-            }
-          }
-          if (!hit) continue;
-          bits |= 1u << rr;
-          if (FILL) {
-            float S = 0.f;
-            uint32_t common = mi & mj;
-            while (common) {
-              const int m = __ffs(common) - 1;
-              common &= common - 1u;
-              S += Fs[p * a.n1 + m] * Fs[(int64_t)j * a.n1 + m];
-            }
-            float val = (float)a.AC * gpd::kstat_unit_f(rho2, s2) * S;
-            if (j == p) val += (float)a.sigma2;
-            v[rr] = val * s_rd[w][rr] * dj;
-          }
+          if (fabsf(r2 - 1.0f) < a.guard) hit = dist2_fp64(a.xs, a.dim, r0 + rr, j) < a.rs2;
+          else hit = r2 < 1.0f;
+          if (hit) bits |= 1u << rr;
         }
       }
       const unsigned bal = __ballot_sync(kFull, bits != 0u);
-      if (FILL && bits != 0u) {
-        const int64_t q = out + count + __popc(bal & gpd::lanemask_lt());
-        bcol[q] = j;
-        bmask[q] = (uint8_t)bits;
-        float4* dst = (float4*)(bval + q * kBR);
-        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+      if (FILL) {
+        float v[kBR];
+#pragma unroll
+        for (int rr = 0; rr < kBR; ++rr) {
+          const unsigned br = __ballot_sync(kFull, (bits >> rr) & 1u);
+          const int64_t row_next = __shfl_sync(kFull, myrow, rr);
+          v[rr] = ((bits >> rr) & 1u) ? csr_val[row_next + __popc(br & gpd::lanemask_lt())] : 0.f;
+          if (lane == rr) myrow += __popc(br);
+        }
+        if (bits != 0u) {
+          const int64_t q = out + count + __popc(bal & gpd::lanemask_lt());
+          bcol[q] = j;
+          bmask[q] = (uint8_t)bits;
+          float4* dst = (float4*)(bval + q * kBR);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
       }
       count += __popc(bal);
     }
@@ -940,6 +933,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     GP_CHECK(gp::ensure(c, c->bcol, (size_t)nbe * sizeof(int32_t)));
     GP_CHECK(gp::ensure(c, c->bmask, (size_t)nbe));
     GP_CHECK(gp::ensure(c, c->bval, (size_t)nbe * kBR * sizeof(float)));
+    // pa.row_ptr / pa.val point at the filled scalar CSR
     k_bpair<true><<<gbk, kBWarps * 32, 0, c->stream>>>(pa, nblk, (const int64_t*)c->brp.p, nullptr,
                                                         (int32_t*)c->bcol.p, (uint8_t*)c->bmask.p,
                                                         (float*)c->bval.p);

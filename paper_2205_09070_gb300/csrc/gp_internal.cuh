@@ -86,6 +86,7 @@ struct AsmScalars {
   unsigned ticket1;
   unsigned ticket2;
   unsigned ticket3;
+  unsigned ticket4;
   int status;
 };
 
@@ -125,7 +126,7 @@ struct gp_ctx {
   gp::DevBuf part_a, part_b, part_c, hist_alpha, hist_beta;
   gp::DevBuf g, grad_part, grad_bump;
   gp::DevBuf cg, asm_s;
-  gp::DevBuf csr_tmp;
+  gp::DevBuf csr_tmp, slq_g;
 
   // pinned host staging
   void* pinned = nullptr;
@@ -264,6 +265,23 @@ template <> struct Real<float> {
 template <> struct Real<double> {
   __device__ static double kstat(double r2, double s2) { return kstat_unit_d(r2, s2); }
   __device__ static double dk(double r2, double s2) { return atanh_minus_s_d(r2, s2); }
+};
+
+// Compensated FP32 accumulation of products: the product's rounding error
+// (FMA) and each addition's rounding error (Knuth's TwoSum) are carried in a
+// second float, so a per-thread partial dot product keeps FP64-class accuracy
+// without FP64 arithmetic; partials are then combined in FP64.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ inline void add(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float t = s + p;
+    const float z = t - s;
+    c += ((s - (t - z)) + (p - z)) + e;
+    s = t;
+  }
+  __device__ inline double value() const { return (double)s + (double)c; }
 };
 
 __device__ inline unsigned lanemask_lt() {

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane - grp * G;
   const bool act = grp < NG;
-  double pq0 = 0, pq1 = 0, pq2 = 0, pq3 = 0;
+  gpd::Dot2 pq0, pq1, pq2, pq3;
   // Work split by stored blocks, not by block rows (cluster cores hold many
   // times more blocks per row than the background).
   const int64_t nent = brp[nblk];
@@ -350,10 +350,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
             if (row < n) {
               Q[row * G + gl] = acc[r];
               const float4 pp = __ldg(P + row * G + gl);
-              pq0 += (double)pp.x * acc[r].x;
-              pq1 += (double)pp.y * acc[r].y;
-              pq2 += (double)pp.z * acc[r].z;
-              pq3 += (double)pp.w * acc[r].w;
+              pq0.add(pp.x, acc[r].x);
+              pq1.add(pp.y, acc[r].y);
+              pq2.add(pp.z, acc[r].z);
+              pq3.add(pp.w, acc[r].w);
             }
           }
         }
@@ -368,10 +368,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     cp_async_wait<0>();
   }
   if (grp == 0) {
-    sh[w][4 * gl + 0] = pq0;
-    sh[w][4 * gl + 1] = pq1;
-    sh[w][4 * gl + 2] = pq2;
-    sh[w][4 * gl + 3] = pq3;
+    sh[w][4 * gl + 0] = pq0.value();
+    sh[w][4 * gl + 1] = pq1.value();
+    sh[w][4 * gl + 2] = pq2.value();
+    sh[w][4 * gl + 3] = pq3.value();
   }
   __syncthreads();
   if (threadIdx.x < KP) {
@@ -415,15 +415,18 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restri
 
 // B: R -= alpha Q with per-block partial sums of |r_c|^2.  A thread owns one
 // float4 column slot (fixed, since the grid stride is a multiple of kq) and
-// walks rows four at a time so that several loads are in flight.
-__global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int kq, int it, const float4* __restrict__ Q,
-                                                           float4* __restrict__ R, double* __restrict__ part_rr,
-                                                           const gp::CgState* st) {
+// walks rows four at a time so that several loads are in flight; its sums
+// are compensated FP32 (Dot2), the block's are combined in FP64 by a tree.
+constexpr int kUpdRThreads = 1024;
+
+__global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, int it, const float4* __restrict__ Q,
+                                                            float4* __restrict__ R, double* __restrict__ part_rr,
+                                                            const gp::CgState* st) {
   if (st->fin[it & 1]) return;
-  __shared__ double red[kUpdThreads][4];
-  const int ny = kUpdThreads / kq;
+  __shared__ double red[kUpdRThreads][4];
+  const int ny = kUpdRThreads / kq;
   const int tx = threadIdx.x % kq, ty = threadIdx.x / kq;
-  double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+  gpd::Dot2 r0, r1, r2, r3;
   if (ty < ny) {
     const float4 a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1],
                                  (float)st->alpha[4 * tx + 2], (float)st->alpha[4 * tx + 3]);
@@ -443,10 +446,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int kq, in
         r[u].z = fmaf(-a.z, q[u].z, r[u].z);
         r[u].w = fmaf(-a.w, q[u].w, r[u].w);
         R[(p + u * stride) * kq + tx] = r[u];
-        r0 += (double)r[u].x * r[u].x;
-        r1 += (double)r[u].y * r[u].y;
-        r2 += (double)r[u].z * r[u].z;
-        r3 += (double)r[u].w * r[u].w;
+        r0.add(r[u].x, r[u].x);
+        r1.add(r[u].y, r[u].y);
+        r2.add(r[u].z, r[u].z);
+        r3.add(r[u].w, r[u].w);
       }
     }
     for (; p < n; p += stride) {
@@ -457,24 +460,28 @@ __global__ void __launch_bounds__(kUpdThreads) k_upd_r_f32(int64_t n, int kq, in
       r.z = fmaf(-a.z, q.z, r.z);
       r.w = fmaf(-a.w, q.w, r.w);
       R[p * kq + tx] = r;
-      r0 += (double)r.x * r.x;
-      r1 += (double)r.y * r.y;
-      r2 += (double)r.z * r.z;
-      r3 += (double)r.w * r.w;
+      r0.add(r.x, r.x);
+      r1.add(r.y, r.y);
+      r2.add(r.z, r.z);
+      r3.add(r.w, r.w);
     }
   }
-  red[threadIdx.x][0] = r0;
-  red[threadIdx.x][1] = r1;
-  red[threadIdx.x][2] = r2;
-  red[threadIdx.x][3] = r3;
+  red[threadIdx.x][0] = r0.value();
+  red[threadIdx.x][1] = r1.value();
+  red[threadIdx.x][2] = r2.value();
+  red[threadIdx.x][3] = r3.value();
   __syncthreads();
-  const int kp = 4 * kq;
-  if (threadIdx.x < kp) {
-    const int cx = threadIdx.x / 4, cc = threadIdx.x % 4;
-    double t = 0.0;
-    for (int yy = 0; yy < ny; ++yy) t += red[yy * kq + cx][cc];
-    part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = t;
+  // tree over the row index ty (same column slot tx), fixed order
+  for (int h = 1; h < ny; h <<= 1) {
+    if (ty < ny && (ty & (2 * h - 1)) == 0 && ty + h < ny) {
+      const int o = threadIdx.x + h * kq;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[threadIdx.x][q] += red[o][q];
+    }
+    __syncthreads();
   }
+  const int kp = 4 * kq;
+  if (threadIdx.x < kp) part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = red[threadIdx.x / 4][threadIdx.x % 4];
 }
 
 // beta of iteration it (one block): |r_new|^2 from the partials, convergence,
@@ -831,15 +838,15 @@ __device__ bool tridiag_ql(double* d, double* e, double* z, int m) {
   return true;
 }
 
-// One thread per probe: Lanczos T from the CG coefficients of column 1+l
-// (Saad, Sec. 6.7.3): T_tt = 1/alpha_t + beta_{t-1}/alpha_{t-1},
+// One block per probe (the eigen-solve is serial FP64 work, so each probe
+// gets an SM's FP64 units of its own): Lanczos T from the CG coefficients
+// of column 1+l (Saad, Sec. 6.7.3): T_tt = 1/alpha_t + beta_{t-1}/alpha_{t-1},
 // T_t,t+1 = sqrt(beta_t)/alpha_t; Gamma_l = |z|^2 sum_k tau_k^2 ln theta_k.
+// The last block to finish forms the mean and variance over probes.
 __global__ void k_slq(int nv, int64_t n_act, const double* __restrict__ ha, const double* __restrict__ hb,
-                      const gp::CgState* st, gp::AsmScalars* s) {
-  __shared__ double gam[gp::kMaxProbes];
-  __shared__ int bad[gp::kMaxProbes];
-  const int l = threadIdx.x;
-  if (l < nv) {
+                      const gp::CgState* st, double* gam, gp::AsmScalars* s) {
+  const int l = blockIdx.x;
+  if (threadIdx.x == 0) {
     const int c = 1 + l;
     const int m = st->steps[c];
     double d[gp::kMaxLanczos], e[gp::kMaxLanczos], z[gp::kMaxLanczos];
@@ -854,20 +861,28 @@ __global__ void k_slq(int nv, int64_t n_act, const double* __restrict__ ha, cons
       if (!(d[t] > 0.0)) ok = false;
       else g += z[t] * z[t] * log(d[t]);
     }
-    gam[l] = g * (double)n_act;
-    bad[l] = !ok;
+    gam[2 * l] = g * (double)n_act;
+    gam[2 * l + 1] = ok ? 0.0 : 1.0;
+    __threadfence();
   }
+  __shared__ bool last;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) last = atomicInc(&s->ticket4, gridDim.x - 1) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
     double mean = 0.0;
     int nbad = 0;
     for (int q = 0; q < nv; ++q) {
-      mean += gam[q];
-      nbad += bad[q];
+      mean += __ldcg(gam + 2 * q);
+      nbad += __ldcg(gam + 2 * q + 1) != 0.0;
     }
     mean /= nv;
     double var = 0.0;
-    for (int q = 0; q < nv; ++q) var += (gam[q] - mean) * (gam[q] - mean);
+    for (int q = 0; q < nv; ++q) {
+      const double dq = __ldcg(gam + 2 * q) - mean;
+      var += dq * dq;
+    }
     var = nv > 1 ? var / (nv - 1) : 0.0;
     s->slq_mean = mean;
     s->slq_var = var;
@@ -975,6 +990,8 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   const int kq = kp / 4;
   const int ny = kUpdThreads / kq;
   const unsigned g_upd = grid_for(n, ny, c->num_sms * 8);
+  const int ny_r = kUpdRThreads / kq;
+  const unsigned g_upd_r = grid_for(n, ny_r, c->num_sms * 2);
   if (check_every <= 0) check_every = 16;
   if (check_every > 64) check_every = 64;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
@@ -992,9 +1009,9 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
       if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t + 1], c->stream));
       k_cg_alpha<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, it, st,
                                                    (double*)c->hist_alpha.p, m_hist);
-      k_upd_r_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
-                                                        (double*)c->part_b.p, st);
-      k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_upd, k, kp, it, st,
+      k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                           (double*)c->part_b.p, st);
+      k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, it, st,
                                                   (double*)c->hist_beta.p, m_hist);
       k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (float4*)c->X.p, (const float4*)c->R.p,
                                                          (float4*)c->P.p, st);
@@ -1131,8 +1148,9 @@ int slq(gp_ctx* c, int nv, int kcols) {
     GP_CUDA(cudaMemsetAsync(&s->slq_mean, 0, 2 * sizeof(double), c->stream));
     return GP_OK;
   }
-  k_slq<<<1, kMaxProbes, 0, c->stream>>>(nv, c->n_act, (const double*)c->hist_alpha.p,
-                                         (const double*)c->hist_beta.p, (const CgState*)c->cg.p, s);
+  GP_CHECK(ensure(c, c->slq_g, (size_t)2 * kMaxProbes * sizeof(double)));
+  k_slq<<<nv, 32, 0, c->stream>>>(nv, c->n_act, (const double*)c->hist_alpha.p, (const double*)c->hist_beta.p,
+                                  (const CgState*)c->cg.p, (double*)c->slq_g.p, s);
   GP_LAUNCH_CHECK();
   c->launches += 1;
   return GP_OK;
