@@ -238,9 +238,8 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2205_09070_gb300.sharding import max_over_ranks
+        ms = max_over_ranks(ms, device=dev)
     clocks = clk.summary()
     value = world * a.steps / (ms / 1e3)
 

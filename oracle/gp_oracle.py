@@ -239,11 +239,17 @@ def assemble_csr(x, h, dim, n1, n2, beta=1.0, chunk=512):
     return row_ptr, col, val
 
 
-def dense_K(x, h, dim, n1, n2, beta=1.0):
-    """Dense K (N x N) by brute force; entries outside the pattern are zero."""
+def dense_K(x, h, dim, n1, n2, beta=1.0, chunk=1024):
+    """Dense K (N x N) by brute force; entries outside the pattern are zero.
+    Rows are filled in chunks to bound the temporaries."""
     x = np.asarray(x, dtype=np.float64)
-    _, vals = pair_rows(x, h, dim, n1, n2, np.arange(x.shape[0]), beta)
-    return vals
+    n = x.shape[0]
+    table = bump_table(x, h, dim, n1, n2, beta)
+    K = np.zeros((n, n))
+    for start in range(0, n, chunk):
+        rows = np.arange(start, min(n, start + chunk))
+        _, K[rows] = pair_rows(x, h, dim, n1, n2, rows, beta, table)
+    return K
 
 
 # ----------------------------------------------------------------------------

@@ -173,6 +173,14 @@ class GP:
         self._h = h
         self.n_params = int(self._lib.gp_n_params(ctypes.byref(self.desc)))
 
+    def _hyper(self, h, n_inst=None):
+        """Hyperparameters as a contiguous float64 host array of the right length."""
+        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64)).reshape(-1)
+        want = self.n_params * (1 if n_inst is None else n_inst)
+        if hh.shape[0] != want:
+            raise ValueError(f"expected {want} hyperparameters, got {hh.shape[0]}")
+        return hh
+
     def _check(self, st: int, where: str, allow=(GP_OK,)):
         if st not in allow:
             raise GPError(st, where)
@@ -200,7 +208,7 @@ class GP:
         self._sync_stream()
         n = int(x.shape[0])
         xp, xk = _ptr(x)
-        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+        hh = self._hyper(h)
         o = default_opts(precision=precision)
         info = Info()
         self._check(self._lib.gp_assemble(self._h, xp, n, hh.ctypes.data, ctypes.byref(o), ctypes.byref(info)),
@@ -236,7 +244,7 @@ class GP:
         o = opts or default_opts()
         xp, xk = _ptr(x)
         yp, yk = _ptr(y)
-        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+        hh = self._hyper(h)
         out = ctypes.c_double()
         info = Info()
         allow = (GP_OK, GP_ERR_NOT_CONVERGED) if allow_not_converged else (GP_OK,)
@@ -249,7 +257,7 @@ class GP:
         o = opts or default_opts()
         xp, xk = _ptr(x)
         yp, yk = _ptr(y)
-        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+        hh = self._hyper(h)
         if grad is None:
             grad = np.zeros(self.n_params, np.float64)
         gp_, gk = _ptr(grad)
@@ -267,7 +275,7 @@ class GP:
         n_inst = off.shape[0] - 1
         xp, xk = _ptr(x)
         yp, yk = _ptr(y)
-        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(-1))
+        hh = self._hyper(h, n_inst)
         lml = np.zeros(n_inst, np.float64)
         grad = np.zeros((n_inst, self.n_params), np.float64) if with_grad else None
         info = Info()

@@ -1,0 +1,171 @@
+"""GPU edge cases and error paths through the C ABI: empty and single-point
+inputs, all points outside every bump, host vs device pointers, invalid
+arguments, the iteration cap, ragged batches."""
+
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gp_oracle as O
+from paper_2205_09070_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2205_09070_gb300 import gpsparse
+    assert torch.cuda.is_available()
+    return gpsparse
+
+
+def opts(G, prec="fp32", **kw):
+    base = dict(precision=prec, n_probes=8, lanczos_steps=20, cg_rtol=1e-8 if prec == "fp64" else 1e-6, seed=3)
+    base.update(kw)
+    return G.default_opts(**base)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_empty_input(G, prec):
+    p = W.small_2d(seed=1, n=10)
+    gp = G.GP(p.dim, p.n1, p.n2)
+    x = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+    y = torch.zeros(0, dtype=torch.float64, device="cuda")
+    lml, grad, info = gp.lml_grad(x, y, p.h, opts(G, prec))
+    assert lml == 0.0 and info["n"] == 0 and info["nnz"] == 0
+    assert np.all(grad == 0.0)
+    gp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_point(G, prec):
+    # N = 1 inside a bump: K = A C f^2 + s2, exact LML = -y^2/(2K) - ln(K)/2;
+    # SLQ is exact for a 1x1 matrix (Khat = 1)
+    c = np.array([[[0.5, 0.5]]])
+    h = W.pack_h(c, np.array([[0.3]]), np.array([[1.7]]), 0.1, 1.3, 0.01)
+    x = np.array([[0.52, 0.47]])
+    y = np.array([0.8])
+    K = O.dense_K(x, h, 2, 1, 1)[0, 0]
+    expect = -0.5 * y[0] ** 2 / K - 0.5 * math.log(K)
+    gp = G.GP(2, 1, 1)
+    lml, grad, info = gp.lml_grad(torch.as_tensor(x, device="cuda"), torch.as_tensor(y, device="cuda"), h,
+                                  opts(G, prec))
+    assert info["n_active"] == 1 and info["nnz"] == 1
+    assert lml == pytest.approx(expect, rel=1e-12 if prec == "fp64" else 1e-6)
+    lx, gx = O.lml_grad_exact(x, y, h, 2, 1, 1)
+    assert np.allclose(grad, gx, rtol=1e-8 if prec == "fp64" else 1e-4, atol=1e-10 * np.abs(gx).max())
+    gp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_all_points_inactive(G, prec):
+    p = W.small_2d(seed=2, n=3000)
+    P = O.unpack_h(p.h, p.dim, p.n1, p.n2)
+    h = W.pack_h(np.full((p.n1, p.n2, 2), 7.0), P["radii"], P["amps"], P["r_s"], P["A"], P["sigma2"])
+    gp = G.GP(p.dim, p.n1, p.n2)
+    lml, grad, info = gp.lml_grad(torch.as_tensor(p.x, device="cuda"), torch.as_tensor(p.y, device="cuda"), h,
+                                  opts(G, prec))
+    s2 = P["sigma2"]
+    expect = -0.5 * float(p.y @ p.y) / s2 - 0.5 * p.n * math.log(s2)
+    assert info["n_active"] == 0 and info["nnz"] == 0
+    assert lml == pytest.approx(expect, rel=1e-13)
+    assert grad[-1] == pytest.approx(0.5 * float(p.y @ p.y) / s2 ** 2 - 0.5 * p.n / s2, rel=1e-12)
+    assert np.all(grad[:-1] == 0.0)
+    gp.close()
+
+
+def test_host_and_device_pointers_agree(G):
+    p = W.grad_3d(seed=3, n=2000)
+    o = opts(G, "fp32")
+    gp = G.GP(p.dim, p.n1, p.n2)
+    l_dev, g_dev, _ = gp.lml_grad(torch.as_tensor(p.x, device="cuda"), torch.as_tensor(p.y, device="cuda"), p.h, o)
+    l_host, g_host, _ = gp.lml_grad(p.x, p.y, p.h, o)                 # numpy (pageable host)
+    gpin = torch.zeros(gp.n_params, dtype=torch.float64, device="cuda")
+    l_pin, _, _ = gp.lml_grad(torch.as_tensor(p.x).pin_memory(), torch.as_tensor(p.y).pin_memory(), p.h, o,
+                              grad=gpin)
+    assert l_dev == l_host == l_pin                                    # deterministic reductions
+    assert np.array_equal(g_dev, g_host)
+    assert np.array_equal(gpin.cpu().numpy(), g_dev)
+    gp.close()
+
+
+def test_repeat_calls_bitwise_identical(G):
+    p = W.mixture_3d(seed=9, n=30000, r_s=0.005 * (5e6 / 30000) ** (1 / 3))
+    x = torch.as_tensor(p.x, device="cuda")
+    y = torch.as_tensor(p.y, device="cuda")
+    gp = G.GP(p.dim, p.n1, p.n2)
+    o = opts(G, "fp32", n_probes=32, lanczos_steps=50)
+    a = gp.lml_grad(x, y, p.h, o)
+    b = gp.lml_grad(x, y, p.h, o)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    gp.close()
+
+
+def test_invalid_arguments_are_rejected(G):
+    p = W.small_2d(seed=1, n=200)
+    gp = G.GP(p.dim, p.n1, p.n2)
+    x = torch.as_tensor(p.x, device="cuda")
+    y = torch.as_tensor(p.y, device="cuda")
+    bad = []
+    h = p.h.copy(); h[0] = np.nan; bad.append(h)                        # non-finite centre
+    h = p.h.copy(); h[2] = -0.1; bad.append(h)                          # negative bump radius
+    h = p.h.copy(); h[-3] = 0.0; bad.append(h)                          # zero stationary radius
+    h = p.h.copy(); h[-1] = 0.0; bad.append(h)                          # zero noise
+    h = p.h.copy(); h[-2] = -1.0; bad.append(h)                         # negative amplitude A
+    for hb in bad:
+        with pytest.raises(G.GPError) as e:
+            gp.lml(x, y, hb, opts(G))
+        assert e.value.status == G.GP_ERR_INVALID_ARG
+    for o in (opts(G, n_probes=0), opts(G, n_probes=65), opts(G, lanczos_steps=0), opts(G, max_iter=0),
+              opts(G, cg_rtol=0.0), opts(G, precision=7)):
+        with pytest.raises(G.GPError) as e:
+            gp.lml(x, y, p.h, o)
+        assert e.value.status == G.GP_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        gp.lml(x, y, p.h[:-1], opts(G))                                 # checked by the binding
+    gp.close()
+    fresh = G.GP(p.dim, p.n1, p.n2)
+    with pytest.raises(G.GPError) as e:
+        fresh.get_csr()
+    assert e.value.status == G.GP_ERR_NOT_ASSEMBLED
+    with pytest.raises(G.GPError) as e:
+        fresh.solve(y)
+    assert e.value.status == G.GP_ERR_NOT_ASSEMBLED
+    fresh.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_iteration_cap_reports_not_converged(G, prec):
+    p = W.small_2d(seed=1)
+    gp = G.GP(p.dim, p.n1, p.n2)
+    x = torch.as_tensor(p.x, device="cuda")
+    y = torch.as_tensor(p.y, device="cuda")
+    with pytest.raises(G.GPError) as e:
+        gp.lml_grad(x, y, p.h, opts(G, prec, max_iter=3, check_every=1))
+    assert e.value.status == G.GP_ERR_NOT_CONVERGED
+    lml, grad, info = gp.lml_grad(x, y, p.h, opts(G, prec, max_iter=3, check_every=1), allow_not_converged=True)
+    assert info["iters"] == 3 and np.isfinite(lml) and np.all(np.isfinite(grad))
+    gp.close()
+
+
+def test_batched_matches_single_calls(G):
+    probs = W.batch_2d(seed=4, n_inst=6, n_range=(1, 4000))
+    probs[1] = W.batch_2d(seed=5, n_inst=1, n_range=(1, 1))[0]          # an instance with N = 1
+    offsets = np.concatenate([[0], np.cumsum([q.n for q in probs])])
+    x = np.concatenate([q.x for q in probs])
+    y = np.concatenate([q.y for q in probs])
+    h = np.stack([q.h for q in probs])
+    gp = G.GP(2, 2, 4)
+    o = opts(G, "fp32")
+    lml_b, grad_b, _ = gp.lml_grad_batched(offsets, torch.as_tensor(x, device="cuda"),
+                                           torch.as_tensor(y, device="cuda"), h, o)
+    for k, q in enumerate(probs):
+        l1, g1, _ = gp.lml_grad(torch.as_tensor(q.x, device="cuda"), torch.as_tensor(q.y, device="cuda"), q.h, o)
+        assert lml_b[k] == l1
+        assert np.array_equal(grad_b[k], g1)
+    gp.close()
