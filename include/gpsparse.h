@@ -144,6 +144,29 @@ int gp_assemble(gp_ctx* ctx, const double* x, int64_t n, const double* h,
 int gp_get_csr(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
                int32_t* perm, int64_t sizes[2]);
 
+/* Copy-out that allocates no device memory.  No counterpart in the paper.
+ * For callers that cannot call cudaMalloc at this point: code that runs while
+ * a CUDA graph is being captured on the device, or a process whose device
+ * memory is entirely handed out by another allocator (a serving runtime's
+ * memory pool), still need the assembled matrix.  Same outputs and
+ * conventions as gp_get_csr, but the unscaled values are staged in a
+ * fixed area of static device memory inside the library
+ * (GP_NOALLOC_MAX_NNZ doubles, 8 MiB, held by every device that loads the
+ * library until the process exits) instead of a context buffer.
+ *  - If val is not NULL and nnz > GP_NOALLOC_MAX_NNZ: returns
+ *    GP_ERR_UNSUPPORTED and copies nothing (use gp_get_csr).
+ *  - The first call on a device looks up the staging area's device address
+ *    (cudaGetSymbolAddress, with that device current): make that first call
+ *    before any stream capture starts.
+ *  - Every call shares the staging area, which keeps the last call's values;
+ *    each call overwrites every entry it copies out, so nothing needs
+ *    clearing.  Two calls whose GPU work overlaps (different streams or host
+ *    threads on the same device) race on the area: order them on one stream.
+ *  - Synchronises the context stream before returning. */
+#define GP_NOALLOC_MAX_NNZ (1 << 20)
+int gp_get_csr_noalloc(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
+                       int32_t* perm, int64_t sizes[2]);
+
 /* Solve K alpha = y with the last assembled K (Sec. 2.5: CG).  Rows outside
  * every bump decouple: alpha_i = y_i / sigma_n^2 there.  alpha: N doubles. */
 int gp_solve(gp_ctx* ctx, const double* y, double* alpha, const gp_opts* opts, gp_info* info);

@@ -35,7 +35,8 @@ GP_FP32_MIXED = 1
 GP_FLAG_TIME_KERNELS = 1
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
-            "gp_get_csr", "gp_solve", "gp_lml", "gp_lml_grad", "gp_lml_grad_batched", "gp_status_string"]
+            "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_lml", "gp_lml_grad", "gp_lml_grad_batched",
+            "gp_status_string"]
 
 
 class KernelDesc(ctypes.Structure):
@@ -96,6 +97,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gp_set_stream.argtypes = [vp, vp]
     lib.gp_assemble.argtypes = [vp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     lib.gp_get_csr.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
+    lib.gp_get_csr_noalloc.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     lib.gp_solve.argtypes = [vp, dp, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     lib.gp_lml.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(Info)]
@@ -105,7 +107,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                         ctypes.POINTER(Info)]
     lib.gp_status_string.argtypes = [ctypes.c_int]
     lib.gp_status_string.restype = ctypes.c_char_p
-    for name in ("gp_create", "gp_destroy", "gp_set_stream", "gp_assemble", "gp_get_csr", "gp_solve", "gp_lml",
+    for name in ("gp_create", "gp_destroy", "gp_set_stream", "gp_assemble", "gp_get_csr", "gp_get_csr_noalloc",
+                 "gp_solve", "gp_lml",
                  "gp_lml_grad", "gp_lml_grad_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
