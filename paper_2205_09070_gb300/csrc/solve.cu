@@ -32,18 +32,16 @@ __device__ void block_sum_partials(const double* part, int nblk, int width, int 
                                    double* scratch /* >= blockDim.x doubles */) {
   const int groups = blockDim.x / width;  // width <= kMaxCols < blockDim.x
   const int t = threadIdx.x % width, grp = threadIdx.x / width;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (grp < groups) {
     int b = grp;
-    for (; b + 3 * groups < nblk; b += 4 * groups) {
-      a0 += __ldcg(part + (int64_t)b * stride + t);
-      a1 += __ldcg(part + (int64_t)(b + groups) * stride + t);
-      a2 += __ldcg(part + (int64_t)(b + 2 * groups) * stride + t);
-      a3 += __ldcg(part + (int64_t)(b + 3 * groups) * stride + t);
+    for (; b + 7 * groups < nblk; b += 8 * groups) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += __ldcg(part + (int64_t)(b + u * groups) * stride + t);
     }
-    for (; b < nblk; b += groups) a0 += __ldcg(part + (int64_t)b * stride + t);
+    for (; b < nblk; b += groups) a[0] += __ldcg(part + (int64_t)b * stride + t);
   }
-  scratch[threadIdx.x] = (a0 + a1) + (a2 + a3);
+  scratch[threadIdx.x] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   __syncthreads();
   if (threadIdx.x < width) {
     double s = 0.0;
@@ -991,7 +989,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   const int ny = kUpdThreads / kq;
   const unsigned g_upd = grid_for(n, ny, c->num_sms * 8);
   const int ny_r = kUpdRThreads / kq;
-  const unsigned g_upd_r = grid_for(n, ny_r, c->num_sms * 2);
+  const unsigned g_upd_r = grid_for(n, ny_r, c->num_sms);
   if (check_every <= 0) check_every = 16;
   if (check_every > 64) check_every = 64;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
