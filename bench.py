@@ -122,16 +122,25 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+SPMM_BEGIN = "// A: Q = Khat P on the 8x1 block CSR."
+SPMM_END = "constexpr int kUpdThreads"
+
+
+def spmm_source_sha() -> str:
+    """sha256 of the SpMM kernel's source region (kernel and its helpers)."""
+    src = open(os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "solve.cu")).read()
+    a, b = src.index(SPMM_BEGIN), src.index(SPMM_END)
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
+
+
 def traffic_record(kernel: str, kp: int):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (sha256 of solve.cu); else None."""
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current SpMM source; else None (the counters are stale)."""
     path = os.path.join(ROOT, "profiles", "spmm_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    src = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "solve.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("source_sha256") != sha or rec.get("kernel") != kernel or rec.get("kp") != kp:
+    if rec.get("source_sha256") != spmm_source_sha() or rec.get("kernel") != kernel or rec.get("kp") != kp:
         return None
     return rec
 
@@ -253,7 +262,7 @@ def main():
     bytes_spmm = 8 * nnz + 8 * n_act * kp + 8 * (n_act + 1)
     achieved = bytes_spmm / (spmm_ms * 1e-3) / 1e9
     pk = peaks()
-    kname = f"k_spmm_f32<{kp // 4}>"
+    kname = f"k_bspmm_f32<{kp // 4}>"
     trec = traffic_record(kname, kp)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": trec["bytes_per_launch"] if trec else None,
