@@ -339,77 +339,6 @@ def rademacher(seed, n_probes, orig_index):
 
 
 # ----------------------------------------------------------------------------
-# Block-Jacobi preconditioner (not in the paper: a solver design choice)
-# ----------------------------------------------------------------------------
-
-def zorder_active(x, act, r_s, dim):
-    """Original indices of the active points in the row order the
-    preconditioner's blocks are cut from.
-
-    Definition: cells of edge h = r_s (1 + 1e-9), enlarged by factors of 1.25
-    until the grid over the bounding box of ALL points has at most 2^25 cells;
-    G_k = floor(ext_k / h) + 1 cells and b_k = ceil(log2 G_k) bits per axis.
-    A point's cell is c_k = clamp(floor((x_k - lo_k) / h), 0, G_k - 1); its
-    sub-cell is s_k = clamp(floor(((x_k - lo_k) / h - c_k) * 2^S), 0, 2^S - 1)
-    with S the largest of 0, 1, 2 such that sum b_k + S dim <= 32.  The key is
-    the Morton code of c (bit t of axis k at position sum over earlier (t, k)
-    pairs, x fastest) followed by the Morton code of s in the low S dim bits.
-    Active points are sorted by key, ties by original index."""
-    x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
-    act = np.asarray(act, dtype=np.int64)
-    lo = x.min(axis=0)
-    ext = x.max(axis=0) - lo
-    h = r_s * (1.0 + 1e-9)
-    while np.prod(np.floor(ext / h) + 1.0) > float(1 << 25):
-        h *= 1.25
-    G = (np.floor(ext / h) + 1.0).astype(np.int64)
-    bits = []
-    for g in G:
-        b = 0
-        while (1 << b) < g:
-            b += 1
-        bits.append(b)
-    keybits = sum(bits)
-    S = 0
-    while S < 2 and keybits + (S + 1) * dim <= 32:
-        S += 1
-    keys = []
-    for i in act:
-        u = (x[i] - lo) / h
-        c = np.clip(np.floor(u), 0, G - 1).astype(np.int64)
-        key = 0
-        pos = 0
-        for t in range(max(bits) if bits else 0):
-            for k in range(dim):
-                if t < bits[k]:
-                    key |= int((c[k] >> t) & 1) << pos
-                    pos += 1
-        sub = 0
-        if S:
-            sc = np.clip(np.floor((u - c) * (1 << S)), 0, (1 << S) - 1).astype(np.int64)
-            pos = 0
-            for t in range(S):
-                for k in range(dim):
-                    sub |= int((sc[k] >> t) & 1) << pos
-                    pos += 1
-        keys.append((key << (S * dim)) | sub)
-    idx = np.argsort(np.asarray(keys, dtype=np.int64), kind="stable")
-    return act[idx]
-
-
-def block_jacobi_factor(A, B):
-    """Dense lower-triangular L = blockdiag(chol(A_bb)) over blocks of B
-    consecutive rows (the last block may be shorter); M = L L^T is the
-    block-Jacobi preconditioner of A."""
-    n = A.shape[0]
-    L = np.zeros_like(A)
-    for r0 in range(0, n, B):
-        r1 = min(n, r0 + B)
-        L[r0:r1, r0:r1] = np.linalg.cholesky(A[r0:r1, r0:r1])
-    return L
-
-
-# ----------------------------------------------------------------------------
 # Stochastic estimators on the same probes as the GPU path
 # ----------------------------------------------------------------------------
 
@@ -450,7 +379,7 @@ def lanczos_quadrature(Khat, z, m):
 
 
 def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
-                         beta=1.0, with_grad=True, precond_block=0, probes=None):
+                         beta=1.0, with_grad=True):
     """The stochastic LML and gradient the GPU path estimates, computed densely.
 
     K splits into the active block K_a (rows inside some bump) and
@@ -462,16 +391,6 @@ def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
       tr(K^-1 K_theta) ~ (1/nv) sum_l z_l^T Khat^-1 Khat_theta z_l
                          + [inactive rows, exact: N_inact / sigma_n^2 for noise]
     where Khat_theta = D^-1/2 K_theta D^-1/2 (D held fixed).
-
-    With precond_block = B > 0 the active rows are taken in zorder_active's
-    order and M = L L^T = blockdiag(Khat_bb) over blocks of B rows.  Since
-    ln|Khat| = ln|M| + ln|L^-1 Khat L^-T| and E[z z^T] = I,
-      ln|Khat|  ~  2 sum ln L_ii + (1/nv) sum_l SLQ_m(L^-1 Khat L^-T, z_l)
-      tr(Khat^-1 Khat_theta) ~ (1/nv) sum_l (Khat^-1 L z_l)^T Khat_theta (L^-T z_l)
-    (preconditioned CG on Khat u = L z runs Lanczos on L^-1 Khat L^-T from z).
-
-    `probes`, if given, replaces the SplitMix64 probes: an (N_act x nv)
-    matrix whose rows follow the active points in ascending original index.
     Returns (lml, grad or None, info dict with the pieces)."""
     p = unpack_h(h, dim, n1, n2)
     x = np.asarray(x, dtype=np.float64)
@@ -484,31 +403,10 @@ def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
     D = np.diag(Ka).copy()
     Dm = 1.0 / np.sqrt(D)
     Khat = Ka * Dm[:, None] * Dm[None, :]
-    Z = rademacher(seed, n_probes, act) if probes is None else np.asarray(probes, dtype=np.float64)
-    n_probes = Z.shape[1]
-    # row order of the (preconditioned) solve, as positions within `act`
-    if precond_block and act.size:
-        o = np.searchsorted(act, zorder_active(x, act, p["r_s"], dim))
-    else:
-        o = np.arange(act.size)
-    Kh = Khat[np.ix_(o, o)]
-    Zo = Z[o]
-    if precond_block and act.size:
-        L = block_jacobi_factor(Kh, precond_block)
-        logdet_m = 2.0 * float(np.sum(np.log(np.diag(L))))
-        Linv_K = np.linalg.solve(L, Kh)            # L^-1 Khat
-        Ahat = np.linalg.solve(L, Linv_K.T).T      # (L^-1 (L^-1 Khat)^T)^T = L^-1 Khat L^-T
-        Ahat = 0.5 * (Ahat + Ahat.T)
-        rhs = L @ Zo
-        Zp = np.linalg.solve(L.T, Zo)
-    else:
-        logdet_m = 0.0
-        Ahat = Kh
-        rhs = Zo
-        Zp = Zo
-    quad = np.array([lanczos_quadrature(Ahat, Zo[:, l], lanczos_steps) for l in range(n_probes)]) \
+    Z = rademacher(seed, n_probes, act)
+    quad = np.array([lanczos_quadrature(Khat, Z[:, l], lanczos_steps) for l in range(n_probes)]) \
         if act.size else np.zeros(n_probes)
-    logdet = float(np.sum(np.log(D))) + logdet_m + (float(np.mean(quad)) if act.size else 0.0) \
+    logdet = float(np.sum(np.log(D))) + (float(np.mean(quad)) if act.size else 0.0) \
         + inact.size * math.log(s2)
     alpha = np.zeros_like(y)
     if act.size:
@@ -517,17 +415,16 @@ def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
     quad_form = float(y @ alpha)
     lml = -0.5 * quad_form - 0.5 * logdet
     info = {"logdet": logdet, "quad_form": quad_form, "slq_terms": quad, "n_active": int(act.size),
-            "alpha": alpha, "logdet_precond": logdet_m, "order": act[o]}
+            "alpha": alpha}
     if not with_grad:
         return lml, None, info
-    # U = Khat^-1 (L z); the estimator per parameter is (1/nv) tr(U^T Khat_theta (L^-T z)).
-    U = np.linalg.solve(Kh, rhs) if act.size else np.zeros((0, n_probes))
-    ao = act[o]
-    Dmo = Dm[o]
+    # U_hat = Khat^-1 Z; the estimator per parameter is (1/nv) tr(U_hat^T Khat_theta Z).
+    Uhat = np.linalg.solve(Khat, Z) if act.size else np.zeros((0, n_probes))
     grad = np.zeros(n_params(dim, n1, n2))
     for i, dK in dK_dtheta_all(x, h, dim, n1, n2, beta):
-        dKhat = dK[np.ix_(ao, ao)] * Dmo[:, None] * Dmo[None, :]
-        tr_act = float(np.sum(U * (dKhat @ Zp))) / n_probes if act.size else 0.0
+        dKa = dK[np.ix_(act, act)]
+        dKhat = dKa * Dm[:, None] * Dm[None, :]
+        tr_act = float(np.sum(Uhat * (dKhat @ Z))) / n_probes if act.size else 0.0
         tr_inact = float(np.sum(np.diag(dK)[inact])) / s2
         grad[i] = 0.5 * float(alpha @ (dK @ alpha)) - 0.5 * (tr_act + tr_inact)
     return lml, grad, info
