@@ -311,7 +311,7 @@ def main():
         ms64 = f0.elapsed_time(f1) / a.fp64_steps
         fp64 = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_eval": ms64, "lml": lml64,
                 "iters": info64["iters"], "lml_minus_fp32": lml - lml64,
-                "slq_stderr_fp64": 0.5 * info64["logdet_stderr"],
+                "lml_stderr_fp64": 0.5 * info64["logdet_stderr"],
                 "grad_rel_diff_max": float(np.max(np.abs(grad - grad64)) / np.max(np.abs(grad64))),
                 "speedup_fp32_mixed": (1e3 / (ms / a.steps)) / (1e3 / ms64)}
 

@@ -83,6 +83,10 @@ typedef struct {
   uint64_t seed;          /* probe stream: SplitMix64 counter l*2^40 + original point index */
   int32_t check_every;    /* iterations between host convergence checks (0: default 16) */
   int32_t flags;          /* GP_FLAG_* bits */
+  int32_t precond_block;  /* FP32_MIXED only: 0 = Jacobi scaling alone; 8, 16 or 32 = also
+                             block-Jacobi preconditioned CG, blocks of that many consecutive
+                             rows of the Morton-ordered active block (see gp_lml) */
+  int32_t reserved;       /* must be 0 */
 } gp_opts;
 
 /* gp_opts.flags: time every launch of the SpMM, pair-fill and adjoint kernels
@@ -110,13 +114,16 @@ typedef struct {
   double t_spmm_kernel_ms;    /* summed device time of those SpMM launches */
   double t_fill_kernel_ms;    /* device time of the pair-fill kernel */
   double t_adjoint_kernel_ms; /* device time of the adjoint pair kernel */
+  int32_t lanczos_iters;  /* iterations of the separate SLQ Lanczos run (preconditioned
+                             evaluations only, else 0) */
+  int32_t precond_block;  /* block size the solve used (0: none) */
 } gp_info;
 
 /* Number of hyperparameters: n_funcs*n_bumps*(dim+2) + 3. */
 int64_t gp_n_params(const gp_kernel_desc* desc);
 
 /* Default options: FP32_MIXED, 32 probes, 50 Lanczos steps, 10000 iterations,
- * rtol 1e-6, seed 0x5eed, check every 16 iterations. */
+ * rtol 1e-6, seed 0x5eed, check every 16 iterations, precond_block 32. */
 void gp_default_opts(gp_opts* opts);
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream`
@@ -167,12 +174,19 @@ int gp_get_csr(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
 int gp_get_csr_noalloc(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
                        int32_t* perm, int64_t sizes[2]);
 
-/* Solve K alpha = y with the last assembled K (Sec. 2.5: CG).  Rows outside
+/* Solve K alpha = y with the last assembled K (Sec. 2.5: CG; block-Jacobi
+ * preconditioned when opts->precond_block > 0 and K is FP32).  Rows outside
  * every bump decouple: alpha_i = y_i / sigma_n^2 there.  alpha: N doubles. */
 int gp_solve(gp_ctx* ctx, const double* y, double* alpha, const gp_opts* opts, gp_info* info);
 
 /* Assemble K and evaluate ln L (Eq. eqn:log_likelihood) with
- * ln|K| = sum ln D + SLQ(D^-1/2 K D^-1/2) + N_inactive ln sigma_n^2, D = diag K. */
+ * ln|K| = sum ln D + SLQ(D^-1/2 K D^-1/2) + N_inactive ln sigma_n^2, D = diag K.
+ * The estimator does not depend on precond_block.  With B = precond_block > 0
+ * (FP32_MIXED) the SLQ coefficients come from a run of lanczos_steps plain CG
+ * (Lanczos) iterations on [yhat, z], and the solves Khat u = [yhat, z] that the
+ * quadratic form and the gradient need run as preconditioned CG with
+ * M = blockdiag(Khat over consecutive B-row blocks of the Morton-ordered
+ * active rows), which converges in far fewer iterations. */
 int gp_lml(gp_ctx* ctx, const double* x, const double* y, int64_t n, const double* h,
            const gp_opts* opts, double* lml, gp_info* info);
 

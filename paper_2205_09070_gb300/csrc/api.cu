@@ -121,6 +121,9 @@ int check_opts(const gp_opts* o, bool need_probes) {
   if (!o) return GP_ERR_INVALID_ARG;
   if (o->precision != GP_FP64 && o->precision != GP_FP32_MIXED) return GP_ERR_INVALID_ARG;
   if (o->max_iter < 1 || !(o->cg_rtol > 0.0) || !isfinite(o->cg_rtol)) return GP_ERR_INVALID_ARG;
+  if (o->precond_block != 0 && o->precond_block != 8 && o->precond_block != 16 && o->precond_block != 32)
+    return GP_ERR_INVALID_ARG;
+  if (o->reserved != 0) return GP_ERR_INVALID_ARG;
   if (need_probes) {
     if (o->n_probes < 1 || o->n_probes > gp::kMaxProbes) return GP_ERR_INVALID_ARG;
     if (o->lanczos_steps < 1 || o->lanczos_steps > gp::kMaxLanczos) return GP_ERR_INVALID_ARG;
@@ -189,28 +192,43 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
   GP_CHECK(stage_in(c, c->y_in, y, (size_t)n, &yd));
   GP_CHECK(gp::assemble(c, xd, n, h, o->precision));
   tm.mark(1);
+  GP_CHECK(gp::precond_setup(c, o->precond_block));
   GP_CHECK(gp::inactive_terms(c, yd));
   const int nv = o->n_probes;
   const int k = 1 + nv;
   const int kp = (k + 3) / 4 * 4;
-  int iters = 0;
+  int iters = 0, lanczos_iters = 0;
   double max_rel = 0.0;
   int cg_status;
-  if (o->precision == GP_FP64)
+  if (o->precision == GP_FP64) {
     cg_status = gp::cg_run_fp64(c, k, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
                                 &iters, &max_rel);
-  else
+  } else if (c->pc_block == 0) {
+    // one plain CG run: its first lanczos_steps coefficients feed SLQ
     cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
-                           &iters, &max_rel);
+                           &iters, &max_rel, false);
+  } else {
+    // SLQ needs the Lanczos coefficients of Khat itself from the probes: a
+    // short plain run of lanczos_steps iterations (expected not to converge),
+    // reduced to SLQ terms before the preconditioned run resets the CG state
+    double lanczos_rel = 0.0;
+    const int lst = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->lanczos_steps, o->cg_rtol,
+                               o->check_every, &lanczos_iters, &lanczos_rel, false);
+    if (lst != GP_OK && lst != GP_ERR_NOT_CONVERGED) return lst;
+    GP_CHECK(gp::slq(c, nv, kp));
+    cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters,
+                           &max_rel, true);
+  }
   if (cg_status != GP_OK && cg_status != GP_ERR_NOT_CONVERGED) return cg_status;
   GP_CHECK(gp::quad_form(c, yd, kp));
-  GP_CHECK(gp::slq(c, nv, kp));
+  if (o->precision == GP_FP64 || c->pc_block == 0) GP_CHECK(gp::slq(c, nv, kp));
   tm.mark(2);
   if (grad) GP_CHECK(gp::adjoint(c, nv, kp));
   tm.mark(3);
   gp::AsmScalars hs;
   GP_CHECK(read_scalars(c, &hs));
   if (c->n_act > 0 && hs.status != GP_OK) return hs.status;
+  if (c->pc_block > 0 && hs.pc_status != GP_OK) return hs.pc_status;
   const double s2 = c->sigma2;
   const double n_in = (double)(n - c->n_act);
   const double logdet = hs.sum_log_d * (c->n_act > 0) + hs.slq_mean + n_in * log(s2);
@@ -257,6 +275,8 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
     info->cell_size = c->grid.h;
     info->n_cells = c->grid.ncells;
     info->kp = o->precision == GP_FP64 ? k : kp;
+    info->lanczos_iters = lanczos_iters;
+    info->precond_block = c->pc_block;
     fill_counters(c, info);
   }
   return cg_status;
@@ -281,6 +301,8 @@ void gp_default_opts(gp_opts* o) {
   o->seed = 0x5eedull;
   o->check_every = 16;
   o->flags = 0;
+  o->precond_block = 32;
+  o->reserved = 0;
 }
 
 int gp_create(gp_ctx** out, const gp_kernel_desc* desc, int device, void* stream) {
@@ -329,7 +351,7 @@ int gp_destroy(gp_ctx* c) {
                         &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
                         &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
-                        &c->bval,   &c->slq_g};
+                        &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -413,13 +435,14 @@ int gp_solve(gp_ctx* c, const double* y, double* alpha, const gp_opts* o, gp_inf
   tm.mark(0);
   const double* yd = nullptr;
   GP_CHECK(stage_in(c, c->y_in, y, (size_t)c->n, &yd));
+  GP_CHECK(gp::precond_setup(c, o->precond_block));
   int iters = 0;
   double max_rel = 0.0;
   int st;
   if (c->precision == GP_FP64)
     st = gp::cg_run_fp64(c, 1, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel);
   else
-    st = gp::cg_run(c, 1, 4, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel);
+    st = gp::cg_run(c, 1, 4, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel, true);
   if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
   double* out = alpha;
   const bool dev = gp::is_device_ptr(alpha);
@@ -444,6 +467,7 @@ int gp_solve(gp_ctx* c, const double* y, double* alpha, const gp_opts* o, gp_inf
     info->cell_size = c->grid.h;
     info->n_cells = c->grid.ncells;
     info->kp = 4;
+    info->precond_block = c->pc_block;
     fill_counters(c, info);
   }
   return st;
@@ -491,6 +515,9 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
       info->t_assemble_ms += inf.t_assemble_ms;
       info->t_solve_ms += inf.t_solve_ms;
       info->t_grad_ms += inf.t_grad_ms;
+      info->launches += inf.launches;
+      info->lanczos_iters = inf.lanczos_iters > info->lanczos_iters ? inf.lanczos_iters : info->lanczos_iters;
+      info->precond_block = inf.precond_block > info->precond_block ? inf.precond_block : info->precond_block;
     }
   }
   return status;

@@ -64,7 +64,8 @@ struct CgState {
   double tol2;             // cg_rtol^2
   // FP32 batched path: iteration-parity copies, so that one block of a
   // kernel can publish iteration t+1 while the others still read iteration t
-  double rrp[2][kMaxCols];
+  double rrp[2][kMaxCols];   // rho = r^T M^-1 r (= |r|^2 without preconditioning)
+  double crr[2][kMaxCols];   // |r|^2, for the convergence test
   int donep[2][kMaxCols];
   int fin[2];
 };
@@ -87,7 +88,9 @@ struct AsmScalars {
   unsigned ticket2;
   unsigned ticket3;
   unsigned ticket4;
+  unsigned ticket5;
   int status;
+  int pc_status;           // GP_ERR_NOT_SPD if a diagonal block failed to factor
 };
 
 struct DevBuf {
@@ -122,6 +125,11 @@ struct gp_ctx {
   // 8x1 block CSR of the FP32 path (rows 8b..8b+7 per block row)
   gp::DevBuf bcnt, brp, bcol, bmask, bval;
   int64_t nblk = 0, nbent = 0;
+  // block-Jacobi preconditioner (FP32 path): M^-1 per block of pc_block rows
+  // (FP32, pc_block^2 each); Z = M^-1 R of the preconditioned CG
+  gp::DevBuf pc_Minv, pc_part, Z;
+  int pc_block = 0;
+  int64_t pc_nblk = 0;
   gp::DevBuf X, R, P, Q, zbits;
   gp::DevBuf part_a, part_b, part_c, hist_alpha, hist_beta;
   gp::DevBuf g, grad_part, grad_bump;
@@ -161,12 +169,16 @@ int scan_i32_to_i64(gp_ctx* c, const int32_t* in, int64_t* out, int64_t n);
 
 // assemble.cu
 int assemble(gp_ctx* c, const double* x_dev, int64_t n, const double* h, int precision);
+
+// precond.cu: inverses of the diagonal blocks of the assembled Khat
+// (pc_block rows per block, FP32 path only); pc_block == 0 switches it off.
+int precond_setup(gp_ctx* c, int pc_block);
 int csr_unscaled(gp_ctx* c, double* val_out_dev);
 
 // solve.cu (cg_run: FP32 batched CG on the 8x1 block CSR)
 int cg_run(gp_ctx* c, int k, int kp, const double* y_dev, int n_probes, uint64_t seed,
            int lanczos_steps, int max_iter, double rtol, int check_every,
-           int* iters_out, double* max_rel_resid);
+           int* iters_out, double* max_rel_resid, bool use_pc);
 int cg_run_fp64(gp_ctx* c, int k, const double* y_dev, int n_probes, uint64_t seed,
                 int lanczos_steps, int max_iter, double rtol, int check_every,
                 int* iters_out, double* max_rel_resid);

@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
         st->rr0[c] = r0;
         st->rrp[0][c] = r0;
         st->rrp[1][c] = r0;
+        st->crr[0][c] = r0;
+        st->crr[1][c] = r0;
         st->donep[0][c] = !(r0 > 0.0);
         st->donep[1][c] = st->donep[0][c];
         st->steps[c] = 0;
@@ -482,19 +484,167 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, i
   if (threadIdx.x < kp) part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = red[threadIdx.x / 4][threadIdx.x % 4];
 }
 
+// B with the block-Jacobi preconditioner M (diagonal blocks of B rows of
+// Khat; B divides the 32-row tile, so a tile holds whole blocks):
+//   INIT:  Z = M^-1 R written to P (the first search direction)
+//   else:  R -= alpha Q, Z = M^-1 R
+// and per-block partials of rho = r^T z and |r|^2 per column.  The block has
+// 32 kq threads.  Loads and stores go tile-linear through shared memory (row
+// r = t / kq, float4 slot t % kq); the block products run with warp w on
+// float4 slot w and lane r on row r, so each thread's column sums stay in one
+// slot across tiles and reduce with warp shuffles at the end.
+constexpr int kPcTile = 32;
+constexpr int kPcMaxThreads = kPcTile * gp::kMaxCols / 4;
+
+template <bool INIT>
+__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, int B, int it,
+                                                             const float4* __restrict__ Q, float4* __restrict__ R,
+                                                             float4* __restrict__ Z, const float* __restrict__ Minv,
+                                                             double* __restrict__ part_rho,
+                                                             double* __restrict__ part_rr, const gp::CgState* st) {
+  if (!INIT && st->fin[it & 1]) return;
+  __shared__ float4 Rs[kPcMaxThreads];
+  __shared__ float4 Zs[kPcMaxThreads];
+  __shared__ float Ms[kPcTile * (kPcTile + 1)];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int nthr = kPcTile * kq;
+  const int64_t ntiles = (n + kPcTile - 1) / kPcTile;
+  const int64_t nrows_pc = (n + B - 1) / B * B;  // rows covered by stored blocks
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!INIT) {
+    const int q = t % kq;
+    a = make_float4((float)st->alpha[4 * q], (float)st->alpha[4 * q + 1], (float)st->alpha[4 * q + 2],
+                    (float)st->alpha[4 * q + 3]);
+  }
+  gpd::Dot2 rz[4], rr[4];
+  const int kb = (lane / B) * B;          // first tile row of this lane's block
+  const float* mrow = Ms + lane * (B + 1);  // this lane's row of M^-1
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kPcTile;
+    // M^-1 rows of the tile, padded to B + 1 floats per row (conflict-free
+    // column walks: lane r reads word r (B + 1) + k)
+    for (int e = t; e < kPcTile * B; e += nthr) {
+      const int r = e / B, k = e % B;
+      Ms[r * (B + 1) + k] = r0 + r < nrows_pc ? Minv[(r0 + r) * B + k] : 0.f;
+    }
+    {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 + t / kq < n) {
+        v = R[r0 * kq + t];
+        if (!INIT) {
+          const float4 qv = Q[r0 * kq + t];
+          v.x = fmaf(-a.x, qv.x, v.x);
+          v.y = fmaf(-a.y, qv.y, v.y);
+          v.z = fmaf(-a.z, qv.z, v.z);
+          v.w = fmaf(-a.w, qv.w, v.w);
+          R[r0 * kq + t] = v;
+        }
+      }
+      Rs[t] = v;
+    }
+    __syncthreads();
+    {
+      const float4 rv = Rs[lane * kq + w];
+      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < B; ++k) {
+        const float m = mrow[k];
+        const float4 x = Rs[(kb + k) * kq + w];
+        z.x = fmaf(m, x.x, z.x);
+        z.y = fmaf(m, x.y, z.y);
+        z.z = fmaf(m, x.z, z.z);
+        z.w = fmaf(m, x.w, z.w);
+      }
+      Zs[lane * kq + w] = z;
+      rz[0].add(rv.x, z.x);
+      rz[1].add(rv.y, z.y);
+      rz[2].add(rv.z, z.z);
+      rz[3].add(rv.w, z.w);
+      rr[0].add(rv.x, rv.x);
+      rr[1].add(rv.y, rv.y);
+      rr[2].add(rv.z, rv.z);
+      rr[3].add(rv.w, rv.w);
+    }
+    __syncthreads();
+    if (r0 + t / kq < n) Z[r0 * kq + t] = Zs[t];
+    __syncthreads();
+  }
+  // rows beyond n hold zeros in Rs, so they added nothing above
+  double v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = rz[j].value();
+    v[4 + j] = rr[j].value();
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
+  if (lane == 0) {
+    const int kp = 4 * kq;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      part_rho[(int64_t)blockIdx.x * kp + 4 * w + j] = v[j];
+      part_rr[(int64_t)blockIdx.x * kp + 4 * w + j] = v[4 + j];
+    }
+  }
+}
+
+// Preconditioned start: rho_0 = r^T M^-1 r drives alpha / beta, |r_0|^2 the
+// convergence test (|r| <= rtol |r_0| on the true residual).
+__global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restrict__ part_rho,
+                                                          const double* __restrict__ part_rr, int np, int k, int kp,
+                                                          gp::CgState* st) {
+  __shared__ double scratch[kRedThreads];
+  __shared__ double rho[gp::kMaxCols], rr[gp::kMaxCols];
+  __shared__ int any_running;
+  block_sum_partials(part_rho, np, kp, kp, rho, scratch);
+  block_sum_partials(part_rr, np, kp, kp, rr, scratch);
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  if (threadIdx.x < gp::kMaxCols) {
+    const int c = threadIdx.x;
+    const double r0 = c < k ? rr[c] : 0.0;
+    const double p0 = c < k ? rho[c] : 0.0;
+    st->rr0[c] = r0;
+    st->crr[0][c] = r0;
+    st->crr[1][c] = r0;
+    st->rrp[0][c] = p0;
+    st->rrp[1][c] = p0;
+    const bool done = !(r0 > 0.0) || !(p0 > 0.0);
+    st->donep[0][c] = done;
+    st->donep[1][c] = done;
+    if (c < k && !done) atomicOr(&any_running, 1);
+    if (c < k && (!isfinite(r0) || !isfinite(p0))) {
+      st->status = GP_ERR_NOT_SPD;
+      st->bad_col = c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int f = !any_running || st->status != GP_OK;
+    st->fin[0] = f;
+    st->fin[1] = f;
+    st->finished = f;
+  }
+}
+
 // beta of iteration it (one block): |r_new|^2 from the partials, convergence,
 // and the iteration-(it+1) scalars in parity slot (it+1)&1.
-__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part_rr, int nrr, int k, int kp,
-                                                         int it, gp::CgState* st, double* hist_beta, int m_hist) {
+__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part_rr,
+                                                         const double* __restrict__ part_crr, int nrr, int k,
+                                                         int kp, int it, gp::CgState* st, double* hist_beta,
+                                                         int m_hist) {
   const int cur = it & 1, nxt = (it + 1) & 1;
   if (st->fin[cur]) {
     if (threadIdx.x == 0) st->fin[nxt] = 1;
     return;
   }
   __shared__ double scratch[kRedThreads];
-  __shared__ double rrn[gp::kMaxCols];
+  __shared__ double rrn[gp::kMaxCols];   // rho_new = r^T M^-1 r
+  __shared__ double crn[gp::kMaxCols];   // |r|^2 (the same as rho_new without a preconditioner)
   __shared__ int any_running;
   block_sum_partials(part_rr, nrr, kp, kp, rrn, scratch);
+  if (part_crr) block_sum_partials(part_crr, nrr, kp, kp, crn, scratch);
+  else if (threadIdx.x < kp) crn[threadIdx.x] = rrn[threadIdx.x];
   if (threadIdx.x == 0) any_running = 0;
   __syncthreads();
   if (threadIdx.x < kp) {
@@ -505,14 +655,15 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restric
     if (!was_done) {
       b = rrn[c] / st->rrp[cur][c];
       if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
-      done = rrn[c] <= st->tol2 * st->rr0[c];
-      if (!isfinite(rrn[c])) {
+      done = crn[c] <= st->tol2 * st->rr0[c];
+      if (!isfinite(rrn[c]) || !isfinite(crn[c])) {
         st->status = GP_ERR_NOT_SPD;
         st->bad_col = c;
       }
     }
     st->beta[c] = b;
     st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn[c];
+    st->crr[nxt][c] = was_done ? st->crr[cur][c] : crn[c];
     st->donep[nxt][c] = done;
     if (c < k && !done) atomicOr(&any_running, 1);
   }
@@ -525,8 +676,8 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restric
   }
 }
 
-// C: X += alpha P_old, P = R + beta P_old (runs for iteration it unless the
-// run had already finished before it).
+// C: X += alpha P_old, P = Z + beta P_old with Z = M^-1 R (Z = R without a
+// preconditioner); runs for iteration it unless the run had already finished.
 __global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, int it, float4* __restrict__ X,
                                                             const float4* __restrict__ R, float4* __restrict__ P,
                                                             const gp::CgState* st) {
@@ -950,7 +1101,7 @@ int read_state(gp_ctx* c, gp::CgState* host) {
 namespace gp {
 
 int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
-           int check_every, int* iters_out, double* max_rel) {
+           int check_every, int* iters_out, double* max_rel, bool use_pc) {
   const int64_t n = c->n_act;
   *iters_out = 0;
   *max_rel = 0.0;
@@ -978,6 +1129,26 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     GP_LAUNCH_CHECK();
     c->launches += 1;
   }
+  // block-Jacobi preconditioned CG: Z = M^-1 R, beta from r^T z, stop on |r|
+  const bool pc = use_pc && c->pc_block > 0;
+  const int kq = kp / 4;
+  unsigned g_pc = 0;
+  if (pc) {
+    int per_sm = 0;
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_r_pc<false>, kPcTile * kq, 0));
+    if (per_sm < 1) per_sm = 1;
+    g_pc = grid_for(n, kPcTile, c->num_sms * per_sm);
+    GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
+    GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * kp * sizeof(double)));
+    GP_CHECK(ensure(c, c->part_c, (size_t)g_pc * kp * sizeof(double)));
+    k_upd_r_pc<true><<<g_pc, kPcTile * kq, 0, c->stream>>>(n, kq, c->pc_block, 0, nullptr, (float4*)c->R.p,
+                                                           (float4*)c->P.p, (const float*)c->pc_Minv.p,
+                                                           (double*)c->part_b.p, (double*)c->part_c.p, st);
+    k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (const double*)c->part_c.p, (int)g_pc,
+                                                 k, kp, st);
+    GP_LAUNCH_CHECK();
+    c->launches += 2;
+  }
   const int64_t nblk = c->nblk;
   const size_t spmm_smem = (size_t)kSpmmWarps * 2 * kChunk * (kp + kBR) * sizeof(float);
   GP_CUDA(cudaFuncSetAttribute(spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmm_smem));
@@ -985,7 +1156,6 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spmm_per_sm, spmm, kSpmmThreads, spmm_smem));
   if (spmm_per_sm < 1) spmm_per_sm = 1;
   const unsigned g_spmm = grid_for(nblk, kSpmmWarps, c->num_sms * spmm_per_sm);
-  const int kq = kp / 4;
   const int ny = kUpdThreads / kq;
   const unsigned g_upd = grid_for(n, ny, c->num_sms * 8);
   const int ny_r = kUpdRThreads / kq;
@@ -1007,12 +1177,21 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
       if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t + 1], c->stream));
       k_cg_alpha<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, it, st,
                                                    (double*)c->hist_alpha.p, m_hist);
-      k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
-                                                           (double*)c->part_b.p, st);
-      k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, it, st,
-                                                  (double*)c->hist_beta.p, m_hist);
-      k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (float4*)c->X.p, (const float4*)c->R.p,
-                                                         (float4*)c->P.p, st);
+      if (pc) {
+        k_upd_r_pc<false><<<g_pc, kPcTile * kq, 0, c->stream>>>(
+            n, kq, c->pc_block, it, (const float4*)c->Q.p, (float4*)c->R.p, (float4*)c->Z.p,
+            (const float*)c->pc_Minv.p, (double*)c->part_b.p, (double*)c->part_c.p, st);
+        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (const double*)c->part_c.p,
+                                                    (int)g_pc, k, kp, it, st, (double*)c->hist_beta.p, m_hist);
+      } else {
+        k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                             (double*)c->part_b.p, st);
+        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, nullptr, (int)g_upd_r, k, kp, it,
+                                                    st, (double*)c->hist_beta.p, m_hist);
+      }
+      k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (float4*)c->X.p,
+                                                         (const float4*)(pc ? c->Z.p : c->R.p), (float4*)c->P.p,
+                                                         st);
     }
     GP_LAUNCH_CHECK();
     c->launches += 5 * check_every;
@@ -1032,7 +1211,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   bool all_done = true;
   const int par = hs.iter & 1;
   for (int q = 0; q < k; ++q) {
-    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.rrp[par][q] / hs.rr0[q]));
+    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.crr[par][q] / hs.rr0[q]));
     all_done = all_done && hs.donep[par][q];
   }
   *max_rel = mr;

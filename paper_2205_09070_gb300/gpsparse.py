@@ -47,7 +47,8 @@ class KernelDesc(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_probes", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("cg_rtol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("precond_block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -58,7 +59,8 @@ class Info(ctypes.Structure):
                 ("t_grad_ms", ctypes.c_double), ("cell_size", ctypes.c_double), ("n_cells", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("n_spmm", ctypes.c_int32), ("kp", ctypes.c_int32),
                 ("t_spmm_kernel_ms", ctypes.c_double), ("t_fill_kernel_ms", ctypes.c_double),
-                ("t_adjoint_kernel_ms", ctypes.c_double)]
+                ("t_adjoint_kernel_ms", ctypes.c_double), ("lanczos_iters", ctypes.c_int32),
+                ("precond_block", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -68,15 +68,17 @@ def test_assembly_pattern_bit_exact_and_values(lib, case, prec):
     gp.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_solve_matches_dense(lib, prec):
+@pytest.mark.parametrize("prec,B", [("fp64", 0), ("fp32", 0), ("fp32", 8), ("fp32", 16), ("fp32", 32)])
+def test_solve_matches_dense(lib, prec, B):
     p = W.small_2d(seed=1)
     gp = lib.GP(p.dim, p.n1, p.n2, p.beta)
     x = torch.as_tensor(p.x, device="cuda")
     y = torch.as_tensor(p.y, device="cuda")
     gp.assemble(x, p.h, precision=prec)
     rtol = 1e-10 if prec == "fp64" else 1e-6
-    alpha, info = gp.solve(y, torch.zeros_like(y), lib.default_opts(precision=prec, cg_rtol=rtol))
+    alpha, info = gp.solve(y, torch.zeros_like(y), lib.default_opts(precision=prec, cg_rtol=rtol, precond_block=B))
+    assert info["precond_block"] == (B if prec == "fp32" else 0)
+    print(prec, B, "iters", info["iters"], "max_rel", info["max_rel_resid"])
     K = O.dense_K(p.x, p.h, p.dim, p.n1, p.n2)
     ref = np.linalg.solve(K, p.y)
     a = alpha.cpu().numpy()
@@ -86,18 +88,23 @@ def test_solve_matches_dense(lib, prec):
     gp.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_lml_and_grad_same_probes(lib, prec):
+@pytest.mark.parametrize("prec,B", [("fp64", 0), ("fp32", 0), ("fp32", 8), ("fp32", 16), ("fp32", 32)])
+def test_lml_and_grad_same_probes(lib, prec, B):
+    """Same probes: the GPU's SLQ log-determinant and Hutchinson gradient
+    against the oracle's dense evaluation of the same estimator.  The
+    estimator does not depend on the solver: B = 0 runs one plain CG, B > 0 a
+    short Lanczos run for SLQ plus block-Jacobi preconditioned CG."""
     p = W.small_2d(seed=1)
     nv, m, seed = 16, 40, 1234
     gp = lib.GP(p.dim, p.n1, p.n2, p.beta)
     x = torch.as_tensor(p.x, device="cuda")
     y = torch.as_tensor(p.y, device="cuda")
     rtol = 1e-10 if prec == "fp64" else 1e-6
-    opts = lib.default_opts(precision=prec, n_probes=nv, lanczos_steps=m, cg_rtol=rtol, seed=seed)
+    opts = lib.default_opts(precision=prec, n_probes=nv, lanczos_steps=m, cg_rtol=rtol, seed=seed,
+                            precond_block=B)
     lml, grad, info = gp.lml_grad(x, y, p.h, opts)
     ref, gref, rinfo = O.lml_grad_same_probes(p.x, p.y, p.h, p.dim, p.n1, p.n2, nv, m, seed)
-    print(prec, "lml", lml, ref, "logdet", info["logdet"], rinfo["logdet"], "quad", info["quad_form"],
+    print(prec, B, "lml", lml, ref, "logdet", info["logdet"], rinfo["logdet"], "quad", info["quad_form"],
           rinfo["quad_form"], "iters", info["iters"])
     assert info["quad_form"] == pytest.approx(rinfo["quad_form"], rel=1e-9 if prec == "fp64" else 1e-5)
     assert info["logdet"] == pytest.approx(rinfo["logdet"], rel=1e-7 if prec == "fp64" else 1e-5)
@@ -122,4 +129,32 @@ def test_gradient_identities_hold_on_gpu(lib):
     assert lhs == pytest.approx(0.5 * info["quad_form"] - 0.5 * p.n, rel=1e-4)
     amp = [(b * (p.dim + 2)) + p.dim + 1 for b in range(p.n1 * p.n2)]
     assert sum(p.h[i] * g[i] for i in amp) == pytest.approx(2 * P["A"] * g[-2], rel=1e-4, abs=1e-6 * abs(g).max())
+    gp.close()
+
+
+def test_preconditioning_cuts_iterations_not_the_estimate(lib):
+    """Block-Jacobi PCG changes the solver only: the estimate moves by no more
+    than the solver tolerance allows, the SLQ terms come from the same
+    lanczos_steps Lanczos iterations, and the solve needs fewer iterations."""
+    p = W.grad_3d(seed=3, n=4000)
+    gp = lib.GP(p.dim, p.n1, p.n2, p.beta)
+    x = torch.as_tensor(p.x, device="cuda")
+    y = torch.as_tensor(p.y, device="cuda")
+    res = {}
+    for B in (0, 8, 16, 32):
+        o = lib.default_opts(precision="fp32", n_probes=16, lanczos_steps=30, cg_rtol=1e-6, seed=17,
+                             precond_block=B)
+        res[B] = gp.lml_grad(x, y, p.h, o)
+    l0, g0, i0 = res[0]
+    assert i0["lanczos_iters"] == 0 and i0["precond_block"] == 0
+    scale = np.abs(g0) + 1e-3 * np.abs(g0).max()
+    for B in (8, 16, 32):
+        l, g, info = res[B]
+        print(B, "iters", info["iters"], "vs", i0["iters"], "lanczos", info["lanczos_iters"])
+        assert info["precond_block"] == B
+        assert info["lanczos_iters"] == min(30, i0["iters"])
+        assert info["iters"] < i0["iters"]
+        assert info["logdet"] == pytest.approx(i0["logdet"], rel=1e-5)
+        assert info["quad_form"] == pytest.approx(i0["quad_form"], rel=1e-5)
+        assert np.max(np.abs(g - g0) / scale) < 2e-3
     gp.close()
