@@ -296,9 +296,11 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     ChunkPos nx1 = next_chunk(cur, brp);
     issue(cur, col_of(cur), 0);
     int j1 = col_of(nx1);
-    float4 acc[kBR];
+    // accumulators as float2 pairs (columns x,y and z,w of the lane's float4)
+    // for the packed two-wide FP32 FMA, which rounds each half like fmaf
+    float2 acc[2 * kBR];
 #pragma unroll
-    for (int r = 0; r < kBR; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < 2 * kBR; ++r) acc[r] = make_float2(0.f, 0.f);
     int buf = 0;
     while (cur.bb < b1) {
       const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp) : nx1;
@@ -319,12 +321,12 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
           const float4 v0 = *(const float4*)(sv + src * kBR);
           const float4 v1 = *(const float4*)(sv + src * kBR + 4);
           const float vv[kBR] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+          const float2 plo = make_float2(pj.x, pj.y), phi = make_float2(pj.z, pj.w);
 #pragma unroll
           for (int r = 0; r < kBR; ++r) {
-            acc[r].x = fmaf(vv[r], pj.x, acc[r].x);
-            acc[r].y = fmaf(vv[r], pj.y, acc[r].y);
-            acc[r].z = fmaf(vv[r], pj.z, acc[r].z);
-            acc[r].w = fmaf(vv[r], pj.w, acc[r].w);
+            const float2 v2 = make_float2(vv[r], vv[r]);
+            acc[2 * r] = __ffma2_rn(v2, plo, acc[2 * r]);
+            acc[2 * r + 1] = __ffma2_rn(v2, phi, acc[2 * r + 1]);
           }
         }
       }
@@ -332,15 +334,13 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
       if (cur.base + kChunk >= e) {
         // last chunk of block row cur.bb: group 0 adds the other groups' sums
 #pragma unroll
-        for (int r = 0; r < kBR; ++r) {
-          const float4 q0 = acc[r];
+        for (int r = 0; r < 2 * kBR; ++r) {
+          const float2 q0 = acc[r];
 #pragma unroll
           for (int g2 = 1; g2 < NG; ++g2) {
             const int src = gl + g2 * G;
             acc[r].x += __shfl_sync(kFull, q0.x, src);
             acc[r].y += __shfl_sync(kFull, q0.y, src);
-            acc[r].z += __shfl_sync(kFull, q0.z, src);
-            acc[r].w += __shfl_sync(kFull, q0.w, src);
           }
         }
         if (grp == 0) {
@@ -348,17 +348,18 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
           for (int r = 0; r < kBR; ++r) {
             const int64_t row = cur.bb * kBR + r;
             if (row < n) {
-              Q[row * G + gl] = acc[r];
+              const float4 qv = make_float4(acc[2 * r].x, acc[2 * r].y, acc[2 * r + 1].x, acc[2 * r + 1].y);
+              Q[row * G + gl] = qv;
               const float4 pp = __ldg(P + row * G + gl);
-              pq0.add(pp.x, acc[r].x);
-              pq1.add(pp.y, acc[r].y);
-              pq2.add(pp.z, acc[r].z);
-              pq3.add(pp.w, acc[r].w);
+              pq0.add(pp.x, qv.x);
+              pq1.add(pp.y, qv.y);
+              pq2.add(pp.z, qv.z);
+              pq3.add(pp.w, qv.w);
             }
           }
         }
 #pragma unroll
-        for (int r = 0; r < kBR; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int r = 0; r < 2 * kBR; ++r) acc[r] = make_float2(0.f, 0.f);
       }
       cur = nx1;
       nx1 = nx2;
@@ -488,26 +489,46 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, i
 // Khat; B divides the 32-row tile, so a tile holds whole blocks):
 //   INIT:  Z = M^-1 R written to P (the first search direction)
 //   else:  R -= alpha Q, Z = M^-1 R
-// and per-block partials of rho = r^T z and |r|^2 per column.  The block has
-// 32 kq threads.  Loads and stores go tile-linear through shared memory (row
-// r = t / kq, float4 slot t % kq); the block products run with warp w on
-// float4 slot w and lane r on row r, so each thread's column sums stay in one
-// slot across tiles and reduce with warp shuffles at the end.
+// and per-block partials of rho = r^T z (columns 0..kp-1) and |r|^2
+// (columns kp..2kp-1) in one row of 2 kp doubles per block.
+//
+// A block of 32 kq threads walks its tiles with a 3-stage cp.async pipeline
+// (tiles i+1 and i+2 in flight while tile i is computed).  Thread t copies
+// and updates element t of the tile-linear layout (row t / kq, float4 slot
+// t % kq), so it can use its own R and Q right after its own copies land.
+// The block product runs with warp w on float4 slot w and lane r on row r,
+// reading row r of M^-1 as float4s from rows padded to B + 4 floats, so each
+// thread's column sums stay in one slot across tiles and reduce with warp
+// shuffles at the end.
 constexpr int kPcTile = 32;
 constexpr int kPcMaxThreads = kPcTile * gp::kMaxCols / 4;
+constexpr int kPcStages = 3;
+
+__device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int nbytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+
+size_t pc_smem_bytes(int kq, int B) {
+  const size_t nthr = (size_t)kPcTile * kq;
+  return 16 * nthr * (2 * kPcStages + 1) + 4 * (size_t)kPcStages * kPcTile * (B + 4);
+}
 
 template <bool INIT>
 __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, int B, int it,
                                                              const float4* __restrict__ Q, float4* __restrict__ R,
                                                              float4* __restrict__ Z, const float* __restrict__ Minv,
-                                                             double* __restrict__ part_rho,
-                                                             double* __restrict__ part_rr, const gp::CgState* st) {
+                                                             double* __restrict__ part, const gp::CgState* st) {
   if (!INIT && st->fin[it & 1]) return;
-  __shared__ float4 Rs[kPcMaxThreads];
-  __shared__ float4 Zs[kPcMaxThreads];
-  __shared__ float Ms[kPcTile * (kPcTile + 1)];
+  extern __shared__ float4 pc_smem[];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nthr = kPcTile * kq;
+  const int ldm = B + 4;
+  float4* Rs = pc_smem;                         // kPcStages x nthr
+  float4* Qs = Rs + kPcStages * nthr;           // kPcStages x nthr
+  float4* Zs = Qs + kPcStages * nthr;           // nthr
+  float* Ms = (float*)(Zs + nthr);              // kPcStages x 32 x ldm
   const int64_t ntiles = (n + kPcTile - 1) / kPcTile;
   const int64_t nrows_pc = (n + B - 1) / B * B;  // rows covered by stored blocks
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -516,44 +537,62 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
     a = make_float4((float)st->alpha[4 * q], (float)st->alpha[4 * q + 1], (float)st->alpha[4 * q + 2],
                     (float)st->alpha[4 * q + 3]);
   }
-  gpd::Dot2 rz[4], rr[4];
-  const int kb = (lane / B) * B;          // first tile row of this lane's block
-  const float* mrow = Ms + lane * (B + 1);  // this lane's row of M^-1
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * kPcTile;
-    // M^-1 rows of the tile, padded to B + 1 floats per row (conflict-free
-    // column walks: lane r reads word r (B + 1) + k)
-    for (int e = t; e < kPcTile * B; e += nthr) {
-      const int r = e / B, k = e % B;
-      Ms[r * (B + 1) + k] = r0 + r < nrows_pc ? Minv[(r0 + r) * B + k] : 0.f;
-    }
-    {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r0 + t / kq < n) {
-        v = R[r0 * kq + t];
-        if (!INIT) {
-          const float4 qv = Q[r0 * kq + t];
-          v.x = fmaf(-a.x, qv.x, v.x);
-          v.y = fmaf(-a.y, qv.y, v.y);
-          v.z = fmaf(-a.z, qv.z, v.z);
-          v.w = fmaf(-a.w, qv.w, v.w);
-          R[r0 * kq + t] = v;
-        }
+  auto issue = [&](int64_t tile, int s) {
+    if (tile < ntiles) {
+      const int64_t r0 = tile * kPcTile;
+      const bool ok = r0 + t / kq < n;
+      const int64_t src = ok ? r0 * kq + t : 0;
+      cp_async16_zfill(Rs + s * nthr + t, R + src, ok);
+      if (!INIT) cp_async16_zfill(Qs + s * nthr + t, Q + src, ok);
+      const int c4n = B / 4;
+      for (int e = t; e < kPcTile * c4n; e += nthr) {
+        const int r = e / c4n, c4 = e - r * c4n;
+        const bool okm = r0 + r < nrows_pc;
+        const float* srcm = Minv + (okm ? (r0 + r) * B + 4 * c4 : 0);
+        cp_async16_zfill(Ms + (s * kPcTile + r) * ldm + 4 * c4, srcm, okm);
       }
-      Rs[t] = v;
+    }
+    cp_async_commit();  // empty groups past the end keep the group count uniform
+  };
+  gpd::Dot2 rz[4], rr[4];
+  const int kb = (lane / B) * B;  // first tile row of this lane's block
+  int64_t tile = blockIdx.x;
+  issue(tile, 0);
+  issue(tile + gridDim.x, 1);
+  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+    const int s = i % kPcStages;
+    issue(tile + 2 * (int64_t)gridDim.x, (i + 2) % kPcStages);
+    cp_async_wait<2>();  // this thread's copies of tile i have landed
+    const int64_t r0 = tile * kPcTile;
+    const bool ok = r0 + t / kq < n;
+    if (!INIT) {
+      float4 v = Rs[s * nthr + t];
+      const float4 qv = Qs[s * nthr + t];
+      v.x = fmaf(-a.x, qv.x, v.x);
+      v.y = fmaf(-a.y, qv.y, v.y);
+      v.z = fmaf(-a.z, qv.z, v.z);
+      v.w = fmaf(-a.w, qv.w, v.w);
+      Rs[s * nthr + t] = v;
+      if (ok) R[r0 * kq + t] = v;
     }
     __syncthreads();
     {
-      const float4 rv = Rs[lane * kq + w];
-      float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int k = 0; k < B; ++k) {
-        const float m = mrow[k];
-        const float4 x = Rs[(kb + k) * kq + w];
-        z.x = fmaf(m, x.x, z.x);
-        z.y = fmaf(m, x.y, z.y);
-        z.z = fmaf(m, x.z, z.z);
-        z.w = fmaf(m, x.w, z.w);
+      const float4* Rt = Rs + s * nthr;
+      const float* mrow = Ms + (s * kPcTile + lane) * ldm;
+      const float4 rv = Rt[lane * kq + w];
+      float2 zlo = make_float2(0.f, 0.f), zhi = make_float2(0.f, 0.f);
+      for (int k = 0; k < B; k += 4) {
+        const float4 m = *(const float4*)(mrow + k);
+        const float mk[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 x = Rt[(kb + k + u) * kq + w];
+          const float2 m2 = make_float2(mk[u], mk[u]);
+          zlo = __ffma2_rn(m2, make_float2(x.x, x.y), zlo);
+          zhi = __ffma2_rn(m2, make_float2(x.z, x.w), zhi);
+        }
       }
+      const float4 z = make_float4(zlo.x, zlo.y, zhi.x, zhi.y);
       Zs[lane * kq + w] = z;
       rz[0].add(rv.x, z.x);
       rz[1].add(rv.y, z.y);
@@ -565,10 +604,10 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
       rr[3].add(rv.w, rv.w);
     }
     __syncthreads();
-    if (r0 + t / kq < n) Z[r0 * kq + t] = Zs[t];
-    __syncthreads();
+    if (ok) Z[r0 * kq + t] = Zs[t];
   }
-  // rows beyond n hold zeros in Rs, so they added nothing above
+  cp_async_wait<0>();
+  // rows beyond n were filled with zeros, so they added nothing above
   double v[8];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -580,30 +619,29 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
   if (lane == 0) {
     const int kp = 4 * kq;
+    double* prow = part + (int64_t)blockIdx.x * 2 * kp;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      part_rho[(int64_t)blockIdx.x * kp + 4 * w + j] = v[j];
-      part_rr[(int64_t)blockIdx.x * kp + 4 * w + j] = v[4 + j];
+      prow[4 * w + j] = v[j];
+      prow[kp + 4 * w + j] = v[4 + j];
     }
   }
 }
 
 // Preconditioned start: rho_0 = r^T M^-1 r drives alpha / beta, |r_0|^2 the
 // convergence test (|r| <= rtol |r_0| on the true residual).
-__global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restrict__ part_rho,
-                                                          const double* __restrict__ part_rr, int np, int k, int kp,
+__global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restrict__ part, int np, int k, int kp,
                                                           gp::CgState* st) {
   __shared__ double scratch[kRedThreads];
-  __shared__ double rho[gp::kMaxCols], rr[gp::kMaxCols];
+  __shared__ double sums[2 * gp::kMaxCols];
   __shared__ int any_running;
-  block_sum_partials(part_rho, np, kp, kp, rho, scratch);
-  block_sum_partials(part_rr, np, kp, kp, rr, scratch);
+  block_sum_partials(part, np, 2 * kp, 2 * kp, sums, scratch);
   if (threadIdx.x == 0) any_running = 0;
   __syncthreads();
   if (threadIdx.x < gp::kMaxCols) {
     const int c = threadIdx.x;
-    const double r0 = c < k ? rr[c] : 0.0;
-    const double p0 = c < k ? rho[c] : 0.0;
+    const double p0 = c < k ? sums[c] : 0.0;
+    const double r0 = c < k ? sums[kp + c] : 0.0;
     st->rr0[c] = r0;
     st->crr[0][c] = r0;
     st->crr[1][c] = r0;
@@ -627,11 +665,12 @@ __global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restri
   }
 }
 
-// beta of iteration it (one block): |r_new|^2 from the partials, convergence,
-// and the iteration-(it+1) scalars in parity slot (it+1)&1.
-__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part_rr,
-                                                         const double* __restrict__ part_crr, int nrr, int k,
-                                                         int kp, int it, gp::CgState* st, double* hist_beta,
+// beta of iteration it (one block): rho_new from the partials (|r|^2, or
+// r^T z and |r|^2 side by side in rows of 2 kp when preconditioned),
+// convergence on |r|^2, and the iteration-(it+1) scalars in parity slot
+// (it+1)&1.
+__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part, int nrr, int k, int kp,
+                                                         int pc, int it, gp::CgState* st, double* hist_beta,
                                                          int m_hist) {
   const int cur = it & 1, nxt = (it + 1) & 1;
   if (st->fin[cur]) {
@@ -639,12 +678,12 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restric
     return;
   }
   __shared__ double scratch[kRedThreads];
-  __shared__ double rrn[gp::kMaxCols];   // rho_new = r^T M^-1 r
-  __shared__ double crn[gp::kMaxCols];   // |r|^2 (the same as rho_new without a preconditioner)
+  __shared__ double sums[2 * gp::kMaxCols];
   __shared__ int any_running;
-  block_sum_partials(part_rr, nrr, kp, kp, rrn, scratch);
-  if (part_crr) block_sum_partials(part_crr, nrr, kp, kp, crn, scratch);
-  else if (threadIdx.x < kp) crn[threadIdx.x] = rrn[threadIdx.x];
+  const int width = pc ? 2 * kp : kp;
+  block_sum_partials(part, nrr, width, width, sums, scratch);
+  const double* rrn = sums;               // rho_new = r^T M^-1 r (|r|^2 without a preconditioner)
+  const double* crn = sums + (pc ? kp : 0);  // |r|^2
   if (threadIdx.x == 0) any_running = 0;
   __syncthreads();
   if (threadIdx.x < kp) {
@@ -1133,19 +1172,20 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   const bool pc = use_pc && c->pc_block > 0;
   const int kq = kp / 4;
   unsigned g_pc = 0;
+  size_t pc_smem = 0;
   if (pc) {
-    int per_sm = 0;
-    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_r_pc<false>, kPcTile * kq, 0));
-    if (per_sm < 1) per_sm = 1;
-    g_pc = grid_for(n, kPcTile, c->num_sms * per_sm);
+    pc_smem = pc_smem_bytes(kq, c->pc_block);
+    GP_CUDA(cudaFuncSetAttribute(k_upd_r_pc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+    GP_CUDA(cudaFuncSetAttribute(k_upd_r_pc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+    // two blocks per SM, two tiles each in flight: enough bytes in flight for
+    // HBM without many partial rows for the one-block reduction
+    g_pc = grid_for(n, kPcTile, c->num_sms * 2);
     GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
-    GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * kp * sizeof(double)));
-    GP_CHECK(ensure(c, c->part_c, (size_t)g_pc * kp * sizeof(double)));
-    k_upd_r_pc<true><<<g_pc, kPcTile * kq, 0, c->stream>>>(n, kq, c->pc_block, 0, nullptr, (float4*)c->R.p,
-                                                           (float4*)c->P.p, (const float*)c->pc_Minv.p,
-                                                           (double*)c->part_b.p, (double*)c->part_c.p, st);
-    k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (const double*)c->part_c.p, (int)g_pc,
-                                                 k, kp, st);
+    GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * 2 * kp * sizeof(double)));
+    k_upd_r_pc<true><<<g_pc, kPcTile * kq, pc_smem, c->stream>>>(n, kq, c->pc_block, 0, nullptr, (float4*)c->R.p,
+                                                                 (float4*)c->P.p, (const float*)c->pc_Minv.p,
+                                                                 (double*)c->part_b.p, st);
+    k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, st);
     GP_LAUNCH_CHECK();
     c->launches += 2;
   }
@@ -1178,16 +1218,16 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
       k_cg_alpha<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, it, st,
                                                    (double*)c->hist_alpha.p, m_hist);
       if (pc) {
-        k_upd_r_pc<false><<<g_pc, kPcTile * kq, 0, c->stream>>>(
+        k_upd_r_pc<false><<<g_pc, kPcTile * kq, pc_smem, c->stream>>>(
             n, kq, c->pc_block, it, (const float4*)c->Q.p, (float4*)c->R.p, (float4*)c->Z.p,
-            (const float*)c->pc_Minv.p, (double*)c->part_b.p, (double*)c->part_c.p, st);
-        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (const double*)c->part_c.p,
-                                                    (int)g_pc, k, kp, it, st, (double*)c->hist_beta.p, m_hist);
+            (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
+        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, it, st,
+                                                    (double*)c->hist_beta.p, m_hist);
       } else {
         k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
                                                              (double*)c->part_b.p, st);
-        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, nullptr, (int)g_upd_r, k, kp, it,
-                                                    st, (double*)c->hist_beta.p, m_hist);
+        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, 0, it, st,
+                                                    (double*)c->hist_beta.p, m_hist);
       }
       k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (float4*)c->X.p,
                                                          (const float4*)(pc ? c->Z.p : c->R.p), (float4*)c->P.p,
