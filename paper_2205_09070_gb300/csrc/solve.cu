@@ -191,9 +191,11 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
   }
 }
 
-// A: Q = Khat P on the 8x1 block CSR.  Each warp owns a contiguous run of
-// block rows holding an equal share of the stored blocks and streams them in
-// chunks of 32 blocks through a double-buffered shared-memory stage: while the
+// A: Q = Khat P on the 8x1 block CSR.  Each CTA owns a contiguous run of
+// block rows holding an equal share of the stored blocks; its warps take the
+// rows round-robin (neighbouring block rows gather overlapping P rows, which
+// then hit in L1), and each warp streams its rows' blocks in chunks of 32
+// through a double-buffered shared-memory stage: while the
 // warp computes chunk c, cp.async copies the P rows (kp floats) and the 8
 // values of chunk c+1 into the other buffer, and the column indices of chunk
 // c+2 are already being loaded.  Compute: the warp's lanes form NG = 32/G
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
 // of the block row (8 float4 accumulators per lane).
 // Smallest block row b in [0, nblk] whose first stored block is >= target
 // (brp ascending, brp[nblk] = total).  Every block row then belongs to
-// exactly one warp's share.
+// exactly one CTA's share.
 __device__ inline int64_t first_row_at_or_after(const int64_t* __restrict__ brp, int64_t nblk, int64_t target) {
   int64_t lo = 0, hi = nblk;
   while (lo < hi) {
@@ -231,10 +233,12 @@ struct ChunkPos {
   int64_t bb, base;
 };
 
-__device__ inline ChunkPos next_chunk(ChunkPos c, const int64_t* __restrict__ brp) {
+__device__ inline ChunkPos next_chunk(ChunkPos c, const int64_t* __restrict__ brp, int64_t b1) {
   const int64_t e = __ldg(brp + c.bb + 1);
   if (c.base + kChunk < e) return {c.bb, c.base + kChunk};
-  return {c.bb + 1, e};
+  const int64_t nb = c.bb + kSpmmWarps;
+  if (nb >= b1) return {b1, 0};
+  return {nb, __ldg(brp + nb)};
 }
 
 template <int G>
@@ -258,12 +262,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   // Work split by stored blocks, not by block rows (cluster cores hold many
   // times more blocks per row than the background).
   const int64_t nent = brp[nblk];
-  const int64_t nw = (int64_t)gridDim.x * kSpmmWarps;
-  const int64_t wid = (int64_t)blockIdx.x * kSpmmWarps + w;
-  const int64_t b0 = first_row_at_or_after(brp, nblk, nent * wid / nw);
-  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (wid + 1) / nw);
+  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * blockIdx.x / gridDim.x);
+  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (blockIdx.x + 1) / gridDim.x);
+  const int64_t b0 = cb0 + w;
   if (b0 < b1) {
-    const int64_t e_end = __ldg(brp + b1);
     // stage a chunk: consecutive lanes copy consecutive 16-byte pieces of the
     // same P row (G pieces per row, so one copy instruction covers about 32/G
     // rows), then the chunk's block values (2 float4 each, contiguous)
@@ -290,10 +292,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     auto col_of = [&](ChunkPos c) -> int {
       if (c.bb >= b1) return 0;
       const int64_t idx = c.base + lane;
-      return idx < min(e_end, __ldg(brp + c.bb + 1)) ? __ldg(bcol + idx) : 0;
+      return idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
     };
     ChunkPos cur{b0, __ldg(brp + b0)};
-    ChunkPos nx1 = next_chunk(cur, brp);
+    ChunkPos nx1 = next_chunk(cur, brp, b1);
     issue(cur, col_of(cur), 0);
     int j1 = col_of(nx1);
     // accumulators as float2 pairs (columns x,y and z,w of the lane's float4)
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     for (int r = 0; r < 2 * kBR; ++r) acc[r] = make_float2(0.f, 0.f);
     int buf = 0;
     while (cur.bb < b1) {
-      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp) : nx1;
+      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp, b1) : nx1;
       issue(nx1, j1, buf ^ 1);            // copies of chunk c+1 in flight
       const int j2 = col_of(nx2);          // indices of chunk c+2 in flight
       cp_async_wait<1>();                  // chunk c has landed
