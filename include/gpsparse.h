@@ -86,7 +86,9 @@ typedef struct {
   int32_t precond_block;  /* FP32_MIXED only: 0 = Jacobi scaling alone; 8, 16 or 32 = also
                              block-Jacobi preconditioned CG, blocks of that many consecutive
                              rows of the Morton-ordered active block (see gp_lml) */
-  int32_t reserved;       /* must be 0 */
+  int32_t batch_workers;  /* gp_lml_grad_batched: instances run concurrently on this many
+                             worker streams, each driven by its own host thread with its own
+                             workspace (0: automatic, min(n_inst, 4); at most 16) */
 } gp_opts;
 
 /* gp_opts.flags: time every launch of the SpMM, pair-fill and adjoint kernels
@@ -200,7 +202,12 @@ int gp_lml_grad(gp_ctx* ctx, const double* x, const double* y, int64_t n, const 
 /* Many independent GPs that share the kernel family.  Instance k owns points
  * offsets[k] .. offsets[k+1]-1 of x / y (offsets: host, n_inst+1 entries) and
  * hyperparameters h[k*P .. (k+1)*P).  lml: n_inst doubles, grad: n_inst*P
- * doubles (host or device); grad may be NULL.  info (may be NULL) gets totals. */
+ * doubles (host or device); grad may be NULL.  info (may be NULL) gets totals.
+ * Instances are taken largest first by opts->batch_workers workers, each with
+ * its own stream and workspace (kept in ctx for later calls); the workers
+ * start after the work already queued on the context stream, and the call
+ * returns when all instances are done.  Each instance's result is the one
+ * gp_lml_grad gives for it alone (same kernels, same reduction order). */
 int gp_lml_grad_batched(gp_ctx* ctx, int32_t n_inst, const int64_t* offsets,
                         const double* x, const double* y, const double* h,
                         const gp_opts* opts, double* lml, double* grad, gp_info* info);

@@ -3,7 +3,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "gp_internal.cuh"
@@ -123,7 +126,7 @@ int check_opts(const gp_opts* o, bool need_probes) {
   if (o->max_iter < 1 || !(o->cg_rtol > 0.0) || !isfinite(o->cg_rtol)) return GP_ERR_INVALID_ARG;
   if (o->precond_block != 0 && o->precond_block != 8 && o->precond_block != 16 && o->precond_block != 32)
     return GP_ERR_INVALID_ARG;
-  if (o->reserved != 0) return GP_ERR_INVALID_ARG;
+  if (o->batch_workers < 0 || o->batch_workers > 16) return GP_ERR_INVALID_ARG;
   if (need_probes) {
     if (o->n_probes < 1 || o->n_probes > gp::kMaxProbes) return GP_ERR_INVALID_ARG;
     if (o->lanczos_steps < 1 || o->lanczos_steps > gp::kMaxLanczos) return GP_ERR_INVALID_ARG;
@@ -302,7 +305,7 @@ void gp_default_opts(gp_opts* o) {
   o->check_every = 16;
   o->flags = 0;
   o->precond_block = 32;
-  o->reserved = 0;
+  o->batch_workers = 0;
 }
 
 int gp_create(gp_ctx** out, const gp_kernel_desc* desc, int device, void* stream) {
@@ -359,6 +362,11 @@ int gp_destroy(gp_ctx* c) {
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->kev_ready)
     for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
+  for (auto& gr : c->cg_graph)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (gp_ctx* w : c->workers) gp_destroy(w);
+  if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
   delete c;
   return GP_OK;
 }
@@ -486,28 +494,84 @@ int gp_lml_grad(gp_ctx* c, const double* x, const double* y, int64_t n, const do
 
 int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const double* x, const double* y,
                         const double* h, const gp_opts* o, double* lml, double* grad, gp_info* info) {
-  if (!c || n_inst < 0 || (n_inst > 0 && (!offsets || !h || !lml))) return GP_ERR_INVALID_ARG;
+  if (!c || !o || n_inst < 0 || (n_inst > 0 && (!offsets || !h || !lml))) return GP_ERR_INVALID_ARG;
+  GP_CHECK(check_opts(o, true));
   if (info) memset(info, 0, sizeof(*info));
+  if (n_inst == 0) return GP_OK;
+  for (int32_t q = 0; q < n_inst; ++q)
+    if (offsets[q] < 0 || offsets[q + 1] < offsets[q]) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
   const int64_t P = (int64_t)c->nb * (c->dim + 2) + 3;
-  const bool lml_dev = gp::is_device_ptr(lml), grad_dev = grad && gp::is_device_ptr(grad);
-  std::vector<double> g(P);
-  int status = GP_OK;
-  for (int32_t q = 0; q < n_inst; ++q) {
-    const int64_t a = offsets[q], b = offsets[q + 1];
-    if (b < a) return GP_ERR_INVALID_ARG;
-    double l = 0.0;
-    gp_info inf;
-    int st = evaluate(c, x ? x + a * c->dim : nullptr, y ? y + a : nullptr, b - a, h + q * P, o, &l,
-                      grad ? g.data() : nullptr, &inf);
-    if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
-    if (st != GP_OK) status = st;
-    if (lml_dev) GP_CUDA(cudaMemcpy(lml + q, &l, sizeof(double), cudaMemcpyHostToDevice));
-    else lml[q] = l;
-    if (grad) {
-      if (grad_dev) GP_CUDA(cudaMemcpy(grad + q * P, g.data(), P * sizeof(double), cudaMemcpyHostToDevice));
-      else memcpy(grad + q * P, g.data(), P * sizeof(double));
+  int nw = o->batch_workers > 0 ? o->batch_workers : 4;
+  if (nw > n_inst) nw = n_inst;
+  // worker contexts: own stream, workspace and CG graphs; kept for later calls
+  while ((int)c->workers.size() < nw) {
+    cudaStream_t s = nullptr;
+    GP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const gp_kernel_desc d{c->dim, c->n1, c->n2, c->beta};
+    gp_ctx* w = nullptr;
+    const int st = gp_create(&w, &d, c->device, s);
+    if (st != GP_OK) {
+      cudaStreamDestroy(s);
+      return st;
     }
-    if (info) {
+    w->owned_stream = s;
+    c->workers.push_back(w);
+  }
+  // the workers start after everything already queued on the context stream
+  // (the inputs may be produced there)
+  cudaEvent_t ready = nullptr;
+  GP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  GP_CUDA(cudaEventRecord(ready, c->stream));
+  for (int wi = 0; wi < nw; ++wi) GP_CUDA(cudaStreamWaitEvent(c->workers[wi]->stream, ready, 0));
+  // largest instances first, so the tail is short
+  std::vector<int32_t> order(n_inst);
+  for (int32_t q = 0; q < n_inst; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+  });
+  std::vector<double> lml_h(n_inst, 0.0), grad_h(grad ? (size_t)n_inst * P : 0);
+  std::vector<gp_info> infos(n_inst);
+  std::vector<int> status(n_inst, GP_OK);
+  std::atomic<int32_t> next{0};
+  std::atomic<bool> abort{false};
+  auto work = [&](int wi) {
+    cudaSetDevice(c->device);
+    gp_ctx* w = c->workers[wi];
+    for (;;) {
+      const int32_t t = next.fetch_add(1);
+      if (t >= n_inst || abort.load()) break;
+      const int32_t q = order[t];
+      const int64_t a = offsets[q], b = offsets[q + 1];
+      status[q] = evaluate(w, x ? x + a * c->dim : nullptr, y ? y + a : nullptr, b - a, h + q * P, o, &lml_h[q],
+                           grad ? grad_h.data() + (size_t)q * P : nullptr, &infos[q]);
+      if (status[q] != GP_OK && status[q] != GP_ERR_NOT_CONVERGED) abort.store(true);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int wi = 1; wi < nw; ++wi) pool.emplace_back(work, wi);
+  work(0);
+  for (std::thread& t : pool) t.join();
+  cudaEventDestroy(ready);
+  int result = GP_OK;
+  for (int32_t q = 0; q < n_inst; ++q) {
+    if (status[q] != GP_OK && status[q] != GP_ERR_NOT_CONVERGED) return status[q];
+    if (status[q] != GP_OK) result = status[q];
+  }
+  if (gp::is_device_ptr(lml)) {
+    GP_CUDA(cudaMemcpy(lml, lml_h.data(), (size_t)n_inst * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    memcpy(lml, lml_h.data(), (size_t)n_inst * sizeof(double));
+  }
+  if (grad) {
+    if (gp::is_device_ptr(grad))
+      GP_CUDA(cudaMemcpy(grad, grad_h.data(), grad_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    else
+      memcpy(grad, grad_h.data(), grad_h.size() * sizeof(double));
+  }
+  if (info) {
+    for (int32_t q = 0; q < n_inst; ++q) {
+      const gp_info& inf = infos[q];
       info->n += inf.n;
       info->n_active += inf.n_active;
       info->nnz += inf.nnz;
@@ -518,9 +582,12 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
       info->launches += inf.launches;
       info->lanczos_iters = inf.lanczos_iters > info->lanczos_iters ? inf.lanczos_iters : info->lanczos_iters;
       info->precond_block = inf.precond_block > info->precond_block ? inf.precond_block : info->precond_block;
+      info->n_spmm += inf.n_spmm;
+      info->t_spmm_kernel_ms += inf.t_spmm_kernel_ms;
+      info->kp = inf.kp;
     }
   }
-  return status;
+  return result;
 }
 
 const char* gp_status_string(int s) {

@@ -8,6 +8,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "../../include/gpsparse.h"
 
 namespace gp {
@@ -150,6 +152,19 @@ struct gp_ctx {
   double t_spmm = 0.0, t_fill = 0.0, t_adj = 0.0;
   int n_spmm = 0;
   int bad_col = -1, bad_iter = 0;   // where the last CG run stopped on a breakdown
+  // CUDA graphs of one check interval of the FP32 CG loop (slot 0: plain CG,
+  // slot 1: preconditioned), reused while every launch argument is the same;
+  // captured on a private stream (capture is not allowed on the legacy
+  // default stream) and launched on `stream`
+  struct CgGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key[32] = {};
+  } cg_graph[2];
+  cudaStream_t cap_stream = nullptr;
+  // gp_lml_grad_batched workers: contexts of their own (stream, workspace,
+  // graphs), created on first use and destroyed with this context
+  std::vector<gp_ctx*> workers;
+  cudaStream_t owned_stream = nullptr;  // a worker's stream (0 for user contexts)
 };
 
 namespace gp {

@@ -16,6 +16,7 @@
 // FP64: one single-RHS CG per column, all in FP64 (the plain comparison path),
 // with its scalars finished by the last block of each kernel.
 #include <math.h>
+#include <string.h>
 
 #include "gp_internal.cuh"
 
@@ -242,12 +243,13 @@ __device__ inline ChunkPos next_chunk(ChunkPos c, const int64_t* __restrict__ br
 }
 
 template <int G>
-__global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t nblk, int it,
+__global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t nblk,
                                                             const int64_t* __restrict__ brp,
                                                             const int32_t* __restrict__ bcol,
                                                             const float4* __restrict__ bval,
                                                             const float4* __restrict__ P, float4* __restrict__ Q,
                                                             double* __restrict__ part, const gp::CgState* st) {
+  const int it = st->iter;
   if (st->fin[it & 1]) return;
   constexpr int NG = 32 / G;
   constexpr int KP = 4 * G;
@@ -390,8 +392,9 @@ constexpr int kRedThreads = 1024;
 // alpha of iteration it (one block): p_c^T q_c from the SpMM partials in a
 // fixed order; alpha_c = |r_c|^2 / p_c^T q_c for columns still running.
 __global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restrict__ part_pq, int npq, int k,
-                                                          int kp, int it, gp::CgState* st, double* hist_alpha,
+                                                          int kp, gp::CgState* st, double* hist_alpha,
                                                           int m_hist) {
+  const int it = st->iter;
   if (st->fin[it & 1]) return;
   __shared__ double scratch[kRedThreads];
   __shared__ double pq[gp::kMaxCols];
@@ -422,10 +425,10 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restri
 // are compensated FP32 (Dot2), the block's are combined in FP64 by a tree.
 constexpr int kUpdRThreads = 1024;
 
-__global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, int it, const float4* __restrict__ Q,
+__global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, const float4* __restrict__ Q,
                                                             float4* __restrict__ R, double* __restrict__ part_rr,
                                                             const gp::CgState* st) {
-  if (st->fin[it & 1]) return;
+  if (st->fin[st->iter & 1]) return;
   __shared__ double red[kUpdRThreads][4];
   const int ny = kUpdRThreads / kq;
   const int tx = threadIdx.x % kq, ty = threadIdx.x / kq;
@@ -518,11 +521,11 @@ size_t pc_smem_bytes(int kq, int B) {
 }
 
 template <bool INIT>
-__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, int B, int it,
+__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, int B,
                                                              const float4* __restrict__ Q, float4* __restrict__ R,
                                                              float4* __restrict__ Z, const float* __restrict__ Minv,
                                                              double* __restrict__ part, const gp::CgState* st) {
-  if (!INIT && st->fin[it & 1]) return;
+  if (!INIT && st->fin[st->iter & 1]) return;
   extern __shared__ float4 pc_smem[];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nthr = kPcTile * kq;
@@ -672,8 +675,9 @@ __global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restri
 // convergence on |r|^2, and the iteration-(it+1) scalars in parity slot
 // (it+1)&1.
 __global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part, int nrr, int k, int kp,
-                                                         int pc, int it, gp::CgState* st, double* hist_beta,
+                                                         int pc, gp::CgState* st, double* hist_beta,
                                                          int m_hist) {
+  const int it = st->iter;
   const int cur = it & 1, nxt = (it + 1) & 1;
   if (st->fin[cur]) {
     if (threadIdx.x == 0) st->fin[nxt] = 1;
@@ -719,10 +723,12 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restric
 
 // C: X += alpha P_old, P = Z + beta P_old with Z = M^-1 R (Z = R without a
 // preconditioner); runs for iteration it unless the run had already finished.
-__global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, int it, float4* __restrict__ X,
+__global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, float4* __restrict__ X,
                                                             const float4* __restrict__ R, float4* __restrict__ P,
                                                             const gp::CgState* st) {
-  if (st->fin[it & 1]) return;
+  // beta has already advanced the counter for this iteration (or, when the
+  // run had finished, marked the parity slot of it - 1 finished as well)
+  if (st->fin[(st->iter - 1) & 1]) return;
   const int ny = kUpdThreads / kq;
   const int tx = threadIdx.x % kq, ty = threadIdx.x / kq;
   if (ty >= ny) return;
@@ -1103,8 +1109,8 @@ unsigned grid_for(int64_t items, int per_block, int max_blocks) {
   return (unsigned)g;
 }
 
-typedef void (*SpmmFn)(int64_t, int64_t, int, const int64_t*, const int32_t*, const float4*, const float4*,
-                       float4*, double*, const gp::CgState*);
+typedef void (*SpmmFn)(int64_t, int64_t, const int64_t*, const int32_t*, const float4*, const float4*, float4*,
+                       double*, const gp::CgState*);
 
 SpmmFn spmm_for(int G) {
   switch (G) {
@@ -1184,7 +1190,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     g_pc = grid_for(n, kPcTile, c->num_sms * 2);
     GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
     GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * 2 * kp * sizeof(double)));
-    k_upd_r_pc<true><<<g_pc, kPcTile * kq, pc_smem, c->stream>>>(n, kq, c->pc_block, 0, nullptr, (float4*)c->R.p,
+    k_upd_r_pc<true><<<g_pc, kPcTile * kq, pc_smem, c->stream>>>(n, kq, c->pc_block, nullptr, (float4*)c->R.p,
                                                                  (float4*)c->P.p, (const float*)c->pc_Minv.p,
                                                                  (double*)c->part_b.p, st);
     k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, st);
@@ -1206,36 +1212,77 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   if (check_every > 64) check_every = 64;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
   if (timed) GP_CHECK(kernel_events(c));
+  // one CG iteration: the kernels read the iteration index from the device
+  // state, so the same launches serve every iteration (and a graph of them)
+  auto launch_iteration = [&](cudaStream_t sm, cudaEvent_t ev0, cudaEvent_t ev1) {
+    if (ev0) cudaEventRecord(ev0, sm);
+    spmm<<<g_spmm, kSpmmThreads, spmm_smem, sm>>>(n, nblk, (const int64_t*)c->brp.p, (const int32_t*)c->bcol.p,
+                                                 (const float4*)c->bval.p, (const float4*)c->P.p, (float4*)c->Q.p,
+                                                 (double*)c->part_a.p, st);
+    if (ev1) cudaEventRecord(ev1, sm);
+    k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
+                                          (double*)c->hist_alpha.p, m_hist);
+    if (pc) {
+      k_upd_r_pc<false><<<g_pc, kPcTile * kq, pc_smem, sm>>>(n, kq, c->pc_block, (const float4*)c->Q.p,
+                                                              (float4*)c->R.p, (float4*)c->Z.p,
+                                                              (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
+      k_cg_beta<<<1, kRedThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, st,
+                                           (double*)c->hist_beta.p, m_hist);
+    } else {
+      k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, sm>>>(n, kq, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                    (double*)c->part_b.p, st);
+      k_cg_beta<<<1, kRedThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, 0, st,
+                                           (double*)c->hist_beta.p, m_hist);
+    }
+    k_upd_xp_f32<<<g_upd, kUpdThreads, 0, sm>>>(n, kq, (float4*)c->X.p, (const float4*)(pc ? c->Z.p : c->R.p),
+                                                (float4*)c->P.p, st);
+  };
+  // graph of check_every iterations, rebuilt only when an argument changes
+  // (with GP_FLAG_TIME_KERNELS the graph also records the SpMM events)
+  cudaGraphExec_t exec = nullptr;
+  {
+    const uint64_t key[32] = {(uint64_t)n, (uint64_t)nblk, (uint64_t)k, (uint64_t)kp, (uint64_t)pc,
+                              (uint64_t)c->pc_block, (uint64_t)g_spmm, (uint64_t)g_pc, (uint64_t)g_upd,
+                              (uint64_t)g_upd_r, (uint64_t)m_hist, (uint64_t)check_every, (uint64_t)spmm_smem,
+                              (uint64_t)pc_smem, (uint64_t)(uintptr_t)spmm, (uint64_t)(uintptr_t)c->brp.p,
+                              (uint64_t)(uintptr_t)c->bcol.p, (uint64_t)(uintptr_t)c->bval.p,
+                              (uint64_t)(uintptr_t)c->P.p, (uint64_t)(uintptr_t)c->Q.p, (uint64_t)(uintptr_t)c->R.p,
+                              (uint64_t)(uintptr_t)c->X.p, (uint64_t)(uintptr_t)c->Z.p,
+                              (uint64_t)(uintptr_t)c->part_a.p, (uint64_t)(uintptr_t)c->part_b.p,
+                              (uint64_t)(uintptr_t)c->hist_alpha.p, (uint64_t)(uintptr_t)c->hist_beta.p,
+                              (uint64_t)(uintptr_t)st, (uint64_t)(uintptr_t)c->pc_Minv.p, (uint64_t)timed,
+                              (uint64_t)(uintptr_t)(timed ? c->kev[0] : nullptr), 0};
+    gp_ctx::CgGraph& gr = c->cg_graph[pc ? 1 : 0];
+    if (gr.exec && memcmp(gr.key, key, sizeof(key)) != 0) {
+      GP_CUDA(cudaGraphExecDestroy(gr.exec));
+      gr.exec = nullptr;
+    }
+    if (!gr.exec) {
+      if (!c->cap_stream) GP_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      GP_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      for (int t = 0; t < check_every; ++t)
+        launch_iteration(c->cap_stream, timed ? c->kev[2 * t] : nullptr, timed ? c->kev[2 * t + 1] : nullptr);
+      GP_CUDA(cudaStreamEndCapture(c->cap_stream, &graph));
+      const cudaError_t ie = cudaGraphInstantiate(&gr.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        gr.exec = nullptr;
+        return GP_ERR_CUDA;
+      }
+      memcpy(gr.key, key, sizeof(key));
+    }
+    exec = gr.exec;
+  }
   CgState hs;
   int iter_before = 0;
   for (int it0 = 0; it0 < max_iter; it0 += check_every) {
-    for (int t = 0; t < check_every; ++t) {
-      const int it = it0 + t;
-      if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t], c->stream));
-      spmm<<<g_spmm, kSpmmThreads, spmm_smem, c->stream>>>(n, nblk, it, (const int64_t*)c->brp.p,
-                                                           (const int32_t*)c->bcol.p, (const float4*)c->bval.p,
-                                                           (const float4*)c->P.p, (float4*)c->Q.p,
-                                                           (double*)c->part_a.p, st);
-      if (timed) GP_CUDA(cudaEventRecord(c->kev[2 * t + 1], c->stream));
-      k_cg_alpha<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, it, st,
-                                                   (double*)c->hist_alpha.p, m_hist);
-      if (pc) {
-        k_upd_r_pc<false><<<g_pc, kPcTile * kq, pc_smem, c->stream>>>(
-            n, kq, c->pc_block, it, (const float4*)c->Q.p, (float4*)c->R.p, (float4*)c->Z.p,
-            (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
-        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, it, st,
-                                                    (double*)c->hist_beta.p, m_hist);
-      } else {
-        k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, c->stream>>>(n, kq, it, (const float4*)c->Q.p, (float4*)c->R.p,
-                                                             (double*)c->part_b.p, st);
-        k_cg_beta<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, 0, it, st,
-                                                    (double*)c->hist_beta.p, m_hist);
-      }
-      k_upd_xp_f32<<<g_upd, kUpdThreads, 0, c->stream>>>(n, kq, it, (float4*)c->X.p,
-                                                         (const float4*)(pc ? c->Z.p : c->R.p), (float4*)c->P.p,
-                                                         st);
+    if (exec) {
+      GP_CUDA(cudaGraphLaunch(exec, c->stream));
+    } else {
+      for (int t = 0; t < check_every; ++t) launch_iteration(c->stream, c->kev[2 * t], c->kev[2 * t + 1]);
+      GP_LAUNCH_CHECK();
     }
-    GP_LAUNCH_CHECK();
     c->launches += 5 * check_every;
     GP_CHECK(read_state(c, &hs));
     if (timed) {

@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_probes", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("cg_rtol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("check_every", ctypes.c_int32), ("flags", ctypes.c_int32), ("precond_block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("batch_workers", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
