@@ -1214,12 +1214,15 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   if (timed) GP_CHECK(kernel_events(c));
   // one CG iteration: the kernels read the iteration index from the device
   // state, so the same launches serve every iteration (and a graph of them)
+  // (events recorded during capture become external event-record nodes,
+  // which time like ordinary records)
   auto launch_iteration = [&](cudaStream_t sm, cudaEvent_t ev0, cudaEvent_t ev1) {
-    if (ev0) cudaEventRecord(ev0, sm);
+    const unsigned evf = sm == c->cap_stream ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (ev0) cudaEventRecordWithFlags(ev0, sm, evf);
     spmm<<<g_spmm, kSpmmThreads, spmm_smem, sm>>>(n, nblk, (const int64_t*)c->brp.p, (const int32_t*)c->bcol.p,
                                                  (const float4*)c->bval.p, (const float4*)c->P.p, (float4*)c->Q.p,
                                                  (double*)c->part_a.p, st);
-    if (ev1) cudaEventRecord(ev1, sm);
+    if (ev1) cudaEventRecordWithFlags(ev1, sm, evf);
     k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
                                           (double*)c->hist_alpha.p, m_hist);
     if (pc) {
