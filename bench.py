@@ -122,15 +122,19 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-SPMM_BEGIN = "// A: Q = Khat P on the 8x1 block CSR."
-SPMM_END = "constexpr int kUpdThreads"
+SPMM_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "spmm.cu")
+SPMM_KERNELS = {0: "k_bspmm_f32<{kq}>", 1: "k_bspmm_tma<{kq},1>", 2: "k_bspmm_tma<{kq},{lw}>"}
+
+
+def spmm_kernel_name(variant: int, kp: int) -> str:
+    kq = kp // 4
+    lw = 3 if kq % 3 == 0 and kq >= 6 else 2 if kq % 2 == 0 and kq >= 4 else 1
+    return SPMM_KERNELS.get(variant, "k_bspmm_?<{kq}>").format(kq=kq, lw=lw)
 
 
 def spmm_source_sha() -> str:
-    """sha256 of the SpMM kernel's source region (kernel and its helpers)."""
-    src = open(os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "solve.cu")).read()
-    a, b = src.index(SPMM_BEGIN), src.index(SPMM_END)
-    return hashlib.sha256(src[a:b].encode()).hexdigest()
+    """sha256 of the SpMM source file (every form and its helpers)."""
+    return hashlib.sha256(open(SPMM_SOURCE, "rb").read()).hexdigest()
 
 
 def traffic_record(kernel: str, kp: int):
@@ -262,7 +266,7 @@ def main():
     bytes_spmm = 8 * nnz + 8 * n_act * kp + 8 * (n_act + 1)
     achieved = bytes_spmm / (spmm_ms * 1e-3) / 1e9
     pk = peaks()
-    kname = f"k_bspmm_f32<{kp // 4}>"
+    kname = spmm_kernel_name(infos[-1]["spmm_variant"], kp)
     trec = traffic_record(kname, kp)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": trec["bytes_per_launch"] if trec else None,
@@ -328,7 +332,10 @@ def main():
                            "r_s": float(p.h[-3]), "n_probes": 32, "lanczos_steps": 50, "cg_rtol": 1e-6,
                            "precision": "FP32_MIXED", "parallelism": f"replicas x{world}",
                            "l2": "working set larger than L2 (CSR re-assembled every step)",
-                           "n_active": n_act, "nnz": nnz, "kp": kp, "cg_iters": infos[-1]["iters"]},
+                           "n_active": n_act, "nnz": nnz, "kp": kp, "cg_iters": infos[-1]["iters"],
+                "lanczos_iters": infos[-1]["lanczos_iters"], "precond_block": infos[-1]["precond_block"],
+                "spmm_form": ["cp.async stage", "TMA gather4 stage", "TMA gather4 stage, wide lanes"][
+                    infos[-1]["spmm_variant"]] if infos[-1]["spmm_variant"] >= 0 else None},
                 "lml": lml, "logdet_stderr": infos[-1]["logdet_stderr"],
                 "assembly": {"nnz_per_s": nnz / (t_asm * 1e-3), "ms": t_asm, "fill_kernel_ms": t_fill},
                 "adjoint_kernel_ms": t_adj,

@@ -94,6 +94,21 @@ typedef struct {
 /* gp_opts.flags: time every launch of the SpMM, pair-fill and adjoint kernels
  * with CUDA events on the context stream (reported in gp_info.t_*_kernel_ms). */
 #define GP_FLAG_TIME_KERNELS 1
+/* gp_opts.flags: run the FP32 path's sparse product Q = K P (one per CG
+ * iteration) in the given form instead of the autotuner's choice.  Without
+ * these bits the first FP32 solve of each matrix shape (n_active, block count,
+ * columns) in the process times every form on that matrix (4 launches each,
+ * one host synchronisation) and keeps the fastest for the life of the process;
+ * contexts then agree on the form for a given shape.  The forms give the same
+ * products summed in different orders (FP32 rounding differences only). */
+#define GP_FLAG_SPMM_CPASYNC  2  /* stage filled by per-lane cp.async copies */
+#define GP_FLAG_SPMM_TMA      4  /* stage filled by TMA: tile::gather4 of P rows, bulk copy of values */
+#define GP_FLAG_SPMM_TMA_WIDE 8  /* TMA stage, 2 or 3 float4 columns per lane (else as GP_FLAG_SPMM_TMA) */
+
+/* gp_info.spmm_variant */
+#define GP_SPMM_CPASYNC  0
+#define GP_SPMM_TMA      1
+#define GP_SPMM_TMA_WIDE 2
 
 typedef struct {
   int64_t n;              /* points */
@@ -119,6 +134,7 @@ typedef struct {
   int32_t lanczos_iters;  /* iterations of the separate SLQ Lanczos run (preconditioned
                              evaluations only, else 0) */
   int32_t precond_block;  /* block size the solve used (0: none) */
+  int32_t spmm_variant;   /* GP_SPMM_* form of the FP32 sparse product, -1 if none ran */
 } gp_info;
 
 /* Number of hyperparameters: n_funcs*n_bumps*(dim+2) + 3. */

@@ -86,6 +86,7 @@ void reset_counters(gp_ctx* c, int flags) {
   c->t_spmm = c->t_fill = c->t_adj = 0.0;
   c->n_spmm = 0;
   c->bad_col = -1;
+  c->spmm_variant = -1;
 }
 
 void fill_counters(const gp_ctx* c, gp_info* info) {
@@ -95,6 +96,7 @@ void fill_counters(const gp_ctx* c, gp_info* info) {
   info->t_spmm_kernel_ms = c->t_spmm;
   info->t_fill_kernel_ms = c->t_fill;
   info->t_adjoint_kernel_ms = c->t_adj;
+  info->spmm_variant = c->spmm_variant;
 }
 
 int check_desc(const gp_kernel_desc* d) {
@@ -585,6 +587,8 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
       info->n_spmm += inf.n_spmm;
       info->t_spmm_kernel_ms += inf.t_spmm_kernel_ms;
       info->kp = inf.kp;
+      // the instances' common SpMM form, -1 if they differ
+      info->spmm_variant = q == 0 || inf.spmm_variant == info->spmm_variant ? inf.spmm_variant : -1;
     }
   }
   return result;

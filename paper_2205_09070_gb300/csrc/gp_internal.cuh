@@ -100,6 +100,17 @@ struct DevBuf {
   size_t cap = 0;
 };
 
+// One way of running Q = Khat P (spmm.cu): the kernel, its launch shape and,
+// for the TMA forms, the tensor map of P (an opaque 128-byte CUtensorMap).
+struct SpmmPlan {
+  int variant = -1;  // GP_SPMM_*
+  int kp = 0;
+  const void* fn = nullptr;
+  size_t smem = 0;
+  unsigned grid = 0;
+  alignas(64) unsigned char tmap[128] = {};
+};
+
 }  // namespace gp
 
 struct gp_ctx {
@@ -152,6 +163,7 @@ struct gp_ctx {
   double t_spmm = 0.0, t_fill = 0.0, t_adj = 0.0;
   int n_spmm = 0;
   int bad_col = -1, bad_iter = 0;   // where the last CG run stopped on a breakdown
+  int spmm_variant = -1;            // SpMM form of the last FP32 CG run (GP_SPMM_*)
   // CUDA graphs of one check interval of the FP32 CG loop (slot 0: plain CG,
   // slot 1: preconditioned), reused while every launch argument is the same;
   // captured on a private stream (capture is not allowed on the legacy
@@ -204,6 +216,15 @@ int alpha_out(gp_ctx* c, const double* y_dev, double* alpha_dev, int kp);
 
 // adjoint.cu
 int adjoint(gp_ctx* c, int n_probes, int kp);
+
+// spmm.cu: Q = Khat P on the 8x1 block CSR (c->brp, bcol, bval; P, Q, part_a
+// of the context), one launch per CG iteration.
+bool spmm_available(int variant, int kp);
+int spmm_plan(gp_ctx* c, int kp, int variant, SpmmPlan* plan);
+// the form forced by GP_FLAG_SPMM_* in flags, else the autotuner's choice for
+// this matrix shape (timed once per process, needs the CG state of iteration 0)
+int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan);
+void spmm_launch(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st);
 
 }  // namespace gp
 

@@ -192,199 +192,10 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
   }
 }
 
-// A: Q = Khat P on the 8x1 block CSR.  Each CTA owns a contiguous run of
-// block rows holding an equal share of the stored blocks; its warps take the
-// rows round-robin (neighbouring block rows gather overlapping P rows, which
-// then hit in L1), and each warp streams its rows' blocks in chunks of 32
-// through a double-buffered shared-memory stage: while the
-// warp computes chunk c, cp.async copies the P rows (kp floats) and the 8
-// values of chunk c+1 into the other buffer, and the column indices of chunk
-// c+2 are already being loaded.  Compute: the warp's lanes form NG = 32/G
-// groups of G lanes (one float4 of the kp = 4G columns per lane); a group
-// takes every NG-th block of the chunk and applies its P row to the 8 rows
-// of the block row (8 float4 accumulators per lane).
-// Smallest block row b in [0, nblk] whose first stored block is >= target
-// (brp ascending, brp[nblk] = total).  Every block row then belongs to
-// exactly one CTA's share.
-__device__ inline int64_t first_row_at_or_after(const int64_t* __restrict__ brp, int64_t nblk, int64_t target) {
-  int64_t lo = 0, hi = nblk;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (__ldg(brp + mid) < target) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-constexpr int kSpmmThreads = 128;
-constexpr int kSpmmWarps = kSpmmThreads / 32;
-constexpr int kBR = 8;
-constexpr int kChunk = 32;
-
-__device__ inline void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Position of a chunk in the warp's stream: block row bb, first block base.
-struct ChunkPos {
-  int64_t bb, base;
-};
-
-__device__ inline ChunkPos next_chunk(ChunkPos c, const int64_t* __restrict__ brp, int64_t b1) {
-  const int64_t e = __ldg(brp + c.bb + 1);
-  if (c.base + kChunk < e) return {c.bb, c.base + kChunk};
-  const int64_t nb = c.bb + kSpmmWarps;
-  if (nb >= b1) return {b1, 0};
-  return {nb, __ldg(brp + nb)};
-}
-
-template <int G>
-__global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t nblk,
-                                                            const int64_t* __restrict__ brp,
-                                                            const int32_t* __restrict__ bcol,
-                                                            const float4* __restrict__ bval,
-                                                            const float4* __restrict__ P, float4* __restrict__ Q,
-                                                            double* __restrict__ part, const gp::CgState* st) {
-  const int it = st->iter;
-  if (st->fin[it & 1]) return;
-  constexpr int NG = 32 / G;
-  constexpr int KP = 4 * G;
-  constexpr int kStage = kChunk * (KP + kBR);  // floats per stage buffer
-  extern __shared__ float4 smem_f4[];
-  float* stage = (float*)smem_f4 + (size_t)(threadIdx.x >> 5) * 2 * kStage;
-  __shared__ double sh[kSpmmWarps][KP];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int grp = lane / G, gl = lane - grp * G;
-  const bool act = grp < NG;
-  gpd::Dot2 pq0, pq1, pq2, pq3;
-  // Work split by stored blocks, not by block rows (cluster cores hold many
-  // times more blocks per row than the background).
-  const int64_t nent = brp[nblk];
-  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * blockIdx.x / gridDim.x);
-  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (blockIdx.x + 1) / gridDim.x);
-  const int64_t b0 = cb0 + w;
-  if (b0 < b1) {
-    // stage a chunk: consecutive lanes copy consecutive 16-byte pieces of the
-    // same P row (G pieces per row, so one copy instruction covers about 32/G
-    // rows), then the chunk's block values (2 float4 each, contiguous)
-    auto issue = [&](ChunkPos c, int jl, int buf) {
-      if (c.bb < b1) {
-        const int64_t e = __ldg(brp + c.bb + 1);
-        const int cnt = (int)min((int64_t)kChunk, e - c.base);
-        float* dst = stage + buf * kStage;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-          const int q = lane + 32 * i;  // piece q: entry q / G, slot q % G
-          const int ent = q / G;
-          const int j = __shfl_sync(kFull, jl, ent < 32 ? ent : 31);
-          if (ent < cnt) cp_async16(dst + ent * KP + 4 * (q - ent * G), P + (int64_t)j * G + (q - ent * G));
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int q = lane + 32 * i;
-          if (q < 2 * cnt) cp_async16(dst + kChunk * KP + 4 * q, bval + 2 * c.base + q);
-        }
-      }
-      cp_async_commit();
-    };
-    auto col_of = [&](ChunkPos c) -> int {
-      if (c.bb >= b1) return 0;
-      const int64_t idx = c.base + lane;
-      return idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
-    };
-    ChunkPos cur{b0, __ldg(brp + b0)};
-    ChunkPos nx1 = next_chunk(cur, brp, b1);
-    issue(cur, col_of(cur), 0);
-    int j1 = col_of(nx1);
-    // accumulators as float2 pairs (columns x,y and z,w of the lane's float4)
-    // for the packed two-wide FP32 FMA, which rounds each half like fmaf
-    float2 acc[2 * kBR];
-#pragma unroll
-    for (int r = 0; r < 2 * kBR; ++r) acc[r] = make_float2(0.f, 0.f);
-    int buf = 0;
-    while (cur.bb < b1) {
-      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp, b1) : nx1;
-      issue(nx1, j1, buf ^ 1);            // copies of chunk c+1 in flight
-      const int j2 = col_of(nx2);          // indices of chunk c+2 in flight
-      cp_async_wait<1>();                  // chunk c has landed
-      __syncwarp();
-      const int64_t e = __ldg(brp + cur.bb + 1);
-      const int cnt = (int)min((int64_t)kChunk, e - cur.base);
-      const float* sp = stage + buf * kStage;
-      const float* sv = sp + kChunk * KP;
-      constexpr int kSteps = (kChunk + NG - 1) / NG;
-#pragma unroll 2
-      for (int t = 0; t < kSteps; ++t) {
-        const int src = t * NG + grp;
-        if (act && src < cnt) {
-          const float4 pj = *(const float4*)(sp + src * KP + 4 * gl);
-          const float4 v0 = *(const float4*)(sv + src * kBR);
-          const float4 v1 = *(const float4*)(sv + src * kBR + 4);
-          const float vv[kBR] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-          const float2 plo = make_float2(pj.x, pj.y), phi = make_float2(pj.z, pj.w);
-#pragma unroll
-          for (int r = 0; r < kBR; ++r) {
-            const float2 v2 = make_float2(vv[r], vv[r]);
-            acc[2 * r] = __ffma2_rn(v2, plo, acc[2 * r]);
-            acc[2 * r + 1] = __ffma2_rn(v2, phi, acc[2 * r + 1]);
-          }
-        }
-      }
-      __syncwarp();  // buffer `buf` may be refilled from the next iteration on
-      if (cur.base + kChunk >= e) {
-        // last chunk of block row cur.bb: group 0 adds the other groups' sums
-#pragma unroll
-        for (int r = 0; r < 2 * kBR; ++r) {
-          const float2 q0 = acc[r];
-#pragma unroll
-          for (int g2 = 1; g2 < NG; ++g2) {
-            const int src = gl + g2 * G;
-            acc[r].x += __shfl_sync(kFull, q0.x, src);
-            acc[r].y += __shfl_sync(kFull, q0.y, src);
-          }
-        }
-        if (grp == 0) {
-#pragma unroll
-          for (int r = 0; r < kBR; ++r) {
-            const int64_t row = cur.bb * kBR + r;
-            if (row < n) {
-              const float4 qv = make_float4(acc[2 * r].x, acc[2 * r].y, acc[2 * r + 1].x, acc[2 * r + 1].y);
-              Q[row * G + gl] = qv;
-              const float4 pp = __ldg(P + row * G + gl);
-              pq0.add(pp.x, qv.x);
-              pq1.add(pp.y, qv.y);
-              pq2.add(pp.z, qv.z);
-              pq3.add(pp.w, qv.w);
-            }
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < 2 * kBR; ++r) acc[r] = make_float2(0.f, 0.f);
-      }
-      cur = nx1;
-      nx1 = nx2;
-      j1 = j2;
-      buf ^= 1;
-    }
-    cp_async_wait<0>();
-  }
-  if (grp == 0) {
-    sh[w][4 * gl + 0] = pq0.value();
-    sh[w][4 * gl + 1] = pq1.value();
-    sh[w][4 * gl + 2] = pq2.value();
-    sh[w][4 * gl + 3] = pq3.value();
-  }
-  __syncthreads();
-  if (threadIdx.x < KP) {
-    double t = 0.0;
-    for (int ww = 0; ww < kSpmmWarps; ++ww) t += sh[ww][threadIdx.x];
-    part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
-  }
-}
 
 constexpr int kUpdThreads = 256;
 constexpr int kRedThreads = 1024;
@@ -1109,32 +920,6 @@ unsigned grid_for(int64_t items, int per_block, int max_blocks) {
   return (unsigned)g;
 }
 
-typedef void (*SpmmFn)(int64_t, int64_t, const int64_t*, const int32_t*, const float4*, const float4*, float4*,
-                       double*, const gp::CgState*);
-
-SpmmFn spmm_for(int G) {
-  switch (G) {
-    case 1: return k_bspmm_f32<1>;
-    case 2: return k_bspmm_f32<2>;
-    case 3: return k_bspmm_f32<3>;
-    case 4: return k_bspmm_f32<4>;
-    case 5: return k_bspmm_f32<5>;
-    case 6: return k_bspmm_f32<6>;
-    case 7: return k_bspmm_f32<7>;
-    case 8: return k_bspmm_f32<8>;
-    case 9: return k_bspmm_f32<9>;
-    case 10: return k_bspmm_f32<10>;
-    case 11: return k_bspmm_f32<11>;
-    case 12: return k_bspmm_f32<12>;
-    case 13: return k_bspmm_f32<13>;
-    case 14: return k_bspmm_f32<14>;
-    case 15: return k_bspmm_f32<15>;
-    case 16: return k_bspmm_f32<16>;
-    case 17: return k_bspmm_f32<17>;
-    default: return nullptr;
-  }
-}
-
 int read_state(gp_ctx* c, gp::CgState* host) {
   GP_CHECK(gp::ensure_pinned(c, sizeof(gp::CgState)));
   GP_CUDA(cudaMemcpyAsync(c->pinned, c->cg.p, sizeof(gp::CgState), cudaMemcpyDeviceToHost, c->stream));
@@ -1153,9 +938,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   *iters_out = 0;
   *max_rel = 0.0;
   if (n == 0) return GP_OK;
-  const int G = kp / 4;
-  SpmmFn spmm = spmm_for(G);
-  if (!spmm || kp % 4) return GP_ERR_UNSUPPORTED;
+  if (!spmm_available(GP_SPMM_CPASYNC, kp)) return GP_ERR_UNSUPPORTED;
   GP_CHECK(ensure(c, c->X, (size_t)n * kp * sizeof(float)));
   GP_CHECK(ensure(c, c->R, (size_t)n * kp * sizeof(float)));
   GP_CHECK(ensure(c, c->P, (size_t)n * kp * sizeof(float)));
@@ -1198,12 +981,11 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     c->launches += 2;
   }
   const int64_t nblk = c->nblk;
-  const size_t spmm_smem = (size_t)kSpmmWarps * 2 * kChunk * (kp + kBR) * sizeof(float);
-  GP_CUDA(cudaFuncSetAttribute(spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmm_smem));
-  int spmm_per_sm = 0;
-  GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spmm_per_sm, spmm, kSpmmThreads, spmm_smem));
-  if (spmm_per_sm < 1) spmm_per_sm = 1;
-  const unsigned g_spmm = grid_for(nblk, kSpmmWarps, c->num_sms * spmm_per_sm);
+  // the SpMM form: forced by the flags, else the autotuner's for this shape
+  SpmmPlan plan;
+  GP_CHECK(spmm_select(c, kp, c->flags, st, &plan));
+  c->spmm_variant = plan.variant;
+  const unsigned g_spmm = plan.grid;
   const int ny = kUpdThreads / kq;
   const unsigned g_upd = grid_for(n, ny, c->num_sms * 8);
   const int ny_r = kUpdRThreads / kq;
@@ -1219,9 +1001,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   auto launch_iteration = [&](cudaStream_t sm, cudaEvent_t ev0, cudaEvent_t ev1) {
     const unsigned evf = sm == c->cap_stream ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (ev0) cudaEventRecordWithFlags(ev0, sm, evf);
-    spmm<<<g_spmm, kSpmmThreads, spmm_smem, sm>>>(n, nblk, (const int64_t*)c->brp.p, (const int32_t*)c->bcol.p,
-                                                 (const float4*)c->bval.p, (const float4*)c->P.p, (float4*)c->Q.p,
-                                                 (double*)c->part_a.p, st);
+    spmm_launch(plan, sm, c, st);
     if (ev1) cudaEventRecordWithFlags(ev1, sm, evf);
     k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
                                           (double*)c->hist_alpha.p, m_hist);
@@ -1246,8 +1026,8 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   {
     const uint64_t key[32] = {(uint64_t)n, (uint64_t)nblk, (uint64_t)k, (uint64_t)kp, (uint64_t)pc,
                               (uint64_t)c->pc_block, (uint64_t)g_spmm, (uint64_t)g_pc, (uint64_t)g_upd,
-                              (uint64_t)g_upd_r, (uint64_t)m_hist, (uint64_t)check_every, (uint64_t)spmm_smem,
-                              (uint64_t)pc_smem, (uint64_t)(uintptr_t)spmm, (uint64_t)(uintptr_t)c->brp.p,
+                              (uint64_t)g_upd_r, (uint64_t)m_hist, (uint64_t)check_every, (uint64_t)plan.smem,
+                              (uint64_t)pc_smem, (uint64_t)(uintptr_t)plan.fn, (uint64_t)(uintptr_t)c->brp.p,
                               (uint64_t)(uintptr_t)c->bcol.p, (uint64_t)(uintptr_t)c->bval.p,
                               (uint64_t)(uintptr_t)c->P.p, (uint64_t)(uintptr_t)c->Q.p, (uint64_t)(uintptr_t)c->R.p,
                               (uint64_t)(uintptr_t)c->X.p, (uint64_t)(uintptr_t)c->Z.p,

@@ -33,6 +33,14 @@ GP_FP64 = 0
 GP_FP32_MIXED = 1
 
 GP_FLAG_TIME_KERNELS = 1
+GP_FLAG_SPMM_CPASYNC = 2
+GP_FLAG_SPMM_TMA = 4
+GP_FLAG_SPMM_TMA_WIDE = 8
+
+GP_SPMM_CPASYNC = 0
+GP_SPMM_TMA = 1
+GP_SPMM_TMA_WIDE = 2
+SPMM_FLAGS = {"cpasync": GP_FLAG_SPMM_CPASYNC, "tma": GP_FLAG_SPMM_TMA, "tma_wide": GP_FLAG_SPMM_TMA_WIDE}
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
             "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_lml", "gp_lml_grad", "gp_lml_grad_batched",
@@ -60,7 +68,7 @@ class Info(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("n_spmm", ctypes.c_int32), ("kp", ctypes.c_int32),
                 ("t_spmm_kernel_ms", ctypes.c_double), ("t_fill_kernel_ms", ctypes.c_double),
                 ("t_adjoint_kernel_ms", ctypes.c_double), ("lanczos_iters", ctypes.c_int32),
-                ("precond_block", ctypes.c_int32)]
+                ("precond_block", ctypes.c_int32), ("spmm_variant", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -50,3 +50,18 @@ def test_create_rejects_bad_descriptors_before_touching_a_device():
         assert lib.gp_create(ctypes.byref(h), ctypes.byref(bad), 0, None) == G.GP_ERR_INVALID_ARG
     for big in [G.KernelDesc(4, 1, 1, 1.0), G.KernelDesc(2, 33, 1, 1.0), G.KernelDesc(2, 32, 17, 1.0)]:
         assert lib.gp_create(ctypes.byref(h), ctypes.byref(big), 0, None) == G.GP_ERR_UNSUPPORTED
+
+
+def test_header_constants_and_info_layout_match_the_binding():
+    text = open(HEADER).read()
+    defines = dict(re.findall(r"^#define\s+(GP_\w+)\s+(\d+)\b", text, re.M))
+    for name, value in defines.items():
+        if hasattr(G, name):
+            assert getattr(G, name) == int(value), name
+    for name in ("GP_FLAG_SPMM_CPASYNC", "GP_FLAG_SPMM_TMA", "GP_FLAG_SPMM_TMA_WIDE", "GP_SPMM_CPASYNC",
+                 "GP_SPMM_TMA", "GP_SPMM_TMA_WIDE"):
+        assert name in defines and hasattr(G, name), name
+    # gp_info's members in declaration order equal the ctypes mirror's fields
+    body = text[text.index("typedef struct {\n  int64_t n;"):text.index("} gp_info;")]
+    members = re.findall(r"^\s*(?:int64_t|int32_t|double)\s+(\w+);", body, re.M)
+    assert members == [f for f, _ in G.Info._fields_]
