@@ -302,22 +302,26 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
 }
 
 // B with the block-Jacobi preconditioner M (diagonal blocks of B rows of
-// Khat; B divides the 32-row tile, so a tile holds whole blocks):
+// Khat; B divides the 64-row tile, so a tile holds whole blocks):
 //   INIT:  Z = M^-1 R written to P (the first search direction)
 //   else:  R -= alpha Q, Z = M^-1 R
 // and per-block partials of rho = r^T z (columns 0..kp-1) and |r|^2
 // (columns kp..2kp-1) in one row of 2 kp doubles per block.
 //
-// A block of 32 kq threads walks its tiles with a 3-stage cp.async pipeline
-// (tiles i+1 and i+2 in flight while tile i is computed).  Thread t copies
-// and updates element t of the tile-linear layout (row t / kq, float4 slot
-// t % kq), so it can use its own R and Q right after its own copies land.
-// The block product runs with warp w on float4 slot w and lane r on row r,
-// reading row r of M^-1 as float4s from rows padded to B + 4 floats, so each
+// A block of 32 kq threads walks its 64-row tiles with a 3-stage cp.async
+// pipeline (tiles i+1 and i+2 in flight while tile i is computed).  Thread t
+// copies and updates elements t and t + 32 kq of the tile-linear layout (row
+// e / kq, float4 slot e % kq), so it can use its own R and Q right after its
+// own copies land.  The block product runs with warp w on float4 slot w and
+// lane l on rows 2l and 2l+1: each R row read from shared memory then feeds
+// two rows of M^-1, whose rows are stored pair-interleaved (for each four
+// columns, four of row 2l then four of row 2l+1; pair rows padded to 2B + 4
+// floats, so a quarter warp's 16-byte reads fall in distinct banks).  Each
 // thread's column sums stay in one slot across tiles and reduce with warp
 // shuffles at the end.
-constexpr int kPcTile = 32;
-constexpr int kPcMaxThreads = kPcTile * gp::kMaxCols / 4;
+constexpr int kPcLanes = 32;                       // threads per float4 slot
+constexpr int kPcTile = 2 * kPcLanes;              // rows per tile
+constexpr int kPcMaxThreads = kPcLanes * gp::kMaxCols / 4;
 constexpr int kPcStages = 3;
 
 __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
@@ -327,8 +331,8 @@ __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid
 }
 
 size_t pc_smem_bytes(int kq, int B) {
-  const size_t nthr = (size_t)kPcTile * kq;
-  return 16 * nthr * (2 * kPcStages + 1) + 4 * (size_t)kPcStages * kPcTile * (B + 4);
+  const size_t tile4 = (size_t)kPcTile * kq;  // float4 per R (or Q, Z) tile
+  return 16 * tile4 * (2 * kPcStages + 1) + 4 * (size_t)kPcStages * (kPcTile / 2) * (2 * B + 4);
 }
 
 template <bool INIT>
@@ -339,39 +343,44 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
   if (!INIT && st->fin[st->iter & 1]) return;
   extern __shared__ float4 pc_smem[];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int nthr = kPcTile * kq;
-  const int ldm = B + 4;
-  float4* Rs = pc_smem;                         // kPcStages x nthr
-  float4* Qs = Rs + kPcStages * nthr;           // kPcStages x nthr
-  float4* Zs = Qs + kPcStages * nthr;           // nthr
-  float* Ms = (float*)(Zs + nthr);              // kPcStages x 32 x ldm
+  const int nthr = kPcLanes * kq;
+  const int tile4 = 2 * nthr;                   // float4 per tile = kPcTile * kq
+  const int ldp = 2 * B + 4;                    // floats per pair row of M^-1
+  float4* Rs = pc_smem;                         // kPcStages x tile4
+  float4* Qs = Rs + kPcStages * tile4;          // kPcStages x tile4
+  float4* Zs = Qs + kPcStages * tile4;          // tile4
+  float* Ms = (float*)(Zs + tile4);             // kPcStages x 32 pair rows x ldp
   const int64_t ntiles = (n + kPcTile - 1) / kPcTile;
   const int64_t nrows_pc = (n + B - 1) / B * B;  // rows covered by stored blocks
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!INIT) {
-    const int q = t % kq;
+    const int q = t % kq;  // also the slot of element t + nthr (nthr is a multiple of kq)
     a = make_float4((float)st->alpha[4 * q], (float)st->alpha[4 * q + 1], (float)st->alpha[4 * q + 2],
                     (float)st->alpha[4 * q + 3]);
   }
   auto issue = [&](int64_t tile, int s) {
     if (tile < ntiles) {
       const int64_t r0 = tile * kPcTile;
-      const bool ok = r0 + t / kq < n;
-      const int64_t src = ok ? r0 * kq + t : 0;
-      cp_async16_zfill(Rs + s * nthr + t, R + src, ok);
-      if (!INIT) cp_async16_zfill(Qs + s * nthr + t, Q + src, ok);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = t + h * nthr;
+        const bool ok = r0 + e / kq < n;
+        const int64_t src = ok ? r0 * kq + e : 0;
+        cp_async16_zfill(Rs + s * tile4 + e, R + src, ok);
+        if (!INIT) cp_async16_zfill(Qs + s * tile4 + e, Q + src, ok);
+      }
       const int c4n = B / 4;
       for (int e = t; e < kPcTile * c4n; e += nthr) {
         const int r = e / c4n, c4 = e - r * c4n;
         const bool okm = r0 + r < nrows_pc;
         const float* srcm = Minv + (okm ? (r0 + r) * B + 4 * c4 : 0);
-        cp_async16_zfill(Ms + (s * kPcTile + r) * ldm + 4 * c4, srcm, okm);
+        cp_async16_zfill(Ms + (s * (kPcTile / 2) + (r >> 1)) * ldp + 8 * c4 + 4 * (r & 1), srcm, okm);
       }
     }
     cp_async_commit();  // empty groups past the end keep the group count uniform
   };
   gpd::Dot2 rz[4], rr[4];
-  const int kb = (lane / B) * B;  // first tile row of this lane's block
+  const int kb = ((2 * lane) / B) * B;  // first tile row of this lane's block
   int64_t tile = blockIdx.x;
   issue(tile, 0);
   issue(tile + gridDim.x, 1);
@@ -380,47 +389,71 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
     issue(tile + 2 * (int64_t)gridDim.x, (i + 2) % kPcStages);
     cp_async_wait<2>();  // this thread's copies of tile i have landed
     const int64_t r0 = tile * kPcTile;
-    const bool ok = r0 + t / kq < n;
     if (!INIT) {
-      float4 v = Rs[s * nthr + t];
-      const float4 qv = Qs[s * nthr + t];
-      v.x = fmaf(-a.x, qv.x, v.x);
-      v.y = fmaf(-a.y, qv.y, v.y);
-      v.z = fmaf(-a.z, qv.z, v.z);
-      v.w = fmaf(-a.w, qv.w, v.w);
-      Rs[s * nthr + t] = v;
-      if (ok) R[r0 * kq + t] = v;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = t + h * nthr;
+        float4 v = Rs[s * tile4 + e];
+        const float4 qv = Qs[s * tile4 + e];
+        v.x = fmaf(-a.x, qv.x, v.x);
+        v.y = fmaf(-a.y, qv.y, v.y);
+        v.z = fmaf(-a.z, qv.z, v.z);
+        v.w = fmaf(-a.w, qv.w, v.w);
+        Rs[s * tile4 + e] = v;
+        if (r0 + e / kq < n) R[r0 * kq + e] = v;
+      }
     }
     __syncthreads();
     {
-      const float4* Rt = Rs + s * nthr;
-      const float* mrow = Ms + (s * kPcTile + lane) * ldm;
-      const float4 rv = Rt[lane * kq + w];
-      float2 zlo = make_float2(0.f, 0.f), zhi = make_float2(0.f, 0.f);
+      const float4* Rt = Rs + s * tile4;
+      const float* mrow = Ms + (s * (kPcTile / 2) + lane) * ldp;
+      const float4 rv0 = Rt[(2 * lane) * kq + w];
+      const float4 rv1 = Rt[(2 * lane + 1) * kq + w];
+      float2 z0lo = make_float2(0.f, 0.f), z0hi = make_float2(0.f, 0.f);
+      float2 z1lo = make_float2(0.f, 0.f), z1hi = make_float2(0.f, 0.f);
       for (int k = 0; k < B; k += 4) {
-        const float4 m = *(const float4*)(mrow + k);
-        const float mk[4] = {m.x, m.y, m.z, m.w};
+        const float4 m0 = *(const float4*)(mrow + 2 * k);      // row 2l, columns k..k+3
+        const float4 m1 = *(const float4*)(mrow + 2 * k + 4);  // row 2l+1
+        const float mk0[4] = {m0.x, m0.y, m0.z, m0.w};
+        const float mk1[4] = {m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float4 x = Rt[(kb + k + u) * kq + w];
-          const float2 m2 = make_float2(mk[u], mk[u]);
-          zlo = __ffma2_rn(m2, make_float2(x.x, x.y), zlo);
-          zhi = __ffma2_rn(m2, make_float2(x.z, x.w), zhi);
+          const float2 xlo = make_float2(x.x, x.y), xhi = make_float2(x.z, x.w);
+          const float2 a0 = make_float2(mk0[u], mk0[u]), a1 = make_float2(mk1[u], mk1[u]);
+          z0lo = __ffma2_rn(a0, xlo, z0lo);
+          z0hi = __ffma2_rn(a0, xhi, z0hi);
+          z1lo = __ffma2_rn(a1, xlo, z1lo);
+          z1hi = __ffma2_rn(a1, xhi, z1hi);
         }
       }
-      const float4 z = make_float4(zlo.x, zlo.y, zhi.x, zhi.y);
-      Zs[lane * kq + w] = z;
-      rz[0].add(rv.x, z.x);
-      rz[1].add(rv.y, z.y);
-      rz[2].add(rv.z, z.z);
-      rz[3].add(rv.w, z.w);
-      rr[0].add(rv.x, rv.x);
-      rr[1].add(rv.y, rv.y);
-      rr[2].add(rv.z, rv.z);
-      rr[3].add(rv.w, rv.w);
+      const float4 z0 = make_float4(z0lo.x, z0lo.y, z0hi.x, z0hi.y);
+      const float4 z1 = make_float4(z1lo.x, z1lo.y, z1hi.x, z1hi.y);
+      Zs[(2 * lane) * kq + w] = z0;
+      Zs[(2 * lane + 1) * kq + w] = z1;
+      rz[0].add(rv0.x, z0.x);
+      rz[1].add(rv0.y, z0.y);
+      rz[2].add(rv0.z, z0.z);
+      rz[3].add(rv0.w, z0.w);
+      rz[0].add(rv1.x, z1.x);
+      rz[1].add(rv1.y, z1.y);
+      rz[2].add(rv1.z, z1.z);
+      rz[3].add(rv1.w, z1.w);
+      rr[0].add(rv0.x, rv0.x);
+      rr[1].add(rv0.y, rv0.y);
+      rr[2].add(rv0.z, rv0.z);
+      rr[3].add(rv0.w, rv0.w);
+      rr[0].add(rv1.x, rv1.x);
+      rr[1].add(rv1.y, rv1.y);
+      rr[2].add(rv1.z, rv1.z);
+      rr[3].add(rv1.w, rv1.w);
     }
     __syncthreads();
-    if (ok) Z[r0 * kq + t] = Zs[t];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + h * nthr;
+      if (r0 + e / kq < n) Z[r0 * kq + e] = Zs[e];
+    }
   }
   cp_async_wait<0>();
   // rows beyond n were filled with zeros, so they added nothing above
@@ -973,7 +1006,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     g_pc = grid_for(n, kPcTile, c->num_sms * 2);
     GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
     GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * 2 * kp * sizeof(double)));
-    k_upd_r_pc<true><<<g_pc, kPcTile * kq, pc_smem, c->stream>>>(n, kq, c->pc_block, nullptr, (float4*)c->R.p,
+    k_upd_r_pc<true><<<g_pc, kPcLanes * kq, pc_smem, c->stream>>>(n, kq, c->pc_block, nullptr, (float4*)c->R.p,
                                                                  (float4*)c->P.p, (const float*)c->pc_Minv.p,
                                                                  (double*)c->part_b.p, st);
     k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, st);
@@ -1006,7 +1039,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
                                           (double*)c->hist_alpha.p, m_hist);
     if (pc) {
-      k_upd_r_pc<false><<<g_pc, kPcTile * kq, pc_smem, sm>>>(n, kq, c->pc_block, (const float4*)c->Q.p,
+      k_upd_r_pc<false><<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, c->pc_block, (const float4*)c->Q.p,
                                                               (float4*)c->R.p, (float4*)c->Z.p,
                                                               (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
       k_cg_beta<<<1, kRedThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, st,

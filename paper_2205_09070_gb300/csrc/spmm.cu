@@ -286,7 +286,15 @@ __device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigne
 // gather4 each, padded to 128 bytes), then its 32 blocks' values.
 constexpr int tma_group_bytes(int kq) { return (64 * kq + 127) / 128 * 128; }
 constexpr int tma_stage_bytes(int kq) { return (kChunk / 4) * tma_group_bytes(kq) + kChunk * kBR * 4; }
-constexpr size_t tma_smem_bytes(int kq) { return (size_t)kSpmmWarps * 2 * tma_stage_bytes(kq) + 128; }
+// stage buffers per warp: three (two chunks in flight while one is computed)
+// where three CTAs of four warps still fit an SM's 228 KB of shared memory
+// (with the per-CTA reservation), else two
+constexpr int tma_stages(int kq) {
+  return 3 * (kSpmmWarps * 3 * tma_stage_bytes(kq) + 128 + 1024 + 256) <= 228 * 1024 ? 3 : 2;
+}
+constexpr size_t tma_smem_bytes(int kq) {
+  return (size_t)kSpmmWarps * tma_stages(kq) * tma_stage_bytes(kq) + 128;
+}
 // float4 columns per lane of the wide form
 constexpr int wide_lw(int kq) { return (kq % 3 == 0 && kq >= 6) ? 3 : (kq % 2 == 0 && kq >= 4) ? 2 : 1; }
 // rows per pass of the wide form's cross-group sum (its scratch is one stage buffer)
@@ -300,9 +308,11 @@ constexpr int wide_rows_per_pass(int ng, int kq) {
 // Q = Khat P with TMA-filled stages.  KQ = kp / 4 float4 columns; each lane
 // holds LW of them for the 8 rows of a block row, a group of G = KQ / LW lanes
 // applies one block, NG = 32 / G groups work on different blocks of the same
-// block row.  Work split, chunking, prefetch depth and the p^T q partials as
-// in k_bspmm_f32.  A bounded wait that gives up records GP_ERR_TIMEOUT in the
-// CG state, waits (bounded) for the copies it issued, and leaves.
+// block row.  Work split, chunking and the p^T q partials as in k_bspmm_f32;
+// each warp keeps NS - 1 chunks in flight (TMA requests take longer to land
+// than per-lane copies, so the stage ring is deeper).  A bounded wait that
+// gives up records GP_ERR_TIMEOUT in the CG state, waits (bounded) for the
+// copies it issued, and leaves.
 template <int KQ, int LW>
 __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t nblk,
                                                             const int64_t* __restrict__ brp,
@@ -321,12 +331,12 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
   constexpr int GB = tma_group_bytes(KQ);
   constexpr int PB = (kChunk / 4) * GB;
   constexpr int SB = tma_stage_bytes(KQ);
+  constexpr int NS = tma_stages(KQ);
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar_s[kSpmmWarps][2];
-  __shared__ double shp[kSpmmWarps][32][4];
+  __shared__ __align__(8) uint64_t bar_s[kSpmmWarps][3];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned char* stage =
-      (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127) + (size_t)w * 2 * SB;
+      (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127) + (size_t)w * NS * SB;
   uint64_t* bar = bar_s[w];
   const int grp = lane / G, gl = lane - grp * G;
   const bool act = grp < NG;
@@ -335,8 +345,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
   const int slot = LW == 1 ? (lane < KQ ? lane : -1) : (lane < M * KQ ? lane % KQ : -1);
   gpd::Dot2 pq0, pq1, pq2, pq3;
   if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < NS; ++b) mbar_init(&bar[b], 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -369,10 +378,15 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
       const int64_t idx = c.base + lane;
       return idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
     };
-    ChunkPos cur{b0, __ldg(brp + b0)};
-    ChunkPos nx1 = next_chunk(cur, brp, b1);
-    issue(cur, col_of(cur), 0);
-    int j1 = col_of(nx1);
+    // chunk ring: pos[i] is chunk c+i; chunks c .. c+NS-2 are in flight or
+    // landed, the column indices of chunk c+NS-1 are in jn
+    ChunkPos pos[NS + 1];
+    pos[0] = ChunkPos{b0, __ldg(brp + b0)};
+#pragma unroll
+    for (int i = 1; i <= NS; ++i) pos[i] = pos[i - 1].bb < b1 ? next_chunk(pos[i - 1], brp, b1) : pos[i - 1];
+#pragma unroll
+    for (int i = 0; i < NS - 1; ++i) issue(pos[i], col_of(pos[i]), i);
+    int jn = col_of(pos[NS - 1]);
     float2 acc[kBR][2 * LW];
 #pragma unroll
     for (int r = 0; r < kBR; ++r)
@@ -380,10 +394,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
       for (int u = 0; u < 2 * LW; ++u) acc[r][u] = make_float2(0.f, 0.f);
     int buf = 0;
     bool failed = false;
-    while (cur.bb < b1) {
-      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp, b1) : nx1;
-      issue(nx1, j1, buf ^ 1);   // copies of chunk c+1 in flight
-      const int j2 = col_of(nx2);  // indices of chunk c+2 in flight
+    while (pos[0].bb < b1) {
+      const ChunkPos cur = pos[0];
+      issue(pos[NS - 1], jn, buf + NS - 1 < NS ? buf + NS - 1 : buf - 1);  // chunk c+NS-1 in flight
+      jn = col_of(pos[NS]);                                                // its successor's indices
       const bool ok = __all_sync(kFull, mbar_wait(&bar[buf], (phase >> buf) & 1u));
       if (!ok) {
         failed = true;
@@ -497,30 +511,35 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
 #pragma unroll
           for (int u = 0; u < 2 * LW; ++u) acc[r][u] = make_float2(0.f, 0.f);
       }
-      cur = nx1;
-      nx1 = nx2;
-      j1 = j2;
-      buf ^= 1;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) pos[i] = pos[i + 1];
+      pos[NS] = pos[NS].bb < b1 ? next_chunk(pos[NS], brp, b1) : pos[NS];
+      buf = buf + 1 < NS ? buf + 1 : 0;
     }
     if (failed) {
       if (lane == 0) atomicCAS(&st->status, GP_OK, GP_ERR_TIMEOUT);
       // the copies this warp issued must land before its shared memory goes
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < NS; ++b)
         if (inflight & (1u << b)) mbar_wait(&bar[b], (phase >> b) & 1u);
     }
   }
-  shp[w][lane][0] = slot >= 0 ? pq0.value() : 0.0;
-  shp[w][lane][1] = slot >= 0 ? pq1.value() : 0.0;
-  shp[w][lane][2] = slot >= 0 ? pq2.value() : 0.0;
-  shp[w][lane][3] = slot >= 0 ? pq3.value() : 0.0;
+  // per-lane partials in the warp's first stage buffer (every copy into it
+  // has landed), then summed per column in a fixed order
+  double* shp = (double*)stage;  // [32][4] of this warp
+  __syncwarp();
+  shp[4 * lane + 0] = slot >= 0 ? pq0.value() : 0.0;
+  shp[4 * lane + 1] = slot >= 0 ? pq1.value() : 0.0;
+  shp[4 * lane + 2] = slot >= 0 ? pq2.value() : 0.0;
+  shp[4 * lane + 3] = slot >= 0 ? pq3.value() : 0.0;
   __syncthreads();
   if (threadIdx.x < KP) {
     const int q = threadIdx.x >> 2, cc = threadIdx.x & 3;
+    const unsigned char* base = (const unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     double t = 0.0;
     for (int ww = 0; ww < kSpmmWarps; ++ww)
       for (int l = 0; l < 32; ++l) {
         const int sl = LW == 1 ? (l < KQ ? l : -1) : (l < M * KQ ? l % KQ : -1);
-        if (sl == q) t += shp[ww][l][cc];
+        if (sl == q) t += ((const double*)(base + (size_t)ww * NS * SB))[4 * l + cc];
       }
     part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
   }
