@@ -253,6 +253,34 @@ def dense_K(x, h, dim, n1, n2, beta=1.0, chunk=1024):
 
 
 # ----------------------------------------------------------------------------
+# Sec. 2.1: posterior mean at test points, kappa^T (K + V)^-1 y (prior mean 0)
+# ----------------------------------------------------------------------------
+
+def cross_K(xs, x, h, dim, n1, n2, beta=1.0):
+    """kappa[a, i] = k(xs_a, x_i) = A k~(|xs_a - x_i| / r_s) sum_m f_m(xs_a) f_m(x_i)
+    by brute force over all pairs (Eq. eq:bump_kernel with Eq. eq:kstat).  A
+    test point is not an observation, so no noise term enters."""
+    p = unpack_h(h, dim, n1, n2)
+    xs = np.asarray(xs, dtype=np.float64).reshape(-1, dim)
+    x = np.asarray(x, dtype=np.float64)
+    Fq, _ = bump_table(xs, h, dim, n1, n2, beta)
+    F, _ = bump_table(x, h, dim, n1, n2, beta)
+    d2 = np.sum((xs[:, None, :] - x[None, :, :]) ** 2, axis=2)
+    S = np.zeros(d2.shape)
+    for m in range(n1):
+        S += Fq[:, m][:, None] * F[:, m][None, :]
+    return np.where(d2 < p["r_s"] ** 2, p["A"] * kstat(np.sqrt(d2) / p["r_s"]) * S, 0.0)
+
+
+def predict_mean(x, y, h, xs, dim, n1, n2, beta=1.0):
+    """Posterior mean m(xs) = kappa^T K^-1 y (Sec. 2.1, with V = sigma_n^2 I
+    inside K and prior mean 0): dense K, dense solve, brute-force kappa."""
+    K = dense_K(x, h, dim, n1, n2, beta)
+    alpha = np.linalg.solve(K, np.asarray(y, dtype=np.float64))
+    return cross_K(xs, x, h, dim, n1, n2, beta) @ alpha
+
+
+# ----------------------------------------------------------------------------
 # Eq. (eqn:log_likelihood): exact LML and its exact gradient
 # ----------------------------------------------------------------------------
 

@@ -329,3 +329,59 @@ def test_same_probe_estimator_identities_and_statistics():
     se = np.std(info_s["slq_terms"]) / math.sqrt(nv)
     assert abs(info_s["logdet"] - 2 * np.sum(np.log(np.diag(np.linalg.cholesky(K))))) < 5 * se + 1e-8
     assert np.median(np.abs(g_s - g_x) / (np.abs(g_x) + 1e-3)) < 0.2
+
+
+# --------------------------------------------------------------------- posterior mean
+
+def test_cross_K_matches_pure_python_brute_force():
+    # pair by pair with plain loops: bump sums with math.exp, the strict
+    # support tests, k~ from the independent series where it has converged
+    x, y, h, dim, n1, n2 = small_problem(seed=31, n=40)
+    rng = np.random.default_rng(32)
+    xs = rng.uniform(-0.1, 1.1, (15, dim))
+    p = O.unpack_h(h, dim, n1, n2)
+    kappa = O.cross_K(xs, x, h, dim, n1, n2)
+
+    def f(pt, m):
+        tot = 0.0
+        for b in range(n2):
+            q = sum((pt[k] - p["centres"][m, b][k]) ** 2 for k in range(dim)) / p["radii"][m, b] ** 2
+            if q < 1.0:
+                tot += p["amps"][m, b] * math.exp(1.0 - 1.0 / (1.0 - q))
+        return tot
+
+    checked = 0
+    for a in range(len(xs)):
+        for i in range(len(x)):
+            d = math.dist(xs[a], x[i])
+            S = sum(f(xs[a], m) * f(x[i], m) for m in range(n1))
+            if d >= p["r_s"] or S == 0.0:
+                assert kappa[a, i] == 0.0
+                continue
+            rho = d / p["r_s"]
+            k = series_kstat(np.array([rho]), terms=4000)[0] if rho >= 0.3 else O.kstat(np.array([rho]))[0]
+            # the printed form of Eq. eq:kstat cancels as rho -> 1: entries
+            # there are tiny and carry an absolute error of order 1e-12 k~(0)
+            floor = 1e-12 * p["A"] * O.KSTAT_PREFACTOR * abs(S)
+            assert kappa[a, i] == pytest.approx(p["A"] * k * S, rel=1e-9, abs=floor)
+            checked += 1
+    assert checked > 20
+
+
+def test_predict_mean_at_training_points_and_outside_supports():
+    # K alpha = y with K = Kf + sigma2 I gives Kf alpha = y - sigma2 alpha:
+    # the posterior mean at the training inputs is y - sigma2 K^-1 y
+    x, y, h, dim, n1, n2 = small_problem(seed=33, n=120)
+    p = O.unpack_h(h, dim, n1, n2)
+    K = O.dense_K(x, h, dim, n1, n2)
+    alpha = np.linalg.solve(K, y)
+    m_train = O.predict_mean(x, y, h, x, dim, n1, n2)
+    assert np.allclose(m_train, y - p["sigma2"] * alpha, rtol=1e-10, atol=1e-12 * np.abs(y).max())
+    # points outside every bump, or farther than r_s from every training point,
+    # have an exactly zero mean
+    far = np.array([[5.0, 5.0], [-3.0, 0.5]])
+    assert np.array_equal(O.predict_mean(x, y, h, far, dim, n1, n2), np.zeros(2))
+    _, mask = O.bump_table(x, h, dim, n1, n2)
+    outside = x[mask == 0][:3]
+    if len(outside):
+        assert np.array_equal(O.predict_mean(x, y, h, outside, dim, n1, n2), np.zeros(len(outside)))
