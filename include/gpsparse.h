@@ -197,6 +197,23 @@ int gp_get_csr_noalloc(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
  * every bump decouple: alpha_i = y_i / sigma_n^2 there.  alpha: N doubles. */
 int gp_solve(gp_ctx* ctx, const double* y, double* alpha, const gp_opts* opts, gp_info* info);
 
+/* Posterior mean at test points (Sec. 2.1: m(x*) = kappa^T (K + V)^-1 y with
+ * kappa_i = k(x*, x_i) from Eq. eq:bump_kernel and zero prior mean; V =
+ * sigma_n^2 I is part of K).  Solves K alpha = y with the last assembled K
+ * exactly as gp_solve does (same opts), then for every test point sums
+ * k(x*, x_i) alpha_i over the training points within r_s of it that share the
+ * support of some f_m with it (a cell-list pass over the assembled grid, FP64
+ * throughout; no noise term, a test point is not an observation).
+ *   y:     N doubles (the training targets of the assembled points)
+ *   xstar: n_star x dim doubles, row-major; any coordinates (points outside the
+ *          training box or every bump get mean 0 where no pair is in support)
+ *   mean:  n_star doubles
+ * Arrays may be host or device.  Returns GP_ERR_NOT_ASSEMBLED before a
+ * gp_assemble, GP_ERR_NOT_CONVERGED (means still written) if CG hit max_iter.
+ * info (may be NULL) reports the solve as gp_solve does. */
+int gp_predict(gp_ctx* ctx, const double* y, const double* xstar, int64_t n_star, double* mean,
+               const gp_opts* opts, gp_info* info);
+
 /* Assemble K and evaluate ln L (Eq. eqn:log_likelihood) with
  * ln|K| = sum ln D + SLQ(D^-1/2 K D^-1/2) + N_inactive ln sigma_n^2, D = diag K.
  * The estimator does not depend on precond_block.  With B = precond_block > 0

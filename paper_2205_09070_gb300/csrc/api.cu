@@ -356,7 +356,8 @@ int gp_destroy(gp_ctx* c) {
                         &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
                         &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
-                        &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z};
+                        &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z,
+                        &c->xstar_in, &c->pred_tmp};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -434,6 +435,42 @@ int gp_get_csr(gp_ctx* c, int64_t* row_ptr, int32_t* col, double* val, int32_t* 
   return GP_OK;
 }
 
+namespace {
+
+// alpha = K^-1 y (original point order) into the device array out (c->n
+// doubles) with the last assembled K: CG on the Jacobi-scaled active block
+// (block-Jacobi preconditioned in FP32 when opts ask for it), y_i / sigma^2
+// on the rows outside every bump.
+int solve_alpha(gp_ctx* c, const double* yd, const gp_opts* o, double* out, int* iters, double* max_rel) {
+  GP_CHECK(gp::precond_setup(c, o->precond_block));
+  int st;
+  if (c->precision == GP_FP64)
+    st = gp::cg_run_fp64(c, 1, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, iters, max_rel);
+  else
+    st = gp::cg_run(c, 1, 4, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, iters, max_rel, true);
+  if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
+  if (c->n > 0) GP_CHECK(gp::alpha_out(c, yd, out, 4));
+  return st;
+}
+
+void solve_info(const gp_ctx* c, int iters, double max_rel, double ms, gp_info* info) {
+  memset(info, 0, sizeof(*info));
+  info->n = c->n;
+  info->n_active = c->n_act;
+  info->nnz = c->nnz;
+  info->iters = iters;
+  info->status_detail = -1;
+  info->max_rel_resid = max_rel;
+  info->t_solve_ms = ms;
+  info->cell_size = c->grid.h;
+  info->n_cells = c->grid.ncells;
+  info->kp = 4;
+  info->precond_block = c->pc_block;
+  fill_counters(c, info);
+}
+
+}  // namespace
+
 int gp_solve(gp_ctx* c, const double* y, double* alpha, const gp_opts* o, gp_info* info) {
   if (!c || !alpha || !o) return GP_ERR_INVALID_ARG;
   if (!c->assembled) return GP_ERR_NOT_ASSEMBLED;
@@ -445,41 +482,54 @@ int gp_solve(gp_ctx* c, const double* y, double* alpha, const gp_opts* o, gp_inf
   tm.mark(0);
   const double* yd = nullptr;
   GP_CHECK(stage_in(c, c->y_in, y, (size_t)c->n, &yd));
-  GP_CHECK(gp::precond_setup(c, o->precond_block));
-  int iters = 0;
-  double max_rel = 0.0;
-  int st;
-  if (c->precision == GP_FP64)
-    st = gp::cg_run_fp64(c, 1, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel);
-  else
-    st = gp::cg_run(c, 1, 4, yd, 0, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters, &max_rel, true);
-  if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
   double* out = alpha;
   const bool dev = gp::is_device_ptr(alpha);
   if (!dev) {
     GP_CHECK(gp::ensure(c, c->out_tmp, (size_t)c->n * sizeof(double)));
     out = (double*)c->out_tmp.p;
   }
-  if (c->n > 0) GP_CHECK(gp::alpha_out(c, yd, out, 4));
+  int iters = 0;
+  double max_rel = 0.0;
+  const int st = solve_alpha(c, yd, o, out, &iters, &max_rel);
+  if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
   if (!dev && c->n > 0)
     GP_CUDA(cudaMemcpyAsync(alpha, out, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   tm.mark(1);
   GP_CUDA(cudaStreamSynchronize(c->stream));
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->n = c->n;
-    info->n_active = c->n_act;
-    info->nnz = c->nnz;
-    info->iters = iters;
-    info->status_detail = -1;
-    info->max_rel_resid = max_rel;
-    info->t_solve_ms = tm.ms(0, 1);
-    info->cell_size = c->grid.h;
-    info->n_cells = c->grid.ncells;
-    info->kp = 4;
-    info->precond_block = c->pc_block;
-    fill_counters(c, info);
+  if (info) solve_info(c, iters, max_rel, tm.ms(0, 1), info);
+  return st;
+}
+
+int gp_predict(gp_ctx* c, const double* y, const double* xstar, int64_t n_star, double* mean, const gp_opts* o,
+               gp_info* info) {
+  if (!c || !o || n_star < 0 || (n_star > 0 && (!xstar || !mean))) return GP_ERR_INVALID_ARG;
+  if (!c->assembled) return GP_ERR_NOT_ASSEMBLED;
+  GP_CHECK(check_opts(o, false));
+  if (c->n > 0 && !y) return GP_ERR_INVALID_ARG;
+  GP_CUDA(cudaSetDevice(c->device));
+  reset_counters(c, o->flags);
+  Timer tm(c);
+  tm.mark(0);
+  const double *yd = nullptr, *xsd = nullptr;
+  GP_CHECK(stage_in(c, c->y_in, y, (size_t)c->n, &yd));
+  GP_CHECK(stage_in(c, c->xstar_in, xstar, (size_t)n_star * c->dim, &xsd));
+  GP_CHECK(gp::ensure(c, c->out_tmp, (size_t)(c->n > 0 ? c->n : 1) * sizeof(double)));
+  int iters = 0;
+  double max_rel = 0.0;
+  const int st = solve_alpha(c, yd, o, (double*)c->out_tmp.p, &iters, &max_rel);
+  if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
+  double* md = mean;
+  const bool dev = n_star > 0 && gp::is_device_ptr(mean);
+  if (!dev && n_star > 0) {
+    GP_CHECK(gp::ensure(c, c->pred_tmp, (size_t)n_star * sizeof(double)));
+    md = (double*)c->pred_tmp.p;
   }
+  GP_CHECK(gp::predict_mean(c, xsd, n_star, (const double*)c->out_tmp.p, md));
+  if (!dev && n_star > 0)
+    GP_CUDA(cudaMemcpyAsync(mean, md, (size_t)n_star * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  tm.mark(1);
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  if (info) solve_info(c, iters, max_rel, tm.ms(0, 1), info);
   return st;
 }
 

@@ -19,7 +19,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr double kPrefactor = 0.26596152026762182;  // sqrt(2) / (3 sqrt(pi)), Eq. eq:kstat
 
 // ------------------------------------------------------------------ bbox
 __global__ void __launch_bounds__(kThreads) k_bbox(const double* __restrict__ x, int64_t n, int dim,
@@ -128,17 +127,6 @@ __global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restric
 }
 
 // ------------------------------------------------------------------ cells
-__device__ inline void cell_of(const double* xi, const gp::Grid& g, int* c) {
-  for (int k = 0; k < gp::kMaxDim; ++k) c[k] = 0;
-  for (int k = 0; k < g.dim; ++k) {
-    double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h);
-    long long ci = (long long)floor(u);
-    ci = ci < 0 ? 0 : ci;
-    ci = ci > g.G[k] - 1 ? g.G[k] - 1 : ci;
-    c[k] = (int)ci;
-  }
-}
-
 __device__ inline uint32_t morton(const int* c, const gp::Grid& g) {
   uint32_t key = 0;
   int pos = 0;
@@ -178,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double* __restrict__ x,
     double xi[gp::kMaxDim] = {0, 0, 0};
     for (int k = 0; k < g.dim; ++k) xi[k] = x[i * g.dim + k];
     int c[gp::kMaxDim];
-    cell_of(xi, g, c);
+    gpd::cell_of(xi, g, c);
     int64_t a = pos[i];
     keys[a] = sort_key(xi, c, g);
     vals[a] = (uint32_t)i;
@@ -273,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ 
     double xi[gp::kMaxDim] = {0, 0, 0};
     for (int k = 0; k < g.dim; ++k) xi[k] = x[(int64_t)i * g.dim + k];
     int c[gp::kMaxDim];
-    cell_of(xi, g, c);
+    gpd::cell_of(xi, g, c);
     cellc[p] = make_int4(c[0], c[1], c[2], 0);
     float r[3] = {0.f, 0.f, 0.f};
     for (int k = 0; k < g.dim; ++k) {
@@ -849,7 +837,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   GP_CHECK(gp::ensure(c, c->dinv, (size_t)n_act * sizeof(T)));
   GP_CHECK(gp::ensure(c, c->dinv64, (size_t)n_act * sizeof(double)));
   GP_CHECK(gp::ensure(c, c->part_b, (size_t)maxb * sizeof(double)));
-  const double AC = c->A * kPrefactor;
+  const double AC = c->A * gp::kStatPrefactor;
   {
     unsigned gb = grid_for(n_act, kThreads, maxb);
     k_sorted<T><<<gb, kThreads, 0, c->stream>>>(x, n_act, (const uint32_t*)c->keys.p, (const uint32_t*)c->vals.p, g,

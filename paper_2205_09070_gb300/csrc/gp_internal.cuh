@@ -21,6 +21,7 @@ constexpr int kMaxProbes = 64;     // probe sign bits: two 32-bit words per row
 constexpr int kMaxCols = 68;       // 1 + n_probes, padded to a multiple of 4
 constexpr int kMaxLanczos = 64;
 constexpr int kScanItems = 4096;   // elements per block of the 3-phase scan
+constexpr double kStatPrefactor = 0.26596152026762182;  // sqrt(2) / (3 sqrt(pi)) = k~(0), Eq. eq:kstat
 
 // One bump of Eq. eq:bump, in the layout the kernels read.
 struct BumpParam {
@@ -129,6 +130,7 @@ struct gp_ctx {
 
   // device buffers (grow-only)
   gp::DevBuf x_in, y_in, out_tmp;
+  gp::DevBuf xstar_in, pred_tmp;  // gp_predict: staged test points, posterior means
   gp::DevBuf bump;
   gp::DevBuf mask0, F0, pos;
   gp::DevBuf keys, vals, keys2, vals2, hist, hist_scan, scan_part;
@@ -217,6 +219,10 @@ int alpha_out(gp_ctx* c, const double* y_dev, double* alpha_dev, int kp);
 // adjoint.cu
 int adjoint(gp_ctx* c, int n_probes, int kp);
 
+// predict.cu: posterior mean at ns test points (device arrays) from alpha =
+// K^-1 y in original point order (device, c->n doubles), over the last assembly.
+int predict_mean(gp_ctx* c, const double* xstar, int64_t ns, const double* alpha, double* mean);
+
 // spmm.cu: Q = Khat P on the 8x1 block CSR (c->brp, bcol, bval; P, Q, part_a
 // of the context), one launch per CG iteration.
 bool spmm_available(int variant, int kp);
@@ -230,6 +236,19 @@ void spmm_launch(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st);
 
 // ---------------------------------------------------------------- device utils
 namespace gpd {
+
+// Cell of a point in the uniform search grid: floor((x - lo) / h) per axis,
+// clamped to the grid (a point outside it lands in a boundary cell; the exact
+// distance test still decides every pair).
+__device__ inline void cell_of(const double* xi, const gp::Grid& g, int* c) {
+  for (int k = 0; k < gp::kMaxDim; ++k) c[k] = 0;
+  for (int k = 0; k < g.dim; ++k) {
+    double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h);
+    if (!(u >= 0.0)) u = 0.0;  // also NaN
+    if (u > (double)(g.G[k] - 1)) u = (double)(g.G[k] - 1);
+    c[k] = (int)floor(u);
+  }
+}
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the k-th output of the
 // stream whose state starts at `seed` is the finaliser applied to

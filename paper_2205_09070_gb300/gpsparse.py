@@ -43,8 +43,8 @@ GP_SPMM_TMA_WIDE = 2
 SPMM_FLAGS = {"cpasync": GP_FLAG_SPMM_CPASYNC, "tma": GP_FLAG_SPMM_TMA, "tma_wide": GP_FLAG_SPMM_TMA_WIDE}
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
-            "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_lml", "gp_lml_grad", "gp_lml_grad_batched",
-            "gp_status_string"]
+            "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_predict", "gp_lml", "gp_lml_grad",
+            "gp_lml_grad_batched", "gp_status_string"]
 
 
 class KernelDesc(ctypes.Structure):
@@ -109,6 +109,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gp_get_csr.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     lib.gp_get_csr_noalloc.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     lib.gp_solve.argtypes = [vp, dp, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    lib.gp_predict.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     lib.gp_lml.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(Info)]
     lib.gp_lml_grad.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double), dp,
@@ -118,7 +119,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gp_status_string.argtypes = [ctypes.c_int]
     lib.gp_status_string.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_destroy", "gp_set_stream", "gp_assemble", "gp_get_csr", "gp_get_csr_noalloc",
-                 "gp_solve", "gp_lml",
+                 "gp_solve", "gp_predict", "gp_lml",
                  "gp_lml_grad", "gp_lml_grad_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -251,6 +252,28 @@ class GP:
         allow = (GP_OK, GP_ERR_NOT_CONVERGED) if allow_not_converged else (GP_OK,)
         self._check(self._lib.gp_solve(self._h, yp, ap, ctypes.byref(o), ctypes.byref(info)), "gp_solve", allow)
         return alpha, info.as_dict()
+
+    def predict(self, y, xstar, mean=None, opts: Opts | None = None, allow_not_converged=False):
+        """Posterior mean at the test points xstar (n_star x dim) given the
+        targets y of the assembled points; mean is allocated like xstar's rows
+        if not given (numpy for host input, torch on the device for device input)."""
+        self._sync_stream()
+        o = opts or default_opts()
+        yp, yk = _ptr(y)
+        xp, xk = _ptr(xstar)
+        ns = int(xstar.shape[0])
+        if mean is None:
+            if isinstance(xstar, np.ndarray):
+                mean = np.zeros(ns, np.float64)
+            else:
+                import torch
+                mean = torch.zeros(ns, dtype=torch.float64, device=xstar.device)
+        mp, mk = _ptr(mean)
+        info = Info()
+        allow = (GP_OK, GP_ERR_NOT_CONVERGED) if allow_not_converged else (GP_OK,)
+        self._check(self._lib.gp_predict(self._h, yp, xp, ns, mp, ctypes.byref(o), ctypes.byref(info)),
+                    "gp_predict", allow)
+        return mean, info.as_dict()
 
     def lml(self, x, y, h, opts: Opts | None = None, allow_not_converged=False):
         self._sync_stream()
