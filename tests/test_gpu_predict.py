@@ -36,7 +36,7 @@ CASES = {
 }
 
 
-def test_points(p, n_new=700, seed=5):
+def query_points(p, n_new=700, seed=5):
     # fresh points over a box a little larger than the data, some training
     # points, and two points far outside everything
     rng = np.random.default_rng(seed)
@@ -52,7 +52,7 @@ def test_points(p, n_new=700, seed=5):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_predict_matches_oracle(G, case, prec):
     p = CASES[case]()
-    xs = test_points(p)
+    xs = query_points(p)
     gp = G.GP(p.dim, p.n1, p.n2, p.beta)
     x = torch.as_tensor(p.x, device="cuda")
     y = torch.as_tensor(p.y, device="cuda")
@@ -82,7 +82,7 @@ def test_predict_matches_oracle(G, case, prec):
 
 def test_predict_host_arrays_and_edge_cases(G):
     p = W.small_2d(seed=1)
-    xs = test_points(p, n_new=100)
+    xs = query_points(p, n_new=100)
     gp = G.GP(p.dim, p.n1, p.n2, p.beta)
     lib = G.load()
     mean = np.zeros(len(xs))
@@ -116,7 +116,7 @@ def test_predict_when_no_training_point_is_active(G):
     gp = G.GP(p.dim, p.n1, p.n2, p.beta)
     gp.assemble(torch.as_tensor(p.x, device="cuda"), h, precision="fp32")
     mean, info = gp.predict(torch.as_tensor(p.y, device="cuda"),
-                            torch.as_tensor(test_points(p, n_new=50), device="cuda"))
+                            torch.as_tensor(query_points(p, n_new=50), device="cuda"))
     assert info["n_active"] == 0
     assert torch.count_nonzero(mean).item() == 0
     gp.close()
