@@ -55,6 +55,9 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1200)
+    ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide"],
+                    help="SpMM form: the library's autotuner (auto) or a forced form; profiling runs force "
+                         "the form the plain run chose, since the tuner's timings are meaningless under ncu")
     return ap.parse_args()
 
 
@@ -227,8 +230,10 @@ def main():
     x = torch.as_tensor(p.x, device=dev)
     y = torch.as_tensor(p.y, device=dev)
     gp = GP(p.dim, p.n1, p.n2, p.beta, device=local)
+    from paper_2205_09070_gb300.gpsparse import SPMM_FLAGS
+    spmm_flag = SPMM_FLAGS.get(a.spmm, 0)
     opts = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
-                        max_iter=20000, flags=GP_FLAG_TIME_KERNELS)
+                        max_iter=20000, flags=GP_FLAG_TIME_KERNELS | spmm_flag)
 
     for _ in range(a.warmup):
         gp.lml_grad(x, y, p.h, opts)
@@ -285,7 +290,7 @@ def main():
     yh = torch.as_tensor(p.y).pin_memory()
     gh = torch.zeros(gp.n_params, dtype=torch.float64).pin_memory()
     opts_e2e = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
-                            max_iter=20000)
+                            max_iter=20000, flags=spmm_flag)
     e2e = None
     if a.e2e_steps > 0:
         gp.lml_grad(xh, yh, p.h, opts_e2e, grad=gh)
@@ -330,7 +335,7 @@ def main():
                 "data": "synthetic (seeded; stands in for the NOAA GHCN-Daily station-day data)",
                 "config": {"workload": p.name, "n": p.n, "dim": p.dim, "n_funcs": p.n1, "n_bumps": p.n2,
                            "r_s": float(p.h[-3]), "n_probes": 32, "lanczos_steps": 50, "cg_rtol": 1e-6,
-                           "precision": "FP32_MIXED", "parallelism": f"replicas x{world}",
+                           "precision": "FP32_MIXED", "parallelism": f"replicas x{world}", "spmm": a.spmm,
                            "l2": "working set larger than L2 (CSR re-assembled every step)",
                            "n_active": n_act, "nnz": nnz, "kp": kp, "cg_iters": infos[-1]["iters"],
                 "lanczos_iters": infos[-1]["lanczos_iters"], "precond_block": infos[-1]["precond_block"],

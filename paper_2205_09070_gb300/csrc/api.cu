@@ -220,9 +220,12 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
     const int lst = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->lanczos_steps, o->cg_rtol,
                                o->check_every, &lanczos_iters, &lanczos_rel, false);
     if (lst != GP_OK && lst != GP_ERR_NOT_CONVERGED) return lst;
-    GP_CHECK(gp::slq(c, nv, kp));
+    // the eigen-solves overlap the preconditioned run (side stream)
+    GP_CHECK(gp::slq(c, nv, kp, true));
     cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters,
                            &max_rel, true);
+    const int jst = gp::slq_join(c);
+    if (jst != GP_OK) return jst;
   }
   if (cg_status != GP_OK && cg_status != GP_ERR_NOT_CONVERGED) return cg_status;
   GP_CHECK(gp::quad_form(c, yd, kp));
@@ -348,6 +351,7 @@ int gp_destroy(gp_ctx* c) {
   if (!c) return GP_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->aux_stream) cudaStreamSynchronize(c->aux_stream);
   gp::DevBuf* bufs[] = {&c->x_in,   &c->y_in,   &c->out_tmp,    &c->bump,      &c->mask0,     &c->F0,
                         &c->pos,    &c->keys,   &c->vals,       &c->keys2,     &c->vals2,     &c->hist,
                         &c->hist_scan, &c->scan_part, &c->cells, &c->perm,     &c->skey,      &c->cellc,
@@ -357,7 +361,7 @@ int gp_destroy(gp_ctx* c) {
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
                         &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
                         &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z,
-                        &c->xstar_in, &c->pred_tmp};
+                        &c->xstar_in, &c->pred_tmp, &c->slq_steps};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -368,6 +372,9 @@ int gp_destroy(gp_ctx* c) {
   for (auto& gr : c->cg_graph)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  for (cudaEvent_t e : c->aux_ev)
+    if (e) cudaEventDestroy(e);
   for (gp_ctx* w : c->workers) gp_destroy(w);
   if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
   delete c;

@@ -54,16 +54,31 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const double* __restrict__ x,
     last = atomicInc(&s->ticket0, gridDim.x - 1) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    for (int k = 0; k < dim; ++k) {
-      double a = INFINITY, b = -INFINITY;
-      for (unsigned g = 0; g < gridDim.x; ++g) {
-        a = fmin(a, __ldcg(part + (g * gp::kMaxDim + k) * 2));
-        b = fmax(b, __ldcg(part + (g * gp::kMaxDim + k) * 2 + 1));
+  if (!last) return;
+  // the last block: every thread folds a strided share of the partials, then
+  // a tree per axis and side
+  __threadfence();
+  for (int k = 0; k < dim; ++k) {
+    for (int side = 0; side < 2; ++side) {
+      double v = side ? -INFINITY : INFINITY;
+      for (unsigned g = threadIdx.x; g < gridDim.x; g += blockDim.x) {
+        const double t = __ldcg(part + (g * gp::kMaxDim + k) * 2 + side);
+        v = side ? fmax(v, t) : fmin(v, t);
       }
-      s->bbox_lo[k] = a;
-      s->bbox_hi[k] = b;
+      sh[threadIdx.x] = v;
+      __syncthreads();
+      for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+          const double a = sh[threadIdx.x], b = sh[threadIdx.x + o];
+          sh[threadIdx.x] = side ? fmax(a, b) : fmin(a, b);
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        if (side) s->bbox_hi[k] = sh[0];
+        else s->bbox_lo[k] = sh[0];
+      }
+      __syncthreads();
     }
   }
 }

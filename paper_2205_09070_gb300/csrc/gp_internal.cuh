@@ -175,6 +175,12 @@ struct gp_ctx {
     uint64_t key[32] = {};
   } cg_graph[2];
   cudaStream_t cap_stream = nullptr;
+  // side stream for work that overlaps the CG loop (the SLQ eigen-solves):
+  // fork / join events, and the Lanczos step counts it reads
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t aux_ev[2] = {};
+  bool slq_pending = false;
+  gp::DevBuf slq_steps;
   // gp_lml_grad_batched workers: contexts of their own (stream, workspace,
   // graphs), created on first use and destroyed with this context
   std::vector<gp_ctx*> workers;
@@ -213,7 +219,11 @@ int cg_run_fp64(gp_ctx* c, int k, const double* y_dev, int n_probes, uint64_t se
                 int* iters_out, double* max_rel_resid);
 int inactive_terms(gp_ctx* c, const double* y_dev);
 int quad_form(gp_ctx* c, const double* y_dev, int kp);
-int slq(gp_ctx* c, int n_probes, int kcols);
+// SLQ terms from the recorded Lanczos coefficients; with overlap the eigen-
+// solves run on the context's side stream, and slq_join orders the context
+// stream after them (every caller joins before it returns).
+int slq(gp_ctx* c, int n_probes, int kcols, bool overlap = false);
+int slq_join(gp_ctx* c);
 int alpha_out(gp_ctx* c, const double* y_dev, double* alpha_dev, int kp);
 
 // adjoint.cu

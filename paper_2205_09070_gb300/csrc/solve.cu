@@ -4,15 +4,17 @@
 // by its step lengths alpha_t and direction updates beta_t).
 //
 // FP32_MIXED: one CG over the block [yhat, z_1 .. z_nv] (row-major, kp floats
-// per row).  Per iteration t three kernels:
-//   A  Q = Khat P on the 8x1 block CSR; per-block partial sums of p_c^T q_c
-//   B  every block reduces A's partials (fixed order) -> alpha_c;
-//      R -= alpha Q; per-block partial sums of |r_c|^2
-//   C  every block reduces A's and B's partials -> alpha_c, beta_c;
-//      X += alpha P_old, P = R + beta P_old; block 0 publishes the
-//      iteration-(t+1) residual norms, convergence flags and the stop flag
-// Scalars of iteration t live in parity slot t&1, so no kernel waits on
-// another and no block runs a serial tail; all reductions are deterministic.
+// per row).  Per iteration t five launches:
+//   A      Q = Khat P on the 8x1 block CSR (spmm.cu); per-CTA partials of p_c^T q_c
+//   alpha  one block reduces A's partials in a fixed order -> alpha_c
+//   B      R -= alpha Q (and Z = M^-1 R when preconditioned); partials of
+//          |r_c|^2 (and r_c^T z_c)
+//   beta   one block reduces B's partials -> beta_c, convergence flags, and
+//          publishes the iteration-(t+1) scalars
+//   C      X += alpha P_old, P = Z + beta P_old
+// Scalars of iteration t live in parity slot t&1 and every kernel reads the
+// iteration index from the device state, so one captured graph of launches
+// serves every iteration; all reductions are deterministic.
 // FP64: one single-RHS CG per column, all in FP64 (the plain comparison path),
 // with its scalars finished by the last block of each kernel.
 #include <math.h>
@@ -335,8 +337,8 @@ size_t pc_smem_bytes(int kq, int B) {
   return 16 * tile4 * (2 * kPcStages + 1) + 4 * (size_t)kPcStages * (kPcTile / 2) * (2 * B + 4);
 }
 
-template <bool INIT>
-__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, int B,
+template <bool INIT, int B>
+__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
                                                              const float4* __restrict__ Q, float4* __restrict__ R,
                                                              float4* __restrict__ Z, const float* __restrict__ Minv,
                                                              double* __restrict__ part, const gp::CgState* st) {
@@ -411,6 +413,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
       const float4 rv1 = Rt[(2 * lane + 1) * kq + w];
       float2 z0lo = make_float2(0.f, 0.f), z0hi = make_float2(0.f, 0.f);
       float2 z1lo = make_float2(0.f, 0.f), z1hi = make_float2(0.f, 0.f);
+#pragma unroll
       for (int k = 0; k < B; k += 4) {
         const float4 m0 = *(const float4*)(mrow + 2 * k);      // row 2l, columns k..k+3
         const float4 m1 = *(const float4*)(mrow + 2 * k + 4);  // row 2l+1
@@ -474,6 +477,18 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq, i
       prow[4 * w + j] = v[j];
       prow[kp + 4 * w + j] = v[4 + j];
     }
+  }
+}
+
+typedef void (*UpdPcFn)(int64_t, int, const float4*, float4*, float4*, const float*, double*, const gp::CgState*);
+
+template <bool INIT>
+UpdPcFn upd_pc_fn(int B) {
+  switch (B) {
+    case 8: return k_upd_r_pc<INIT, 8>;
+    case 16: return k_upd_r_pc<INIT, 16>;
+    case 32: return k_upd_r_pc<INIT, 32>;
+    default: return nullptr;
   }
 }
 
@@ -884,11 +899,11 @@ __device__ bool tridiag_ql(double* d, double* e, double* z, int m) {
 // T_t,t+1 = sqrt(beta_t)/alpha_t; Gamma_l = |z|^2 sum_k tau_k^2 ln theta_k.
 // The last block to finish forms the mean and variance over probes.
 __global__ void k_slq(int nv, int64_t n_act, const double* __restrict__ ha, const double* __restrict__ hb,
-                      const gp::CgState* st, double* gam, gp::AsmScalars* s) {
+                      const int* __restrict__ steps, double* gam, gp::AsmScalars* s) {
   const int l = blockIdx.x;
   if (threadIdx.x == 0) {
     const int c = 1 + l;
-    const int m = st->steps[c];
+    const int m = steps[c];
     double d[gp::kMaxLanczos], e[gp::kMaxLanczos], z[gp::kMaxLanczos];
     for (int t = 0; t < m; ++t) {
       const double at = ha[t * gp::kMaxCols + c];
@@ -994,19 +1009,23 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   }
   // block-Jacobi preconditioned CG: Z = M^-1 R, beta from r^T z, stop on |r|
   const bool pc = use_pc && c->pc_block > 0;
+  UpdPcFn upd_pc_init = nullptr, upd_pc = nullptr;
   const int kq = kp / 4;
   unsigned g_pc = 0;
   size_t pc_smem = 0;
   if (pc) {
     pc_smem = pc_smem_bytes(kq, c->pc_block);
-    GP_CUDA(cudaFuncSetAttribute(k_upd_r_pc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
-    GP_CUDA(cudaFuncSetAttribute(k_upd_r_pc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+    upd_pc_init = upd_pc_fn<true>(c->pc_block);
+    upd_pc = upd_pc_fn<false>(c->pc_block);
+    if (!upd_pc_init || !upd_pc) return GP_ERR_UNSUPPORTED;
+    GP_CUDA(cudaFuncSetAttribute(upd_pc_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+    GP_CUDA(cudaFuncSetAttribute(upd_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
     // two blocks per SM, two tiles each in flight: enough bytes in flight for
     // HBM without many partial rows for the one-block reduction
     g_pc = grid_for(n, kPcTile, c->num_sms * 2);
     GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
     GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * 2 * kp * sizeof(double)));
-    k_upd_r_pc<true><<<g_pc, kPcLanes * kq, pc_smem, c->stream>>>(n, kq, c->pc_block, nullptr, (float4*)c->R.p,
+    upd_pc_init<<<g_pc, kPcLanes * kq, pc_smem, c->stream>>>(n, kq, nullptr, (float4*)c->R.p,
                                                                  (float4*)c->P.p, (const float*)c->pc_Minv.p,
                                                                  (double*)c->part_b.p, st);
     k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, st);
@@ -1039,7 +1058,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
                                           (double*)c->hist_alpha.p, m_hist);
     if (pc) {
-      k_upd_r_pc<false><<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, c->pc_block, (const float4*)c->Q.p,
+      upd_pc<<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, (const float4*)c->Q.p,
                                                               (float4*)c->R.p, (float4*)c->Z.p,
                                                               (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
       k_cg_beta<<<1, kRedThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, st,
@@ -1223,7 +1242,7 @@ int quad_form(gp_ctx* c, const double* y, int kp) {
   return GP_OK;
 }
 
-int slq(gp_ctx* c, int nv, int kcols) {
+int slq(gp_ctx* c, int nv, int kcols, bool overlap) {
   (void)kcols;
   AsmScalars* s = (AsmScalars*)c->asm_s.p;
   if (c->n_act == 0) {
@@ -1231,10 +1250,40 @@ int slq(gp_ctx* c, int nv, int kcols) {
     return GP_OK;
   }
   GP_CHECK(ensure(c, c->slq_g, (size_t)2 * kMaxProbes * sizeof(double)));
-  k_slq<<<nv, 32, 0, c->stream>>>(nv, c->n_act, (const double*)c->hist_alpha.p, (const double*)c->hist_beta.p,
-                                  (const CgState*)c->cg.p, (double*)c->slq_g.p, s);
+  const int* steps = ((const CgState*)c->cg.p)->steps;
+  cudaStream_t sm = c->stream;
+  if (overlap) {
+    // the eigen-solves are serial FP64 work on 32 SMs: run them on the side
+    // stream while the next solve runs; they read the Lanczos coefficients
+    // (not written again before the join) and a copy of the step counts
+    if (!c->aux_stream) {
+      GP_CUDA(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+      GP_CUDA(cudaEventCreateWithFlags(&c->aux_ev[0], cudaEventDisableTiming));
+      GP_CUDA(cudaEventCreateWithFlags(&c->aux_ev[1], cudaEventDisableTiming));
+    }
+    GP_CHECK(ensure(c, c->slq_steps, (size_t)kMaxCols * sizeof(int)));
+    GP_CUDA(cudaMemcpyAsync(c->slq_steps.p, steps, (size_t)kMaxCols * sizeof(int), cudaMemcpyDeviceToDevice,
+                            c->stream));
+    GP_CUDA(cudaEventRecord(c->aux_ev[0], c->stream));
+    GP_CUDA(cudaStreamWaitEvent(c->aux_stream, c->aux_ev[0], 0));
+    steps = (const int*)c->slq_steps.p;
+    sm = c->aux_stream;
+  }
+  k_slq<<<nv, 32, 0, sm>>>(nv, c->n_act, (const double*)c->hist_alpha.p, (const double*)c->hist_beta.p, steps,
+                           (double*)c->slq_g.p, s);
   GP_LAUNCH_CHECK();
   c->launches += 1;
+  if (overlap) {
+    GP_CUDA(cudaEventRecord(c->aux_ev[1], c->aux_stream));
+    c->slq_pending = true;
+  }
+  return GP_OK;
+}
+
+int slq_join(gp_ctx* c) {
+  if (!c->slq_pending) return GP_OK;
+  c->slq_pending = false;
+  GP_CUDA(cudaStreamWaitEvent(c->stream, c->aux_ev[1], 0));
   return GP_OK;
 }
 

@@ -286,12 +286,11 @@ __device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigne
 // gather4 each, padded to 128 bytes), then its 32 blocks' values.
 constexpr int tma_group_bytes(int kq) { return (64 * kq + 127) / 128 * 128; }
 constexpr int tma_stage_bytes(int kq) { return (kChunk / 4) * tma_group_bytes(kq) + kChunk * kBR * 4; }
-// stage buffers per warp: three (two chunks in flight while one is computed)
-// where three CTAs of four warps still fit an SM's 228 KB of shared memory
-// (with the per-CTA reservation), else two
-constexpr int tma_stages(int kq) {
-  return 3 * (kSpmmWarps * 3 * tma_stage_bytes(kq) + 128 + 1024 + 256) <= 228 * 1024 ? 3 : 2;
-}
+// Stage buffers per warp (NS - 1 chunks in flight while one is computed).
+// Two: on the 1M-point mixture (kp = 36) a third buffer made the TMA forms
+// slower (narrow 462 -> 563 us, wide 422 -> 450 us per launch), since it costs
+// a CTA per SM and the gather4 requests, not their latency, set the pace.
+constexpr int tma_stages(int) { return 2; }
 constexpr size_t tma_smem_bytes(int kq) {
   return (size_t)kSpmmWarps * tma_stages(kq) * tma_stage_bytes(kq) + 128;
 }
@@ -309,10 +308,9 @@ constexpr int wide_rows_per_pass(int ng, int kq) {
 // holds LW of them for the 8 rows of a block row, a group of G = KQ / LW lanes
 // applies one block, NG = 32 / G groups work on different blocks of the same
 // block row.  Work split, chunking and the p^T q partials as in k_bspmm_f32;
-// each warp keeps NS - 1 chunks in flight (TMA requests take longer to land
-// than per-lane copies, so the stage ring is deeper).  A bounded wait that
-// gives up records GP_ERR_TIMEOUT in the CG state, waits (bounded) for the
-// copies it issued, and leaves.
+// each warp keeps NS - 1 chunks in flight in a ring of NS stage buffers.  A
+// bounded wait that gives up records GP_ERR_TIMEOUT in the CG state, waits
+// (bounded) for the copies it issued, and leaves.
 template <int KQ, int LW>
 __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t nblk,
                                                             const int64_t* __restrict__ brp,
@@ -333,7 +331,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
   constexpr int SB = tma_stage_bytes(KQ);
   constexpr int NS = tma_stages(KQ);
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar_s[kSpmmWarps][3];
+  __shared__ __align__(8) uint64_t bar_s[kSpmmWarps][NS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned char* stage =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127) + (size_t)w * NS * SB;
