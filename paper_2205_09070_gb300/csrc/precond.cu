@@ -2,8 +2,9 @@
 //
 // The active rows are in Morton / sub-cell order, so B consecutive rows are
 // close in space and strongly coupled.  M = blockdiag(Khat_bb) over blocks of
-// B consecutive rows; each block is factored in FP64 (one warp per block,
-// Cholesky M_bb = L L^T, then M_bb^-1 = L^-T L^-1) and M^-1 is stored in FP32,
+// B consecutive rows (B = 8, 16, 32 or 64); each block is factored in FP64
+// (one CTA of B threads per block, Cholesky M_bb = L L^T, then
+// M_bb^-1 = L^-T L^-1) and M^-1 is stored in FP32,
 // B x B row-major per block, zero outside the block's rows for the last,
 // shorter block.  Preconditioning changes only how fast CG converges: the
 // solves Khat u = b it feeds are the same.
@@ -13,32 +14,36 @@
 
 namespace {
 
-constexpr int kPcMax = 32;
-
-// One warp per diagonal block (grid-stride).  Lane i owns row i of the block.
-__global__ void __launch_bounds__(32) k_pc_setup(int64_t n, int B, int64_t nblk, const int64_t* __restrict__ rp,
-                                                 const int32_t* __restrict__ col, const float* __restrict__ val,
-                                                 float* __restrict__ Mout, int* __restrict__ part,
-                                                 gp::AsmScalars* s) {
-  __shared__ double A[kPcMax][kPcMax + 1];  // block of Khat, overwritten by L (lower)
-  __shared__ double Y[kPcMax][kPcMax + 1];  // L^-1 (lower)
-  const int lane = threadIdx.x;
+// One CTA of B threads per diagonal block (grid-stride); thread i owns row i
+// of the block.  A (the block of Khat, overwritten by L) and Y = L^-1 live in
+// dynamic shared memory, B x (B+1) doubles each.
+template <int B>
+__global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                float* __restrict__ Mout, int* __restrict__ part,
+                                                gp::AsmScalars* s) {
+  extern __shared__ double pc_sm[];
+  double (*A)[B + 1] = (double (*)[B + 1])pc_sm;
+  double (*Y)[B + 1] = (double (*)[B + 1])(pc_sm + B * (B + 1));
+  __shared__ int bad_any;
+  const int t = threadIdx.x;
+  if (t == 0) bad_any = 0;
   int bad = 0;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     const int64_t r0 = b * B;
     const int nb = (int)min((int64_t)B, n - r0);
-    for (int j = 0; j < kPcMax; ++j) A[lane][j] = 0.0;
-    if (lane < nb) {
-      const int64_t row = r0 + lane;
+    for (int j = 0; j < B; ++j) A[t][j] = 0.0;
+    if (t < nb) {
+      const int64_t row = r0 + t;
       for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
         const int64_t j = col[e];
-        if (j >= r0 && j < r0 + nb) A[lane][j - r0] = (double)val[e];
+        if (j >= r0 && j < r0 + nb) A[t][j - r0] = (double)val[e];
       }
     }
-    __syncwarp();
+    __syncthreads();
     // Cholesky, column by column (dot-product form, lower triangle only)
     for (int j = 0; j < nb; ++j) {
-      if (lane == j) {
+      if (t == j) {
         double d = A[j][j];
         for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
         if (!(d > 0.0)) {
@@ -47,56 +52,71 @@ __global__ void __launch_bounds__(32) k_pc_setup(int64_t n, int B, int64_t nblk,
         }
         A[j][j] = sqrt(d);
       }
-      __syncwarp();
-      if (lane > j && lane < nb) {
-        double t = A[lane][j];
-        for (int k = 0; k < j; ++k) t -= A[lane][k] * A[j][k];
-        A[lane][j] = t / A[j][j];
+      __syncthreads();
+      if (t > j && t < nb) {
+        double v = A[t][j];
+        for (int k = 0; k < j; ++k) v -= A[t][k] * A[j][k];
+        A[t][j] = v / A[j][j];
       }
-      __syncwarp();
+      __syncthreads();
     }
-    // Y = L^-1, lane c computes column c by forward substitution
-    for (int r = 0; r < kPcMax; ++r) Y[r][lane] = 0.0;
-    if (lane < nb) {
-      for (int r = lane; r < nb; ++r) {
-        double t = r == lane ? 1.0 : 0.0;
-        for (int k = lane; k < r; ++k) t -= A[r][k] * Y[k][lane];
-        Y[r][lane] = t / A[r][r];
+    // Y = L^-1, thread c computes column c by forward substitution
+    for (int r = 0; r < B; ++r) Y[r][t] = 0.0;
+    if (t < nb) {
+      for (int r = t; r < nb; ++r) {
+        double v = r == t ? 1.0 : 0.0;
+        for (int k = t; k < r; ++k) v -= A[r][k] * Y[k][t];
+        Y[r][t] = v / A[r][r];
       }
     }
-    __syncwarp();
-    // M^-1 = Y^T Y, row `lane`, FP32, zero outside nb x nb
+    __syncthreads();
+    // M^-1 = Y^T Y, row t, FP32, zero outside nb x nb
     float* Mb = Mout + b * (int64_t)B * B;
-    if (lane < B) {
-      for (int jj = 0; jj < B; ++jj) {
-        float m = 0.f;
-        if (lane < nb && jj < nb) {
-          double t = 0.0;
-          const int k0 = lane > jj ? lane : jj;
-          for (int k = k0; k < nb; ++k) t += Y[k][lane] * Y[k][jj];
-          m = (float)t;
-        }
-        Mb[lane * B + jj] = m;
+    for (int jj = 0; jj < B; ++jj) {
+      float m = 0.f;
+      if (t < nb && jj < nb) {
+        double v = 0.0;
+        const int k0 = t > jj ? t : jj;
+        for (int k = k0; k < nb; ++k) v += Y[k][t] * Y[k][jj];
+        m = (float)v;
       }
+      Mb[t * B + jj] = m;
     }
-    __syncwarp();
+    __syncthreads();
   }
-  // a failed block anywhere makes the status GP_ERR_NOT_SPD (last block decides)
-  bad = __reduce_or_sync(0xffffffffu, bad);
-  if (lane == 0) {
-    part[blockIdx.x] = bad;
+  // a failed block anywhere makes the status GP_ERR_NOT_SPD (last CTA decides)
+  if (bad) atomicOr(&bad_any, 1);
+  __syncthreads();
+  if (t == 0) {
+    part[blockIdx.x] = bad_any;
     __threadfence();
   }
   __shared__ bool last;
-  __syncwarp();
-  if (lane == 0) last = atomicInc(&s->ticket5, gridDim.x - 1) == gridDim.x - 1;
-  __syncwarp();
-  if (last && lane == 0) {
+  if (t == 0) last = atomicInc(&s->ticket5, gridDim.x - 1) == gridDim.x - 1;
+  __syncthreads();
+  if (last && t == 0) {
     __threadfence();
     int nbad = 0;
     for (unsigned q = 0; q < gridDim.x; ++q) nbad |= __ldcg(part + q);
     s->pc_status = nbad ? GP_ERR_NOT_SPD : GP_OK;
   }
+}
+
+template <int B>
+int launch_setup(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
+  const size_t smem = 2 * sizeof(double) * B * (B + 1);
+  GP_CUDA(cudaFuncSetAttribute(k_pc_setup<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc_setup<B>, B, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t cap = (int64_t)c->num_sms * per_sm;
+  const int64_t g = nblk < cap ? nblk : cap;
+  GP_CHECK(gp::ensure(c, c->pc_part, (size_t)g * sizeof(int)));
+  k_pc_setup<B><<<(unsigned)g, B, smem, c->stream>>>(c->n_act, nblk, (const int64_t*)c->row_ptr.p,
+                                                     (const int32_t*)c->col.p, (const float*)c->val.p,
+                                                     (float*)c->pc_Minv.p, (int*)c->pc_part.p, s);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
 }
 
 }  // namespace
@@ -109,15 +129,15 @@ int precond_setup(gp_ctx* c, int B) {
   AsmScalars* s = (AsmScalars*)c->asm_s.p;
   GP_CUDA(cudaMemsetAsync(&s->pc_status, 0, sizeof(int), c->stream));
   if (B == 0 || c->n_act == 0 || c->precision != GP_FP32_MIXED) return GP_OK;
-  if (B != 8 && B != 16 && B != 32) return GP_ERR_INVALID_ARG;
+  if (B != 8 && B != 16 && B != 32 && B != 64) return GP_ERR_INVALID_ARG;
   const int64_t nblk = (c->n_act + B - 1) / B;
   GP_CHECK(ensure(c, c->pc_Minv, (size_t)nblk * B * B * sizeof(float)));
-  const int64_t g = nblk < (int64_t)c->num_sms * 16 ? nblk : (int64_t)c->num_sms * 16;
-  GP_CHECK(ensure(c, c->pc_part, (size_t)g * sizeof(int)));
-  k_pc_setup<<<(unsigned)g, 32, 0, c->stream>>>(c->n_act, B, nblk, (const int64_t*)c->row_ptr.p,
-                                                (const int32_t*)c->col.p, (const float*)c->val.p,
-                                                (float*)c->pc_Minv.p, (int*)c->pc_part.p, s);
-  GP_LAUNCH_CHECK();
+  switch (B) {
+    case 8: GP_CHECK(launch_setup<8>(c, nblk, s)); break;
+    case 16: GP_CHECK(launch_setup<16>(c, nblk, s)); break;
+    case 32: GP_CHECK(launch_setup<32>(c, nblk, s)); break;
+    default: GP_CHECK(launch_setup<64>(c, nblk, s)); break;
+  }
   c->launches += 1;
   c->pc_block = B;
   c->pc_nblk = nblk;

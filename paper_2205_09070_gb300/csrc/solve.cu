@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
 // (columns kp..2kp-1) in one row of 2 kp doubles per block.
 //
 // A block of 32 kq threads walks its 64-row tiles with a 3-stage cp.async
-// pipeline (tiles i+1 and i+2 in flight while tile i is computed).  Thread t
+// pipeline (tiles i+1 and i+2 in flight while tile i is computed; one tile
+// ahead for B = 64).  Thread t
 // copies and updates elements t and t + 32 kq of the tile-linear layout (row
 // e / kq, float4 slot e % kq), so it can use its own R and Q right after its
 // own copies land.  The block product runs with warp w on float4 slot w and
@@ -324,7 +325,9 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
 constexpr int kPcLanes = 32;                       // threads per float4 slot
 constexpr int kPcTile = 2 * kPcLanes;              // rows per tile
 constexpr int kPcMaxThreads = kPcLanes * gp::kMaxCols / 4;
-constexpr int kPcStages = 3;
+// pipeline depth: 3 tiles per block in flight, 2 for 64-row blocks of M^-1
+// (their 16 KB per tile would otherwise leave one block per SM)
+constexpr int pc_stages(int B) { return B >= 64 ? 2 : 3; }
 
 __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -334,7 +337,8 @@ __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid
 
 size_t pc_smem_bytes(int kq, int B) {
   const size_t tile4 = (size_t)kPcTile * kq;  // float4 per R (or Q, Z) tile
-  return 16 * tile4 * (2 * kPcStages + 1) + 4 * (size_t)kPcStages * (kPcTile / 2) * (2 * B + 4);
+  const size_t S = pc_stages(B);
+  return 16 * tile4 * (2 * S + 1) + 4 * S * (kPcTile / 2) * (2 * B + 4);
 }
 
 template <bool INIT, int B>
@@ -343,6 +347,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
                                                              float4* __restrict__ Z, const float* __restrict__ Minv,
                                                              double* __restrict__ part, const gp::CgState* st) {
   if (!INIT && st->fin[st->iter & 1]) return;
+  constexpr int kPcStages = pc_stages(B);
   extern __shared__ float4 pc_smem[];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nthr = kPcLanes * kq;
@@ -384,12 +389,12 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
   gpd::Dot2 rz[4], rr[4];
   const int kb = ((2 * lane) / B) * B;  // first tile row of this lane's block
   int64_t tile = blockIdx.x;
-  issue(tile, 0);
-  issue(tile + gridDim.x, 1);
+#pragma unroll
+  for (int q = 0; q < kPcStages - 1; ++q) issue(tile + q * (int64_t)gridDim.x, q);
   for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
     const int s = i % kPcStages;
-    issue(tile + 2 * (int64_t)gridDim.x, (i + 2) % kPcStages);
-    cp_async_wait<2>();  // this thread's copies of tile i have landed
+    issue(tile + (kPcStages - 1) * (int64_t)gridDim.x, (i + kPcStages - 1) % kPcStages);
+    cp_async_wait<kPcStages - 1>();  // this thread's copies of tile i have landed
     const int64_t r0 = tile * kPcTile;
     if (!INIT) {
 #pragma unroll
@@ -488,6 +493,7 @@ UpdPcFn upd_pc_fn(int B) {
     case 8: return k_upd_r_pc<INIT, 8>;
     case 16: return k_upd_r_pc<INIT, 16>;
     case 32: return k_upd_r_pc<INIT, 32>;
+    case 64: return k_upd_r_pc<INIT, 64>;
     default: return nullptr;
   }
 }

@@ -122,7 +122,7 @@ def test_invalid_arguments_are_rejected(G):
             gp.lml(x, y, hb, opts(G))
         assert e.value.status == G.GP_ERR_INVALID_ARG
     for o in (opts(G, n_probes=0), opts(G, n_probes=65), opts(G, lanczos_steps=0), opts(G, max_iter=0),
-              opts(G, cg_rtol=0.0), opts(G, precision=7), opts(G, precond_block=5), opts(G, precond_block=64),
+              opts(G, cg_rtol=0.0), opts(G, precision=7), opts(G, precond_block=5), opts(G, precond_block=128),
               opts(G, batch_workers=-1), opts(G, batch_workers=17)):
         with pytest.raises(G.GPError) as e:
             gp.lml(x, y, p.h, o)
