@@ -127,7 +127,7 @@ int check_opts(const gp_opts* o, bool need_probes) {
   if (o->precision != GP_FP64 && o->precision != GP_FP32_MIXED) return GP_ERR_INVALID_ARG;
   if (o->max_iter < 1 || !(o->cg_rtol > 0.0) || !isfinite(o->cg_rtol)) return GP_ERR_INVALID_ARG;
   if (o->precond_block != 0 && o->precond_block != 8 && o->precond_block != 16 && o->precond_block != 32 &&
-      o->precond_block != 64)
+      o->precond_block != 64 && o->precond_block != 128)
     return GP_ERR_INVALID_ARG;
   if (o->batch_workers < 0 || o->batch_workers > 16) return GP_ERR_INVALID_ARG;
   if (need_probes) {

@@ -2,7 +2,7 @@
 //
 // The active rows are in Morton / sub-cell order, so B consecutive rows are
 // close in space and strongly coupled.  M = blockdiag(Khat_bb) over blocks of
-// B consecutive rows (B = 8, 16, 32 or 64); each block is factored in FP64
+// B consecutive rows (B = 8, 16, 32, 64 or 128); each block is factored in FP64
 // (one CTA of B threads per block, Cholesky M_bb = L L^T, then
 // M_bb^-1 = L^-T L^-1) and M^-1 is stored in FP32,
 // B x B row-major per block, zero outside the block's rows for the last,
@@ -10,13 +10,22 @@
 // solves Khat u = b it feeds are the same.
 #include <math.h>
 
+#include <type_traits>
+
 #include "gp_internal.cuh"
 
 namespace {
 
 // One CTA of B threads per diagonal block (grid-stride); thread i owns row i
-// of the block.  A (the block of Khat, overwritten by L) and Y = L^-1 live in
-// dynamic shared memory, B x (B+1) doubles each.
+// of the block.  A (the block of Khat, overwritten by L; FP64) and Y = L^-1
+// live in dynamic shared memory, B x (B+1) entries each.  Y is FP64 up to
+// B = 64 and FP32 for B = 128 (two FP64 128 x 128 blocks exceed an SM's
+// shared memory); its sums still run in FP64, and M^-1 is stored in FP32
+// either way: a preconditioner only has to be symmetric positive definite
+// and close to the block inverse.
+template <int B>
+using PcY = typename std::conditional<(B >= 128), float, double>::type;
+
 template <int B>
 __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const float* __restrict__ val,
@@ -24,7 +33,7 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
                                                 gp::AsmScalars* s) {
   extern __shared__ double pc_sm[];
   double (*A)[B + 1] = (double (*)[B + 1])pc_sm;
-  double (*Y)[B + 1] = (double (*)[B + 1])(pc_sm + B * (B + 1));
+  PcY<B> (*Y)[B + 1] = (PcY<B> (*)[B + 1])(pc_sm + B * (B + 1));
   __shared__ int bad_any;
   const int t = threadIdx.x;
   if (t == 0) bad_any = 0;
@@ -61,12 +70,12 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
       __syncthreads();
     }
     // Y = L^-1, thread c computes column c by forward substitution
-    for (int r = 0; r < B; ++r) Y[r][t] = 0.0;
+    for (int r = 0; r < B; ++r) Y[r][t] = 0;
     if (t < nb) {
       for (int r = t; r < nb; ++r) {
         double v = r == t ? 1.0 : 0.0;
-        for (int k = t; k < r; ++k) v -= A[r][k] * Y[k][t];
-        Y[r][t] = v / A[r][r];
+        for (int k = t; k < r; ++k) v -= A[r][k] * (double)Y[k][t];
+        Y[r][t] = (PcY<B>)(v / A[r][r]);
       }
     }
     __syncthreads();
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
       if (t < nb && jj < nb) {
         double v = 0.0;
         const int k0 = t > jj ? t : jj;
-        for (int k = k0; k < nb; ++k) v += Y[k][t] * Y[k][jj];
+        for (int k = k0; k < nb; ++k) v += (double)Y[k][t] * (double)Y[k][jj];
         m = (float)v;
       }
       Mb[t * B + jj] = m;
@@ -104,7 +113,7 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
 
 template <int B>
 int launch_setup(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
-  const size_t smem = 2 * sizeof(double) * B * (B + 1);
+  const size_t smem = (sizeof(double) + sizeof(PcY<B>)) * B * (B + 1);
   GP_CUDA(cudaFuncSetAttribute(k_pc_setup<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc_setup<B>, B, smem));
@@ -129,14 +138,15 @@ int precond_setup(gp_ctx* c, int B) {
   AsmScalars* s = (AsmScalars*)c->asm_s.p;
   GP_CUDA(cudaMemsetAsync(&s->pc_status, 0, sizeof(int), c->stream));
   if (B == 0 || c->n_act == 0 || c->precision != GP_FP32_MIXED) return GP_OK;
-  if (B != 8 && B != 16 && B != 32 && B != 64) return GP_ERR_INVALID_ARG;
+  if (B != 8 && B != 16 && B != 32 && B != 64 && B != 128) return GP_ERR_INVALID_ARG;
   const int64_t nblk = (c->n_act + B - 1) / B;
   GP_CHECK(ensure(c, c->pc_Minv, (size_t)nblk * B * B * sizeof(float)));
   switch (B) {
     case 8: GP_CHECK(launch_setup<8>(c, nblk, s)); break;
     case 16: GP_CHECK(launch_setup<16>(c, nblk, s)); break;
     case 32: GP_CHECK(launch_setup<32>(c, nblk, s)); break;
-    default: GP_CHECK(launch_setup<64>(c, nblk, s)); break;
+    case 64: GP_CHECK(launch_setup<64>(c, nblk, s)); break;
+    default: GP_CHECK(launch_setup<128>(c, nblk, s)); break;
   }
   c->launches += 1;
   c->pc_block = B;

@@ -304,29 +304,29 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
 }
 
 // B with the block-Jacobi preconditioner M (diagonal blocks of B rows of
-// Khat; B divides the 64-row tile, so a tile holds whole blocks):
+// Khat; B divides the tile of 32 RPL rows, so a tile holds whole blocks):
 //   INIT:  Z = M^-1 R written to P (the first search direction)
 //   else:  R -= alpha Q, Z = M^-1 R
 // and per-block partials of rho = r^T z (columns 0..kp-1) and |r|^2
 // (columns kp..2kp-1) in one row of 2 kp doubles per block.
 //
-// A block of 32 kq threads walks its 64-row tiles with a 3-stage cp.async
-// pipeline (tiles i+1 and i+2 in flight while tile i is computed; one tile
-// ahead for B = 64).  Thread t
-// copies and updates elements t and t + 32 kq of the tile-linear layout (row
-// e / kq, float4 slot e % kq), so it can use its own R and Q right after its
-// own copies land.  The block product runs with warp w on float4 slot w and
-// lane l on rows 2l and 2l+1: each R row read from shared memory then feeds
-// two rows of M^-1, whose rows are stored pair-interleaved (for each four
-// columns, four of row 2l then four of row 2l+1; pair rows padded to 2B + 4
-// floats, so a quarter warp's 16-byte reads fall in distinct banks).  Each
-// thread's column sums stay in one slot across tiles and reduce with warp
-// shuffles at the end.
+// A block of 32 kq threads walks its tiles with an S-stage cp.async pipeline
+// (S - 1 tiles in flight while one is computed).  Thread t copies and updates
+// elements t + h 32 kq (h < RPL) of the tile-linear layout (row e / kq,
+// float4 slot e % kq), so it can use its own R and Q right after its own
+// copies land.  The block product runs with warp w on float4 slot w and lane
+// l on rows RPL l .. RPL l + RPL - 1 (RPL = 2, or 4 for B = 128): each R row
+// read from shared memory then feeds RPL rows of M^-1, whose rows are stored
+// interleaved per lane (for each four columns, four of each of the lane's
+// rows in turn; lane rows padded to RPL B + 4 floats, so a quarter warp's
+// 16-byte reads fall in distinct banks).  Each thread's column sums stay in
+// one slot across tiles and reduce with warp shuffles at the end.
 constexpr int kPcLanes = 32;                       // threads per float4 slot
-constexpr int kPcTile = 2 * kPcLanes;              // rows per tile
 constexpr int kPcMaxThreads = kPcLanes * gp::kMaxCols / 4;
-// pipeline depth: 3 tiles per block in flight, 2 for 64-row blocks of M^-1
-// (their 16 KB per tile would otherwise leave one block per SM)
+constexpr int pc_rows_per_lane(int B) { return B >= 128 ? 4 : 2; }
+constexpr int pc_tile(int B) { return kPcLanes * pc_rows_per_lane(B); }
+// pipeline depth: 3 tiles per block in flight for B <= 32, 2 for larger
+// blocks of M^-1 (16 KB or 64 KB per tile)
 constexpr int pc_stages(int B) { return B >= 64 ? 2 : 3; }
 
 __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
@@ -336,9 +336,9 @@ __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid
 }
 
 size_t pc_smem_bytes(int kq, int B) {
-  const size_t tile4 = (size_t)kPcTile * kq;  // float4 per R (or Q, Z) tile
+  const size_t tile4 = (size_t)pc_tile(B) * kq;  // float4 per R (or Q, Z) tile
   const size_t S = pc_stages(B);
-  return 16 * tile4 * (2 * S + 1) + 4 * S * (kPcTile / 2) * (2 * B + 4);
+  return 16 * tile4 * (2 * S + 1) + 4 * S * kPcLanes * (pc_rows_per_lane(B) * B + 4);
 }
 
 template <bool INIT, int B>
@@ -348,46 +348,48 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
                                                              double* __restrict__ part, const gp::CgState* st) {
   if (!INIT && st->fin[st->iter & 1]) return;
   constexpr int kPcStages = pc_stages(B);
+  constexpr int RPL = pc_rows_per_lane(B);
+  constexpr int TILE = pc_tile(B);
   extern __shared__ float4 pc_smem[];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nthr = kPcLanes * kq;
-  const int tile4 = 2 * nthr;                   // float4 per tile = kPcTile * kq
-  const int ldp = 2 * B + 4;                    // floats per pair row of M^-1
+  const int tile4 = RPL * nthr;                 // float4 per tile = TILE * kq
+  constexpr int ldp = RPL * B + 4;              // floats per lane row block of M^-1
   float4* Rs = pc_smem;                         // kPcStages x tile4
   float4* Qs = Rs + kPcStages * tile4;          // kPcStages x tile4
   float4* Zs = Qs + kPcStages * tile4;          // tile4
-  float* Ms = (float*)(Zs + tile4);             // kPcStages x 32 pair rows x ldp
-  const int64_t ntiles = (n + kPcTile - 1) / kPcTile;
+  float* Ms = (float*)(Zs + tile4);             // kPcStages x 32 lane blocks x ldp
+  const int64_t ntiles = (n + TILE - 1) / TILE;
   const int64_t nrows_pc = (n + B - 1) / B * B;  // rows covered by stored blocks
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!INIT) {
-    const int q = t % kq;  // also the slot of element t + nthr (nthr is a multiple of kq)
+    const int q = t % kq;  // also the slot of elements t + h nthr (nthr is a multiple of kq)
     a = make_float4((float)st->alpha[4 * q], (float)st->alpha[4 * q + 1], (float)st->alpha[4 * q + 2],
                     (float)st->alpha[4 * q + 3]);
   }
   auto issue = [&](int64_t tile, int s) {
     if (tile < ntiles) {
-      const int64_t r0 = tile * kPcTile;
+      const int64_t r0 = tile * TILE;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < RPL; ++h) {
         const int e = t + h * nthr;
         const bool ok = r0 + e / kq < n;
         const int64_t src = ok ? r0 * kq + e : 0;
         cp_async16_zfill(Rs + s * tile4 + e, R + src, ok);
         if (!INIT) cp_async16_zfill(Qs + s * tile4 + e, Q + src, ok);
       }
-      const int c4n = B / 4;
-      for (int e = t; e < kPcTile * c4n; e += nthr) {
+      constexpr int c4n = B / 4;
+      for (int e = t; e < TILE * c4n; e += nthr) {
         const int r = e / c4n, c4 = e - r * c4n;
         const bool okm = r0 + r < nrows_pc;
         const float* srcm = Minv + (okm ? (r0 + r) * B + 4 * c4 : 0);
-        cp_async16_zfill(Ms + (s * (kPcTile / 2) + (r >> 1)) * ldp + 8 * c4 + 4 * (r & 1), srcm, okm);
+        cp_async16_zfill(Ms + (s * kPcLanes + r / RPL) * ldp + 4 * RPL * c4 + 4 * (r % RPL), srcm, okm);
       }
     }
     cp_async_commit();  // empty groups past the end keep the group count uniform
   };
   gpd::Dot2 rz[4], rr[4];
-  const int kb = ((2 * lane) / B) * B;  // first tile row of this lane's block
+  const int kb = ((RPL * lane) / B) * B;  // first tile row of this lane's block
   int64_t tile = blockIdx.x;
 #pragma unroll
   for (int q = 0; q < kPcStages - 1; ++q) issue(tile + q * (int64_t)gridDim.x, q);
@@ -395,10 +397,10 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
     const int s = i % kPcStages;
     issue(tile + (kPcStages - 1) * (int64_t)gridDim.x, (i + kPcStages - 1) % kPcStages);
     cp_async_wait<kPcStages - 1>();  // this thread's copies of tile i have landed
-    const int64_t r0 = tile * kPcTile;
+    const int64_t r0 = tile * TILE;
     if (!INIT) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < RPL; ++h) {
         const int e = t + h * nthr;
         float4 v = Rs[s * tile4 + e];
         const float4 qv = Qs[s * tile4 + e];
@@ -413,52 +415,49 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
     __syncthreads();
     {
       const float4* Rt = Rs + s * tile4;
-      const float* mrow = Ms + (s * (kPcTile / 2) + lane) * ldp;
-      const float4 rv0 = Rt[(2 * lane) * kq + w];
-      const float4 rv1 = Rt[(2 * lane + 1) * kq + w];
-      float2 z0lo = make_float2(0.f, 0.f), z0hi = make_float2(0.f, 0.f);
-      float2 z1lo = make_float2(0.f, 0.f), z1hi = make_float2(0.f, 0.f);
+      const float* mrow = Ms + (s * kPcLanes + lane) * ldp;
+      float2 zlo[RPL], zhi[RPL];
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        zlo[u] = make_float2(0.f, 0.f);
+        zhi[u] = make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int k = 0; k < B; k += 4) {
-        const float4 m0 = *(const float4*)(mrow + 2 * k);      // row 2l, columns k..k+3
-        const float4 m1 = *(const float4*)(mrow + 2 * k + 4);  // row 2l+1
-        const float mk0[4] = {m0.x, m0.y, m0.z, m0.w};
-        const float mk1[4] = {m1.x, m1.y, m1.z, m1.w};
+        float4 m[RPL];  // rows RPL l + u, columns k..k+3
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 x = Rt[(kb + k + u) * kq + w];
+        for (int u = 0; u < RPL; ++u) m[u] = *(const float4*)(mrow + RPL * k + 4 * u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 x = Rt[(kb + k + c) * kq + w];
           const float2 xlo = make_float2(x.x, x.y), xhi = make_float2(x.z, x.w);
-          const float2 a0 = make_float2(mk0[u], mk0[u]), a1 = make_float2(mk1[u], mk1[u]);
-          z0lo = __ffma2_rn(a0, xlo, z0lo);
-          z0hi = __ffma2_rn(a0, xhi, z0hi);
-          z1lo = __ffma2_rn(a1, xlo, z1lo);
-          z1hi = __ffma2_rn(a1, xhi, z1hi);
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const float mc = c == 0 ? m[u].x : c == 1 ? m[u].y : c == 2 ? m[u].z : m[u].w;
+            const float2 a2 = make_float2(mc, mc);
+            zlo[u] = __ffma2_rn(a2, xlo, zlo[u]);
+            zhi[u] = __ffma2_rn(a2, xhi, zhi[u]);
+          }
         }
       }
-      const float4 z0 = make_float4(z0lo.x, z0lo.y, z0hi.x, z0hi.y);
-      const float4 z1 = make_float4(z1lo.x, z1lo.y, z1hi.x, z1hi.y);
-      Zs[(2 * lane) * kq + w] = z0;
-      Zs[(2 * lane + 1) * kq + w] = z1;
-      rz[0].add(rv0.x, z0.x);
-      rz[1].add(rv0.y, z0.y);
-      rz[2].add(rv0.z, z0.z);
-      rz[3].add(rv0.w, z0.w);
-      rz[0].add(rv1.x, z1.x);
-      rz[1].add(rv1.y, z1.y);
-      rz[2].add(rv1.z, z1.z);
-      rz[3].add(rv1.w, z1.w);
-      rr[0].add(rv0.x, rv0.x);
-      rr[1].add(rv0.y, rv0.y);
-      rr[2].add(rv0.z, rv0.z);
-      rr[3].add(rv0.w, rv0.w);
-      rr[0].add(rv1.x, rv1.x);
-      rr[1].add(rv1.y, rv1.y);
-      rr[2].add(rv1.z, rv1.z);
-      rr[3].add(rv1.w, rv1.w);
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const float4 rv = Rt[(RPL * lane + u) * kq + w];
+        const float4 z = make_float4(zlo[u].x, zlo[u].y, zhi[u].x, zhi[u].y);
+        Zs[(RPL * lane + u) * kq + w] = z;
+        rz[0].add(rv.x, z.x);
+        rz[1].add(rv.y, z.y);
+        rz[2].add(rv.z, z.z);
+        rz[3].add(rv.w, z.w);
+        rr[0].add(rv.x, rv.x);
+        rr[1].add(rv.y, rv.y);
+        rr[2].add(rv.z, rv.z);
+        rr[3].add(rv.w, rv.w);
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < RPL; ++h) {
       const int e = t + h * nthr;
       if (r0 + e / kq < n) Z[r0 * kq + e] = Zs[e];
     }
@@ -494,6 +493,7 @@ UpdPcFn upd_pc_fn(int B) {
     case 16: return k_upd_r_pc<INIT, 16>;
     case 32: return k_upd_r_pc<INIT, 32>;
     case 64: return k_upd_r_pc<INIT, 64>;
+    case 128: return k_upd_r_pc<INIT, 128>;
     default: return nullptr;
   }
 }
@@ -1021,6 +1021,9 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   size_t pc_smem = 0;
   if (pc) {
     pc_smem = pc_smem_bytes(kq, c->pc_block);
+    int smem_max = 0;
+    GP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (pc_smem > (size_t)smem_max) return GP_ERR_UNSUPPORTED;  // B = 128 with kp > 36
     upd_pc_init = upd_pc_fn<true>(c->pc_block);
     upd_pc = upd_pc_fn<false>(c->pc_block);
     if (!upd_pc_init || !upd_pc) return GP_ERR_UNSUPPORTED;
@@ -1028,7 +1031,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     GP_CUDA(cudaFuncSetAttribute(upd_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
     // two blocks per SM, two tiles each in flight: enough bytes in flight for
     // HBM without many partial rows for the one-block reduction
-    g_pc = grid_for(n, kPcTile, c->num_sms * 2);
+    g_pc = grid_for(n, pc_tile(c->pc_block), c->num_sms * 2);
     GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
     GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * 2 * kp * sizeof(double)));
     upd_pc_init<<<g_pc, kPcLanes * kq, pc_smem, c->stream>>>(n, kq, nullptr, (float4*)c->R.p,

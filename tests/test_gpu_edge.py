@@ -122,7 +122,7 @@ def test_invalid_arguments_are_rejected(G):
             gp.lml(x, y, hb, opts(G))
         assert e.value.status == G.GP_ERR_INVALID_ARG
     for o in (opts(G, n_probes=0), opts(G, n_probes=65), opts(G, lanczos_steps=0), opts(G, max_iter=0),
-              opts(G, cg_rtol=0.0), opts(G, precision=7), opts(G, precond_block=5), opts(G, precond_block=128),
+              opts(G, cg_rtol=0.0), opts(G, precision=7), opts(G, precond_block=5), opts(G, precond_block=256),
               opts(G, batch_workers=-1), opts(G, batch_workers=17)):
         with pytest.raises(G.GPError) as e:
             gp.lml(x, y, p.h, o)
@@ -169,4 +169,19 @@ def test_batched_matches_single_calls(G):
         l1, g1, _ = gp.lml_grad(torch.as_tensor(q.x, device="cuda"), torch.as_tensor(q.y, device="cuda"), q.h, o)
         assert lml_b[k] == l1
         assert np.array_equal(grad_b[k], g1)
+    gp.close()
+
+
+def test_block_jacobi_128_needs_at_most_35_probes(G):
+    # its tile of R, Q and 128 x 128 blocks of M^-1 fills an SM's shared
+    # memory at kp = 36; more columns are refused, not silently changed
+    p = W.grad_3d(seed=3, n=2000)
+    gp = G.GP(p.dim, p.n1, p.n2)
+    x = torch.as_tensor(p.x, device="cuda")
+    y = torch.as_tensor(p.y, device="cuda")
+    lml, info = gp.lml(x, y, p.h, opts(G, n_probes=35, precond_block=128))
+    assert info["precond_block"] == 128
+    with pytest.raises(G.GPError) as e:
+        gp.lml(x, y, p.h, opts(G, n_probes=36, precond_block=128))
+    assert e.value.status == G.GP_ERR_UNSUPPORTED
     gp.close()

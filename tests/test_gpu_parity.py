@@ -68,7 +68,8 @@ def test_assembly_pattern_bit_exact_and_values(lib, case, prec):
     gp.close()
 
 
-@pytest.mark.parametrize("prec,B", [("fp64", 0), ("fp32", 0), ("fp32", 8), ("fp32", 16), ("fp32", 32), ("fp32", 64)])
+@pytest.mark.parametrize("prec,B", [("fp64", 0), ("fp32", 0), ("fp32", 8), ("fp32", 16), ("fp32", 32), ("fp32", 64),
+                                    ("fp32", 128)])
 def test_solve_matches_dense(lib, prec, B):
     p = W.small_2d(seed=1)
     gp = lib.GP(p.dim, p.n1, p.n2, p.beta)
@@ -88,7 +89,8 @@ def test_solve_matches_dense(lib, prec, B):
     gp.close()
 
 
-@pytest.mark.parametrize("prec,B", [("fp64", 0), ("fp32", 0), ("fp32", 8), ("fp32", 16), ("fp32", 32), ("fp32", 64)])
+@pytest.mark.parametrize("prec,B", [("fp64", 0), ("fp32", 0), ("fp32", 8), ("fp32", 16), ("fp32", 32), ("fp32", 64),
+                                    ("fp32", 128)])
 def test_lml_and_grad_same_probes(lib, prec, B):
     """Same probes: the GPU's SLQ log-determinant and Hutchinson gradient
     against the oracle's dense evaluation of the same estimator.  The
@@ -141,14 +143,14 @@ def test_preconditioning_cuts_iterations_not_the_estimate(lib):
     x = torch.as_tensor(p.x, device="cuda")
     y = torch.as_tensor(p.y, device="cuda")
     res = {}
-    for B in (0, 8, 16, 32, 64):
+    for B in (0, 8, 16, 32, 64, 128):
         o = lib.default_opts(precision="fp32", n_probes=16, lanczos_steps=30, cg_rtol=1e-6, seed=17,
                              precond_block=B)
         res[B] = gp.lml_grad(x, y, p.h, o)
     l0, g0, i0 = res[0]
     assert i0["lanczos_iters"] == 0 and i0["precond_block"] == 0
     scale = np.abs(g0) + 1e-3 * np.abs(g0).max()
-    for B in (8, 16, 32, 64):
+    for B in (8, 16, 32, 64, 128):
         l, g, info = res[B]
         print(B, "iters", info["iters"], "vs", i0["iters"], "lanczos", info["lanczos_iters"])
         assert info["precond_block"] == B
