@@ -85,9 +85,7 @@ typedef struct {
   int32_t flags;          /* GP_FLAG_* bits */
   int32_t precond_block;  /* FP32_MIXED only: 0 = Jacobi scaling alone; 8, 16, 32, 64 or 128 = also
                              block-Jacobi preconditioned CG, blocks of that many consecutive
-                             rows of the Morton-ordered active block (see gp_lml); 128 needs
-                             n_probes <= 35 (its tile of R, Q and M^-1 fills an SM's shared
-                             memory), else the evaluation returns GP_ERR_UNSUPPORTED */
+                             rows of the Morton-ordered active block (see gp_lml) */
   int32_t batch_workers;  /* gp_lml_grad_batched: instances run concurrently on this many
                              worker streams, each driven by its own host thread with its own
                              workspace (0: automatic, min(n_inst, 4); at most 16) */

@@ -324,10 +324,10 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
 constexpr int kPcLanes = 32;                       // threads per float4 slot
 constexpr int kPcMaxThreads = kPcLanes * gp::kMaxCols / 4;
 constexpr int pc_rows_per_lane(int B) { return B >= 128 ? 4 : 2; }
-constexpr int pc_tile(int B) { return kPcLanes * pc_rows_per_lane(B); }
-// pipeline depth: 3 tiles per block in flight for B <= 32, 2 for larger
-// blocks of M^-1 (16 KB or 64 KB per tile)
-constexpr int pc_stages(int B) { return B >= 64 ? 2 : 3; }
+// rows per tile (B <= 32) or per block (B >= 64: one tile is one block of M^-1)
+constexpr int pc_tile(int B) { return B >= 64 ? B : kPcLanes * pc_rows_per_lane(B); }
+constexpr int pc_stages(int) { return 3; }
+constexpr int kPcPanel = 32;  // columns of M^-1 per panel (B >= 64)
 
 __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -336,8 +336,14 @@ __device__ inline void cp_async16_zfill(void* smem, const void* gmem, bool valid
 }
 
 size_t pc_smem_bytes(int kq, int B) {
-  const size_t tile4 = (size_t)pc_tile(B) * kq;  // float4 per R (or Q, Z) tile
   const size_t S = pc_stages(B);
+  if (B >= 64) {
+    // per stage: R and Q panels (32 rows x kq float4) and a 32-column panel of
+    // M^-1 (B rows, interleaved per lane: rows padded to RPL 32 + 4 floats)
+    const size_t nthr = (size_t)kPcLanes * kq;
+    return S * (2 * 16 * nthr + 4 * (size_t)kPcLanes * (pc_rows_per_lane(B) * kPcPanel + 4));
+  }
+  const size_t tile4 = (size_t)pc_tile(B) * kq;  // float4 per R (or Q, Z) tile
   return 16 * tile4 * (2 * S + 1) + 4 * S * kPcLanes * (pc_rows_per_lane(B) * B + 4);
 }
 
@@ -484,6 +490,157 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
   }
 }
 
+// The same update for B = 64 or 128, with M^-1 streamed in panels of 32
+// columns: a block of rows r0 .. r0 + B - 1 (one block of M^-1) is taken in
+// B / 32 panels, panel q bringing rows r0 + 32q .. r0 + 32q + 31 of R and Q
+// and columns 32q .. 32q + 31 of the block's M^-1.  Thread t updates element
+// t of the panel (R -= alpha Q); then lane l adds the panel's share
+//   z[RPL l + u] += sum_{k < 32} M^-1[RPL l + u][32q + k] R[32q + k]
+// for its RPL = B / 32 rows and warp w's float4 slot, so Z stays in registers
+// across the block's panels and a stage holds only 26 KB (3 stages, two CTAs
+// per SM) where a whole 128 x 128 block of M^-1 would take 64 KB.  The panel
+// stream runs across the CTA's blocks without a break.
+template <bool INIT, int B>
+__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
+                                                              const float4* __restrict__ Q, float4* __restrict__ R,
+                                                              float4* __restrict__ Z, const float* __restrict__ Minv,
+                                                              double* __restrict__ part, const gp::CgState* st) {
+  if (!INIT && st->fin[st->iter & 1]) return;
+  constexpr int S = pc_stages(B);
+  constexpr int RPL = B / kPcLanes;  // rows per lane
+  constexpr int NPB = B / kPcPanel;  // panels per block
+  constexpr int ldm = RPL * kPcPanel + 4;
+  extern __shared__ float4 pc_smem[];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int nthr = kPcLanes * kq;  // float4 per R (or Q) panel
+  float4* Rs = pc_smem;            // S x nthr
+  float4* Qs = Rs + S * nthr;      // S x nthr
+  float* Ms = (float*)(Qs + S * nthr);  // S x 32 lane groups x ldm
+  const int64_t nblk = (n + B - 1) / B;
+  const int64_t mine = blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t npan = mine * NPB;
+  const int64_t nrows_pc = nblk * B;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!INIT) {
+    const int q = t % kq;
+    a = make_float4((float)st->alpha[4 * q], (float)st->alpha[4 * q + 1], (float)st->alpha[4 * q + 2],
+                    (float)st->alpha[4 * q + 3]);
+  }
+  auto issue = [&](int64_t pi, int s) {
+    if (pi < npan) {
+      const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+      const int q = (int)(pi % NPB);
+      const int64_t r0 = blk * B + kPcPanel * q;  // first row of the panel
+      const bool ok = r0 + t / kq < n;
+      const int64_t src = ok ? r0 * kq + t : 0;
+      cp_async16_zfill(Rs + s * nthr + t, R + src, ok);
+      if (!INIT) cp_async16_zfill(Qs + s * nthr + t, Q + src, ok);
+      for (int e = t; e < B * (kPcPanel / 4); e += nthr) {
+        const int r = e / (kPcPanel / 4), c4 = e - r * (kPcPanel / 4);
+        const int64_t grow = blk * B + r;
+        const bool okm = grow < nrows_pc;
+        const float* srcm = Minv + (okm ? grow * B + kPcPanel * q + 4 * c4 : 0);
+        cp_async16_zfill(Ms + (s * kPcLanes + r / RPL) * ldm + 4 * RPL * c4 + 4 * (r % RPL), srcm, okm);
+      }
+    }
+    cp_async_commit();
+  };
+  gpd::Dot2 rz[4], rr[4];
+  float2 zlo[RPL], zhi[RPL];
+  float4 rv[RPL];
+#pragma unroll
+  for (int q = 0; q < S - 1; ++q) issue(q, q);
+  for (int64_t pi = 0; pi < npan; ++pi) {
+    const int s = (int)(pi % S);
+    issue(pi + S - 1, (int)((pi + S - 1) % S));
+    cp_async_wait<S - 1>();  // this thread's copies of panel pi have landed
+    const int q = (int)(pi % NPB);
+    const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+    const int64_t r0 = blk * B + kPcPanel * q;
+    if (q == 0) {
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        zlo[u] = make_float2(0.f, 0.f);
+        zhi[u] = make_float2(0.f, 0.f);
+      }
+    }
+    if (!INIT) {
+      float4 v = Rs[s * nthr + t];
+      const float4 qv = Qs[s * nthr + t];
+      v.x = fmaf(-a.x, qv.x, v.x);
+      v.y = fmaf(-a.y, qv.y, v.y);
+      v.z = fmaf(-a.z, qv.z, v.z);
+      v.w = fmaf(-a.w, qv.w, v.w);
+      Rs[s * nthr + t] = v;
+      if (r0 + t / kq < n) R[r0 * kq + t] = v;
+    }
+    __syncthreads();
+    const float4* Rt = Rs + s * nthr;
+    // the lane's own rows RPL l .. RPL l + RPL - 1 of the block lie in panel (RPL l) / 32
+    if ((RPL * lane) / kPcPanel == q) {
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) rv[u] = Rt[((RPL * lane + u) % kPcPanel) * kq + w];
+    }
+    const float* mrow = Ms + (s * kPcLanes + lane) * ldm;
+#pragma unroll
+    for (int k = 0; k < kPcPanel; k += 4) {
+      float4 m[RPL];
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) m[u] = *(const float4*)(mrow + RPL * k + 4 * u);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float4 x = Rt[(k + c) * kq + w];
+        const float2 xlo = make_float2(x.x, x.y), xhi = make_float2(x.z, x.w);
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const float mc = c == 0 ? m[u].x : c == 1 ? m[u].y : c == 2 ? m[u].z : m[u].w;
+          const float2 a2 = make_float2(mc, mc);
+          zlo[u] = __ffma2_rn(a2, xlo, zlo[u]);
+          zhi[u] = __ffma2_rn(a2, xhi, zhi[u]);
+        }
+      }
+    }
+    if (q == NPB - 1) {
+      // the block's Z rows of this lane are complete: write them, add r.z, r.r
+#pragma unroll
+      for (int u = 0; u < RPL; ++u) {
+        const int64_t row = blk * B + RPL * lane + u;
+        const float4 z = make_float4(zlo[u].x, zlo[u].y, zhi[u].x, zhi[u].y);
+        if (row < n) Z[row * kq + w] = z;
+        rz[0].add(rv[u].x, z.x);
+        rz[1].add(rv[u].y, z.y);
+        rz[2].add(rv[u].z, z.z);
+        rz[3].add(rv[u].w, z.w);
+        rr[0].add(rv[u].x, rv[u].x);
+        rr[1].add(rv[u].y, rv[u].y);
+        rr[2].add(rv[u].z, rv[u].z);
+        rr[3].add(rv[u].w, rv[u].w);
+      }
+    }
+    __syncthreads();  // stage s is refilled by the next iteration's copies
+  }
+  cp_async_wait<0>();
+  // rows beyond n were filled with zeros, so they added nothing above
+  double v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = rz[j].value();
+    v[4 + j] = rr[j].value();
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
+  if (lane == 0) {
+    const int kp = 4 * kq;
+    double* prow = part + (int64_t)blockIdx.x * 2 * kp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      prow[4 * w + j] = v[j];
+      prow[kp + 4 * w + j] = v[4 + j];
+    }
+  }
+}
+
 typedef void (*UpdPcFn)(int64_t, int, const float4*, float4*, float4*, const float*, double*, const gp::CgState*);
 
 template <bool INIT>
@@ -492,8 +649,8 @@ UpdPcFn upd_pc_fn(int B) {
     case 8: return k_upd_r_pc<INIT, 8>;
     case 16: return k_upd_r_pc<INIT, 16>;
     case 32: return k_upd_r_pc<INIT, 32>;
-    case 64: return k_upd_r_pc<INIT, 64>;
-    case 128: return k_upd_r_pc<INIT, 128>;
+    case 64: return k_upd_r_pcp<INIT, 64>;
+    case 128: return k_upd_r_pcp<INIT, 128>;
     default: return nullptr;
   }
 }
@@ -1023,7 +1180,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     pc_smem = pc_smem_bytes(kq, c->pc_block);
     int smem_max = 0;
     GP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    if (pc_smem > (size_t)smem_max) return GP_ERR_UNSUPPORTED;  // B = 128 with kp > 36
+    if (pc_smem > (size_t)smem_max) return GP_ERR_UNSUPPORTED;
     upd_pc_init = upd_pc_fn<true>(c->pc_block);
     upd_pc = upd_pc_fn<false>(c->pc_block);
     if (!upd_pc_init || !upd_pc) return GP_ERR_UNSUPPORTED;

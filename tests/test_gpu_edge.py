@@ -172,16 +172,17 @@ def test_batched_matches_single_calls(G):
     gp.close()
 
 
-def test_block_jacobi_128_needs_at_most_35_probes(G):
-    # its tile of R, Q and 128 x 128 blocks of M^-1 fills an SM's shared
-    # memory at kp = 36; more columns are refused, not silently changed
+def test_block_jacobi_128_with_the_most_probes(G):
+    # 64 probes (kp = 68) with 128-row blocks: the largest panels of R, Q and
+    # M^-1 the streamed update handles
     p = W.grad_3d(seed=3, n=2000)
     gp = G.GP(p.dim, p.n1, p.n2)
     x = torch.as_tensor(p.x, device="cuda")
     y = torch.as_tensor(p.y, device="cuda")
-    lml, info = gp.lml(x, y, p.h, opts(G, n_probes=35, precond_block=128))
-    assert info["precond_block"] == 128
-    with pytest.raises(G.GPError) as e:
-        gp.lml(x, y, p.h, opts(G, n_probes=36, precond_block=128))
-    assert e.value.status == G.GP_ERR_UNSUPPORTED
+    l128, i128 = gp.lml(x, y, p.h, opts(G, n_probes=64, precond_block=128))
+    l32, i32 = gp.lml(x, y, p.h, opts(G, n_probes=64, precond_block=32))
+    assert i128["precond_block"] == 128 and i128["kp"] == 68
+    assert i128["iters"] <= i32["iters"]
+    assert i128["quad_form"] == pytest.approx(i32["quad_form"], rel=1e-5)
+    assert i128["logdet"] == pytest.approx(i32["logdet"], rel=1e-5)
     gp.close()
