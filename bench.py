@@ -55,6 +55,8 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1200)
+    ap.add_argument("--precond-block", type=int, default=None,
+                    help="block-Jacobi block size of the preconditioned CG (default: the library's)")
     ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide"],
                     help="SpMM form: the library's autotuner (auto) or a forced form; profiling runs force "
                          "the form the plain run chose, since the tuner's timings are meaningless under ncu")
@@ -242,8 +244,9 @@ def main():
     gp = GP(p.dim, p.n1, p.n2, p.beta, device=local)
     from paper_2205_09070_gb300.gpsparse import SPMM_FLAGS
     spmm_flag = SPMM_FLAGS.get(a.spmm, 0)
+    pc_kw = {} if a.precond_block is None else {"precond_block": a.precond_block}
     opts = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
-                        max_iter=20000, flags=GP_FLAG_TIME_KERNELS | spmm_flag)
+                        max_iter=20000, flags=GP_FLAG_TIME_KERNELS | spmm_flag, **pc_kw)
 
     for _ in range(a.warmup):
         gp.lml_grad(x, y, p.h, opts)
@@ -303,7 +306,7 @@ def main():
     yh = torch.as_tensor(p.y).pin_memory()
     gh = torch.zeros(gp.n_params, dtype=torch.float64).pin_memory()
     opts_e2e = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
-                            max_iter=20000, flags=spmm_flag)
+                            max_iter=20000, flags=spmm_flag, **pc_kw)
     e2e = None
     if a.e2e_steps > 0:
         gp.lml_grad(xh, yh, p.h, opts_e2e, grad=gh)
