@@ -2,9 +2,9 @@
 //
 // The active rows are in Morton / sub-cell order, so B consecutive rows are
 // close in space and strongly coupled.  M = blockdiag(Khat_bb) over blocks of
-// B consecutive rows (B = 8, 16, 32, 64 or 128); each block is factored in FP64
-// (one CTA of B threads per block, Cholesky M_bb = L L^T, then
-// M_bb^-1 = L^-T L^-1) and M^-1 is stored in FP32,
+// B consecutive rows (B = 8, 16, 32, 64 or 128); each block is factored
+// (FP64 for B <= 32, FP32 for 64 and 128; one CTA of B threads per block,
+// Cholesky M_bb = L L^T, then M_bb^-1 = L^-T L^-1) and M^-1 is stored in FP32,
 // B x B row-major per block, zero outside the block's rows for the last,
 // shorter block.  Preconditioning changes only how fast CG converges: the
 // solves Khat u = b it feeds are the same.
@@ -18,13 +18,10 @@ namespace {
 
 // One CTA of B threads per diagonal block (grid-stride); thread i owns row i
 // of the block.  A (the block of Khat, overwritten by L; FP64) and Y = L^-1
-// live in dynamic shared memory, B x (B+1) entries each.  Y is FP64 up to
-// B = 64 and FP32 for B = 128 (two FP64 128 x 128 blocks exceed an SM's
-// shared memory); its sums still run in FP64, and M^-1 is stored in FP32
-// either way: a preconditioner only has to be symmetric positive definite
-// and close to the block inverse.
+// live in dynamic shared memory, B x (B+1) entries each (B <= 32; larger
+// blocks take the FP32 set-up below).
 template <int B>
-using PcY = typename std::conditional<(B >= 128), float, double>::type;
+using PcY = double;
 
 template <int B>
 __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const int64_t* __restrict__ rp,
@@ -111,6 +108,103 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
   }
 }
 
+// Blocks of 64 or 128 rows, in FP32 (GB300's FP64 pipe makes the FP64
+// factorisation of 128-row blocks cost ~36 ms per evaluation at 1M points).
+// One CTA of B threads per block, thread t owning row t:
+//   right-looking Cholesky A = L L^T (pivot by thread j, column j scaled,
+//     trailing rows updated in parallel, one row per thread);
+//   Y = L^-1, thread c forward-substituting column c;
+//   M^-1 = Y^T Y, row t per thread, FP32.
+// Y^T Y is symmetric positive definite for any nonsingular Y, so rounding
+// cannot make the preconditioner indefinite; a pivot that rounding drives to
+// or below 1e-6 (the block's unit diagonal times 1e-6) is floored there,
+// which factors a slightly perturbed block and keeps the preconditioner
+// valid.  An indefinite K is still caught by CG (p^T K p <= 0).
+template <int B>
+__global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                  float* __restrict__ Mout, gp::AsmScalars* s) {
+  extern __shared__ float pc_sf[];
+  float (*A)[B + 1] = (float (*)[B + 1])pc_sf;
+  float (*Y)[B + 1] = (float (*)[B + 1])(pc_sf + B * (B + 1));
+  const int t = threadIdx.x;
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int64_t r0 = b * B;
+    const int nb = (int)min((int64_t)B, n - r0);
+    for (int j = 0; j < B; ++j) A[t][j] = 0.f;
+    if (t < nb) {
+      const int64_t row = r0 + t;
+      for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+        const int64_t j = col[e];
+        if (j >= r0 && j < r0 + nb) A[t][j - r0] = val[e];
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      if (t == j) A[j][j] = sqrtf(fmaxf(A[j][j], 1e-6f));
+      __syncthreads();
+      if (t > j && t < nb) A[t][j] /= A[j][j];
+      __syncthreads();
+      if (t > j && t < nb) {
+        const float lt = A[t][j];
+        for (int k = j + 1; k <= t; ++k) A[t][k] = fmaf(-lt, A[k][j], A[t][k]);
+      }
+      __syncthreads();
+    }
+    // Y = L^-1 (lower), column t; four partial sums shorten the add chains
+    for (int r = 0; r < B; ++r) Y[r][t] = 0.f;
+    if (t < nb) {
+      for (int r = t; r < nb; ++r) {
+        float v0 = r == t ? 1.f : 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+        int k = t;
+        for (; k + 3 < r; k += 4) {
+          v0 = fmaf(-A[r][k], Y[k][t], v0);
+          v1 = fmaf(-A[r][k + 1], Y[k + 1][t], v1);
+          v2 = fmaf(-A[r][k + 2], Y[k + 2][t], v2);
+          v3 = fmaf(-A[r][k + 3], Y[k + 3][t], v3);
+        }
+        for (; k < r; ++k) v0 = fmaf(-A[r][k], Y[k][t], v0);
+        Y[r][t] = ((v0 + v1) + (v2 + v3)) / A[r][r];
+      }
+    }
+    __syncthreads();
+    // M^-1 = Y^T Y, row t, zero outside nb x nb
+    float* Mb = Mout + b * (int64_t)B * B;
+    for (int jj = 0; jj < B; ++jj) {
+      float m = 0.f;
+      if (t < nb && jj < nb) {
+        float m1 = 0.f;
+        int k = t > jj ? t : jj;
+        for (; k + 1 < nb; k += 2) {
+          m = fmaf(Y[k][t], Y[k][jj], m);
+          m1 = fmaf(Y[k + 1][t], Y[k + 1][jj], m1);
+        }
+        if (k < nb) m = fmaf(Y[k][t], Y[k][jj], m);
+        m += m1;
+      }
+      Mb[t * B + jj] = m;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && t == 0) s->pc_status = GP_OK;
+}
+
+template <int B>
+int launch_setup32(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
+  const size_t smem = 2 * sizeof(float) * B * (B + 1);
+  GP_CUDA(cudaFuncSetAttribute(k_pc_setup32<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc_setup32<B>, B, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t cap = (int64_t)c->num_sms * per_sm;
+  const int64_t g = nblk < cap ? nblk : cap;
+  k_pc_setup32<B><<<(unsigned)g, B, smem, c->stream>>>(c->n_act, nblk, (const int64_t*)c->row_ptr.p,
+                                                       (const int32_t*)c->col.p, (const float*)c->val.p,
+                                                       (float*)c->pc_Minv.p, s);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
 template <int B>
 int launch_setup(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
   const size_t smem = (sizeof(double) + sizeof(PcY<B>)) * B * (B + 1);
@@ -145,8 +239,8 @@ int precond_setup(gp_ctx* c, int B) {
     case 8: GP_CHECK(launch_setup<8>(c, nblk, s)); break;
     case 16: GP_CHECK(launch_setup<16>(c, nblk, s)); break;
     case 32: GP_CHECK(launch_setup<32>(c, nblk, s)); break;
-    case 64: GP_CHECK(launch_setup<64>(c, nblk, s)); break;
-    default: GP_CHECK(launch_setup<128>(c, nblk, s)); break;
+    case 64: GP_CHECK(launch_setup32<64>(c, nblk, s)); break;
+    default: GP_CHECK(launch_setup32<128>(c, nblk, s)); break;
   }
   c->launches += 1;
   c->pc_block = B;
