@@ -141,7 +141,7 @@ typedef struct {
 int64_t gp_n_params(const gp_kernel_desc* desc);
 
 /* Default options: FP32_MIXED, 32 probes, 50 Lanczos steps, 10000 iterations,
- * rtol 1e-6, seed 0x5eed, check every 16 iterations, precond_block 32. */
+ * rtol 1e-6, seed 0x5eed, check every 16 iterations, precond_block 128. */
 void gp_default_opts(gp_opts* opts);
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream`

@@ -310,7 +310,7 @@ void gp_default_opts(gp_opts* o) {
   o->seed = 0x5eedull;
   o->check_every = 16;
   o->flags = 0;
-  o->precond_block = 32;
+  o->precond_block = 128;
   o->batch_workers = 0;
 }
 

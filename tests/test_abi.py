@@ -38,6 +38,7 @@ def test_host_only_calls():
     o = G.default_opts()
     assert o.precision == G.GP_FP32_MIXED and o.n_probes == 32 and o.lanczos_steps == 50
     assert o.cg_rtol == pytest.approx(1e-6)
+    assert o.precond_block == 128
     for s in range(9):
         assert G.status_string(s)
     assert G.status_string(G.GP_ERR_NOT_SPD).startswith("CG breakdown")
