@@ -345,7 +345,8 @@ def main():
         cpu = cpu_oracle_sample(p, a.cpu_sample)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        metric = METRIC if p.n == 1_000_000 else METRIC.replace("N=1M", f"N={p.n:,}")
+        line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic (seeded; stands in for the NOAA GHCN-Daily station-day data)",
