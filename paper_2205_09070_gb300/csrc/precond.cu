@@ -113,8 +113,12 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
 // One CTA of B threads per block, thread t owning row t:
 //   right-looking Cholesky A = L L^T (pivot by thread j, column j scaled,
 //     trailing rows updated in parallel, one row per thread);
-//   Y = L^-1, thread c forward-substituting column c;
-//   M^-1 = Y^T Y, row t per thread, FP32.
+//   Y = L^-1, thread c forward-substituting column c, stored transposed in
+//     the free upper triangle of A (Y[r][c] at A[c][r], r > c; its diagonal
+//     1 / L_cc in a separate vector), so one B x (B+1) array serves both and
+//     three CTAs share an SM;
+//   M^-1 = Y^T Y, row t per thread (dot products of rows of the upper
+//     triangle), FP32.
 // Y^T Y is symmetric positive definite for any nonsingular Y, so rounding
 // cannot make the preconditioner indefinite; a pivot that rounding drives to
 // or below 1e-6 (the block's unit diagonal times 1e-6) is floored there,
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
                                                   float* __restrict__ Mout, gp::AsmScalars* s) {
   extern __shared__ float pc_sf[];
   float (*A)[B + 1] = (float (*)[B + 1])pc_sf;
-  float (*Y)[B + 1] = (float (*)[B + 1])(pc_sf + B * (B + 1));
+  float* yd = pc_sf + B * (B + 1);  // Y[c][c] = 1 / L_cc
   const int t = threadIdx.x;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     const int64_t r0 = b * B;
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
       const int64_t row = r0 + t;
       for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
         const int64_t j = col[e];
-        if (j >= r0 && j < r0 + nb) A[t][j - r0] = val[e];
+        if (j >= r0 && j <= row) A[t][j - r0] = val[e];  // lower triangle only
       }
     }
     __syncthreads();
@@ -151,35 +155,41 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
       }
       __syncthreads();
     }
-    // Y = L^-1 (lower), column t; four partial sums shorten the add chains
-    for (int r = 0; r < B; ++r) Y[r][t] = 0.f;
+    // Y = L^-1, column t, into row t of the upper triangle; four partial
+    // sums shorten the add chains
     if (t < nb) {
-      for (int r = t; r < nb; ++r) {
-        float v0 = r == t ? 1.f : 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-        int k = t;
+      yd[t] = 1.f / A[t][t];
+      for (int r = t + 1; r < nb; ++r) {
+        // Y[r][t] = -(sum_{k=t}^{r-1} L[r][k] Y[k][t]) / L[r][r], Y[t][t] = yd[t]
+        float v0 = -A[r][t] * yd[t], v1 = 0.f, v2 = 0.f, v3 = 0.f;
+        int k = t + 1;
         for (; k + 3 < r; k += 4) {
-          v0 = fmaf(-A[r][k], Y[k][t], v0);
-          v1 = fmaf(-A[r][k + 1], Y[k + 1][t], v1);
-          v2 = fmaf(-A[r][k + 2], Y[k + 2][t], v2);
-          v3 = fmaf(-A[r][k + 3], Y[k + 3][t], v3);
+          v0 = fmaf(-A[r][k], A[t][k], v0);
+          v1 = fmaf(-A[r][k + 1], A[t][k + 1], v1);
+          v2 = fmaf(-A[r][k + 2], A[t][k + 2], v2);
+          v3 = fmaf(-A[r][k + 3], A[t][k + 3], v3);
         }
-        for (; k < r; ++k) v0 = fmaf(-A[r][k], Y[k][t], v0);
-        Y[r][t] = ((v0 + v1) + (v2 + v3)) / A[r][r];
+        for (; k < r; ++k) v0 = fmaf(-A[r][k], A[t][k], v0);
+        A[t][r] = ((v0 + v1) + (v2 + v3)) / A[r][r];
       }
     }
     __syncthreads();
-    // M^-1 = Y^T Y, row t, zero outside nb x nb
+    // M^-1 = Y^T Y: M[t][jj] = sum_{k >= max(t, jj)} Y[k][t] Y[k][jj], with
+    // Y[k][c] = A[c][k] for k > c and yd[c] for k = c; zero outside nb x nb
     float* Mb = Mout + b * (int64_t)B * B;
     for (int jj = 0; jj < B; ++jj) {
       float m = 0.f;
       if (t < nb && jj < nb) {
+        const int lo = t > jj ? t : jj;
+        // the k = lo term: one of the two factors sits on a diagonal
+        m = (t == jj) ? yd[t] * yd[t] : (t > jj ? yd[t] * A[jj][t] : A[t][jj] * yd[jj]);
         float m1 = 0.f;
-        int k = t > jj ? t : jj;
+        int k = lo + 1;
         for (; k + 1 < nb; k += 2) {
-          m = fmaf(Y[k][t], Y[k][jj], m);
-          m1 = fmaf(Y[k + 1][t], Y[k + 1][jj], m1);
+          m = fmaf(A[t][k], A[jj][k], m);
+          m1 = fmaf(A[t][k + 1], A[jj][k + 1], m1);
         }
-        if (k < nb) m = fmaf(Y[k][t], Y[k][jj], m);
+        if (k < nb) m = fmaf(A[t][k], A[jj][k], m);
         m += m1;
       }
       Mb[t * B + jj] = m;
@@ -191,7 +201,7 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
 
 template <int B>
 int launch_setup32(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
-  const size_t smem = 2 * sizeof(float) * B * (B + 1);
+  const size_t smem = sizeof(float) * ((size_t)B * (B + 1) + B);
   GP_CUDA(cudaFuncSetAttribute(k_pc_setup32<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc_setup32<B>, B, smem));

@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
 // for its RPL = B / 32 rows and warp w's float4 slot, so Z stays in registers
 // across the block's panels and a stage holds only 26 KB (3 stages, two CTAs
 // per SM) where a whole 128 x 128 block of M^-1 would take 64 KB.  The panel
-// stream runs across the CTA's blocks without a break.
+// stream runs across the CTA's blocks without a break, one barrier per panel.
 template <bool INIT, int B>
 __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
                                                               const float4* __restrict__ Q, float4* __restrict__ R,
@@ -552,8 +552,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
   for (int q = 0; q < S - 1; ++q) issue(q, q);
   for (int64_t pi = 0; pi < npan; ++pi) {
     const int s = (int)(pi % S);
-    issue(pi + S - 1, (int)((pi + S - 1) % S));
-    cp_async_wait<S - 1>();  // this thread's copies of panel pi have landed
+    cp_async_wait<S - 2>();  // this thread's copies of panel pi have landed
     const int q = (int)(pi % NPB);
     const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
     const int64_t r0 = blk * B + kPcPanel * q;
@@ -574,7 +573,11 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
       Rs[s * nthr + t] = v;
       if (r0 + t / kq < n) R[r0 * kq + t] = v;
     }
+    // one barrier per panel: panel pi's copies and updates are visible to all
+    // threads, and every thread has finished panel pi-1, whose stage the next
+    // copies refill (S - 1 panels stay in flight while pi is computed)
     __syncthreads();
+    issue(pi + S - 1, (int)((pi + S - 1) % S));
     const float4* Rt = Rs + s * nthr;
     // the lane's own rows RPL l .. RPL l + RPL - 1 of the block lie in panel (RPL l) / 32
     if ((RPL * lane) / kPcPanel == q) {
@@ -617,7 +620,6 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
         rr[3].add(rv[u].w, rv[u].w);
       }
     }
-    __syncthreads();  // stage s is refilled by the next iteration's copies
   }
   cp_async_wait<0>();
   // rows beyond n were filled with zeros, so they added nothing above
