@@ -29,22 +29,26 @@ constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sum partials part[b * stride + t] over blocks b < nblk for t < width with all
-// threads of the block, in a fixed order; result in out[t] (shared).  Four
-// independent accumulators keep several L2 loads in flight per thread.
+// threads of the block, in a fixed order; result in out[t] (shared).  Each
+// thread keeps 16 predicated L2 loads in flight per round (no dependent tail).
 __device__ void block_sum_partials(const double* part, int nblk, int width, int stride, double* out,
                                    double* scratch /* >= blockDim.x doubles */) {
-  const int groups = blockDim.x / width;  // width <= kMaxCols < blockDim.x
+  const int groups = blockDim.x / width;  // width <= 2 kMaxCols < blockDim.x
   const int t = threadIdx.x % width, grp = threadIdx.x / width;
-  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double a[4] = {0, 0, 0, 0};
   if (grp < groups) {
-    int b = grp;
-    for (; b + 7 * groups < nblk; b += 8 * groups) {
+    for (int b0 = grp; b0 < nblk; b0 += 16 * groups) {
+      double v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] += __ldcg(part + (int64_t)(b + u * groups) * stride + t);
+      for (int u = 0; u < 16; ++u) {
+        const int b = b0 + u * groups;
+        v[u] = b < nblk ? __ldcg(part + (int64_t)b * stride + t) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) a[u & 3] += v[u];
     }
-    for (; b < nblk; b += groups) a[0] += __ldcg(part + (int64_t)b * stride + t);
   }
-  scratch[threadIdx.x] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  scratch[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
   __syncthreads();
   if (threadIdx.x < width) {
     double s = 0.0;
