@@ -18,7 +18,9 @@ Paper sections used (arXiv 2205.09070):
   * Sec. 2.2, Eq. (eq:kstat): the compactly supported stationary kernel k~.
   * Sec. 2.2, Eq. (eq:sparsity_estimate) and the two equations after it: the
     sparsity upper bound used as a statistical check.
-  * Sec. 2.5: CG for K x = y and a randomized log-determinant.
+  * Sec. 2.5: CG for K x = y and a randomized log-determinant (the cited
+    estimator of Boutsidis et al., truncated Taylor series of ln(I - C) with
+    Hutchinson probes, beside stochastic Lanczos quadrature).
 
 Readings where the paper is silent, garbled or inconsistent (each is listed in
 DESIGN.md as well):
@@ -404,6 +406,50 @@ def lanczos_quadrature(Khat, z, m):
     T = np.diag(a) + np.diag(b[: k - 1], 1) + np.diag(b[: k - 1], -1)
     theta, Q = np.linalg.eigh(T)
     return nz * nz * float(np.sum(Q[0, :] ** 2 * np.log(theta)))
+
+
+def gershgorin_bound(A):
+    """max_i sum_j |A_ij|: an upper bound on every eigenvalue of A (Gershgorin)."""
+    return float(np.max(np.sum(np.abs(A), axis=1))) if A.shape[0] else 0.0
+
+
+def taylor_logdet_terms(Khat, Z, m, a):
+    """Per-probe terms of the randomized log-determinant of Boutsidis et al.
+    (the estimator Sec. 2.5 uses): with C = I - Khat / a (a >= lambda_max),
+      ln|Khat| = N ln a + ln|I - C| = N ln a - sum_{k>=1} tr(C^k) / k,
+    truncated after m terms, each trace replaced by z^T C^k z for one probe:
+      Gamma_l = N ln a - sum_{k=1}^{m} z_l^T C^k z_l / k.
+    For Rademacher probes E[z z^T] = I, so the mean of Gamma_l is the
+    truncated series.  Z may hold any probe columns."""
+    n = Khat.shape[0]
+    V = np.array(Z, dtype=np.float64, copy=True)
+    acc = np.zeros(V.shape[1])
+    for k in range(1, m + 1):
+        V = V - (Khat @ V) / a                     # V = C^k Z
+        acc += np.sum(Z * V, axis=0) / k           # z^T C^k z / k, per column
+    return n * math.log(a) - acc
+
+
+def logdet_taylor_same_probes(x, h, dim, n1, n2, n_probes, m, seed, beta=1.0):
+    """ln|K| by the truncated-Taylor randomized estimator on the same split and
+    probes as the GPU path: ln|K| = sum_act ln D + mean_l Gamma_l(Khat)
+    + N_inact ln sigma_n^2, Khat = D^-1/2 K_act D^-1/2, a = gershgorin_bound(Khat).
+    Returns (logdet, per-probe Gamma, a)."""
+    p = unpack_h(h, dim, n1, n2)
+    x = np.asarray(x, dtype=np.float64)
+    K = dense_K(x, h, dim, n1, n2, beta)
+    _, mask = bump_table(x, h, dim, n1, n2, beta)
+    act, inact = active_split(K, mask)
+    Ka = K[np.ix_(act, act)]
+    D = np.diag(Ka).copy()
+    Dm = 1.0 / np.sqrt(D)
+    Khat = Ka * Dm[:, None] * Dm[None, :]
+    if act.size == 0:
+        return inact.size * math.log(p["sigma2"]), np.zeros(n_probes), 0.0
+    a = gershgorin_bound(Khat)
+    gam = taylor_logdet_terms(Khat, rademacher(seed, n_probes, act), m, a)
+    logdet = float(np.sum(np.log(D))) + float(np.mean(gam)) + inact.size * math.log(p["sigma2"])
+    return logdet, gam, a
 
 
 def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,

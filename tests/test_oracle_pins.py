@@ -385,3 +385,48 @@ def test_predict_mean_at_training_points_and_outside_supports():
     outside = x[mask == 0][:3]
     if len(outside):
         assert np.array_equal(O.predict_mean(x, y, h, outside, dim, n1, n2), np.zeros(len(outside)))
+
+
+# --------------------------------------------------------------------- Taylor log-determinant
+
+def test_taylor_logdet_exact_traces_match_the_eigenvalue_series():
+    # probes = the N basis vectors give exact traces: the estimator is then
+    # N ln a - sum_i sum_{k<=m} c_i^k / k with c_i = 1 - lambda_i / a, written
+    # here from the eigenvalues instead of matrix powers
+    x, y, h, dim, n1, n2 = small_problem(seed=51, n=120)
+    K = O.dense_K(x, h, dim, n1, n2)
+    D = np.diag(K)
+    Khat = K / np.sqrt(np.outer(D, D))
+    a = O.gershgorin_bound(Khat)
+    lam = np.linalg.eigvalsh(Khat)
+    assert lam[-1] <= a * (1 + 1e-12)
+    c = 1.0 - lam / a
+    for m in (1, 5, 40):
+        series = len(lam) * math.log(a) - sum(np.sum(c ** k) / k for k in range(1, m + 1))
+        got = O.taylor_logdet_terms(Khat, np.eye(len(lam)), m, a)
+        assert np.sum(got) - (len(lam) - 1) * len(lam) * math.log(a) == pytest.approx(series, rel=1e-10)
+    # the full series is ln|Khat|: a well-conditioned matrix converges fast
+    Kw = Khat + 2.0 * np.eye(len(lam))
+    aw = O.gershgorin_bound(Kw)
+    gw = O.taylor_logdet_terms(Kw, np.eye(len(lam)), 400, aw)
+    exact = np.linalg.slogdet(Kw)[1]
+    assert np.sum(gw) - (len(lam) - 1) * len(lam) * math.log(aw) == pytest.approx(exact, rel=1e-9)
+
+
+def test_taylor_logdet_same_probes_split_and_statistics():
+    # the same split as SLQ: all-inactive data give the exact noise model
+    x, y, h, dim, n1, n2 = small_problem(seed=52, n=150)
+    p = O.unpack_h(h, dim, n1, n2)
+    far = h.copy()
+    per = dim + 2
+    for b in range(n1 * n2):
+        far[b * per: b * per + dim] = 40.0
+    ld, gam, a = O.logdet_taylor_same_probes(x, far, dim, n1, n2, 8, 10, 3)
+    assert ld == pytest.approx(len(x) * math.log(p["sigma2"]), rel=1e-14)
+    # with many terms and probes the estimate is within its standard error of
+    # ln|K| (the truncation bias shrinks as c^m for the well-separated spectrum
+    # this small problem has; checked against the eigenvalue series above)
+    ld, gam, a = O.logdet_taylor_same_probes(x, h, dim, n1, n2, 64, 300, 4)
+    exact = np.linalg.slogdet(O.dense_K(x, h, dim, n1, n2))[1]
+    se = np.std(gam, ddof=1) / math.sqrt(len(gam))
+    assert abs(ld - exact) <= 5 * se + 1e-3 * abs(exact)
