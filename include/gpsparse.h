@@ -77,7 +77,8 @@ typedef struct {
 typedef struct {
   int32_t precision;      /* GP_FP64 or GP_FP32_MIXED */
   int32_t n_probes;       /* Rademacher probes for SLQ / Hutchinson, 1..64 */
-  int32_t lanczos_steps;  /* Lanczos (CG) steps used by SLQ, 1..64 */
+  int32_t lanczos_steps;  /* Lanczos (CG) steps used by SLQ, 1..64; with GP_FLAG_LOGDET_TAYLOR
+                             the number of series terms, 1..4096 */
   int32_t max_iter;       /* CG iteration cap */
   double cg_rtol;         /* stop a column when |r| <= cg_rtol |r0| (Jacobi-scaled system) */
   uint64_t seed;          /* probe stream: SplitMix64 counter l*2^40 + original point index */
@@ -104,6 +105,18 @@ typedef struct {
 #define GP_FLAG_SPMM_CPASYNC  2  /* stage filled by per-lane cp.async copies */
 #define GP_FLAG_SPMM_TMA      4  /* stage filled by TMA: tile::gather4 of P rows, bulk copy of values */
 #define GP_FLAG_SPMM_TMA_WIDE 8  /* TMA stage, 2 or 3 float4 columns per lane (else as GP_FLAG_SPMM_TMA) */
+
+/* gp_opts.flags: estimate ln|K| with the randomized estimator the paper cites
+ * (Sec. 2.5, Boutsidis et al.) instead of stochastic Lanczos quadrature: on
+ * the same Jacobi-scaled active block and probes,
+ *   ln|Khat| ~ mean_l [N_act ln a - sum_{k=1}^{m} z_l^T C^k z_l / k],
+ *   C = I - Khat / a,  a = max_i sum_j |Khat_ij| (Gershgorin, >= lambda_max),
+ * with m = lanczos_steps terms (one SpMM over the probe block per term).  The
+ * series converges like (1 - lambda_min / a)^m, so for ill-conditioned K it
+ * is biased low at any practical m; gp_info.logdet_stderr reports the
+ * spread over probes only.  FP32_MIXED only (else GP_ERR_UNSUPPORTED); the
+ * gradient's trace term is Hutchinson's on the same probes either way. */
+#define GP_FLAG_LOGDET_TAYLOR 16
 
 /* gp_info.spmm_variant */
 #define GP_SPMM_CPASYNC  0

@@ -132,7 +132,9 @@ int check_opts(const gp_opts* o, bool need_probes) {
   if (o->batch_workers < 0 || o->batch_workers > 16) return GP_ERR_INVALID_ARG;
   if (need_probes) {
     if (o->n_probes < 1 || o->n_probes > gp::kMaxProbes) return GP_ERR_INVALID_ARG;
-    if (o->lanczos_steps < 1 || o->lanczos_steps > gp::kMaxLanczos) return GP_ERR_INVALID_ARG;
+    // SLQ keeps lanczos_steps coefficients per column; the Taylor series keeps none
+    const int max_steps = (o->flags & GP_FLAG_LOGDET_TAYLOR) ? 4096 : gp::kMaxLanczos;
+    if (o->lanczos_steps < 1 || o->lanczos_steps > max_steps) return GP_ERR_INVALID_ARG;
   }
   return GP_OK;
 }
@@ -206,9 +208,19 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
   int iters = 0, lanczos_iters = 0;
   double max_rel = 0.0;
   int cg_status;
+  // the log-determinant estimator: SLQ, or the truncated Taylor series the
+  // paper cites (FP32 path; lanczos_steps terms on the same probes)
+  const bool taylor = (o->flags & GP_FLAG_LOGDET_TAYLOR) != 0;
+  if (taylor && o->precision != GP_FP32_MIXED) return GP_ERR_UNSUPPORTED;
   if (o->precision == GP_FP64) {
     cg_status = gp::cg_run_fp64(c, k, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
                                 &iters, &max_rel);
+  } else if (taylor) {
+    // the solves alone (preconditioned when asked), then the series on V = C^k Z
+    cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters,
+                           &max_rel, c->pc_block > 0);
+    if (cg_status == GP_OK || cg_status == GP_ERR_NOT_CONVERGED)
+      GP_CHECK(gp::taylor_logdet(c, nv, kp, o->lanczos_steps));
   } else if (c->pc_block == 0) {
     // one plain CG run: its first lanczos_steps coefficients feed SLQ
     cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
@@ -230,7 +242,7 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
   }
   if (cg_status != GP_OK && cg_status != GP_ERR_NOT_CONVERGED) return cg_status;
   GP_CHECK(gp::quad_form(c, yd, kp));
-  if (o->precision == GP_FP64 || c->pc_block == 0) GP_CHECK(gp::slq(c, nv, kp));
+  if (!taylor && (o->precision == GP_FP64 || c->pc_block == 0)) GP_CHECK(gp::slq(c, nv, kp));
   tm.mark(2);
   if (grad) GP_CHECK(gp::adjoint(c, nv, kp));
   tm.mark(3);
@@ -362,7 +374,7 @@ int gp_destroy(gp_ctx* c) {
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
                         &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
                         &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z,
-                        &c->xstar_in, &c->pred_tmp, &c->slq_steps};
+                        &c->xstar_in, &c->pred_tmp, &c->slq_steps, &c->taylor};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);

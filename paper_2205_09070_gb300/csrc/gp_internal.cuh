@@ -131,6 +131,7 @@ struct gp_ctx {
   // device buffers (grow-only)
   gp::DevBuf x_in, y_in, out_tmp;
   gp::DevBuf xstar_in, pred_tmp;  // gp_predict: staged test points, posterior means
+  gp::DevBuf taylor;              // scalars of the truncated-Taylor log-determinant
   gp::DevBuf bump;
   gp::DevBuf mask0, F0, pos;
   gp::DevBuf keys, vals, keys2, vals2, hist, hist_scan, scan_part;
@@ -228,6 +229,10 @@ int alpha_out(gp_ctx* c, const double* y_dev, double* alpha_dev, int kp);
 
 // adjoint.cu
 int adjoint(gp_ctx* c, int n_probes, int kp);
+
+// logdet.cu: ln|Khat| by the truncated Taylor series of ln(I - C) with the
+// probes of the last FP32 CG run (m terms); fills the SLQ scalars' slots.
+int taylor_logdet(gp_ctx* c, int n_probes, int kp, int m);
 
 // predict.cu: posterior mean at ns test points (device arrays) from alpha =
 // K^-1 y in original point order (device, c->n doubles), over the last assembly.

@@ -36,6 +36,7 @@ GP_FLAG_TIME_KERNELS = 1
 GP_FLAG_SPMM_CPASYNC = 2
 GP_FLAG_SPMM_TMA = 4
 GP_FLAG_SPMM_TMA_WIDE = 8
+GP_FLAG_LOGDET_TAYLOR = 16
 
 GP_SPMM_CPASYNC = 0
 GP_SPMM_TMA = 1
