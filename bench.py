@@ -294,8 +294,8 @@ def main():
                 "launches_timed": n_spmm,
                 "share_of_step": t_spmm / ms,
                 "limiter": ("L1/shared data pipe: gathers of 144-byte P rows staged through shared memory "
-                            "(ncu: l1tex throughput 77 % of peak, DRAM 17 %; profiles/k_bspmm_mixture_1m.md)")
-                if kname.startswith("k_bspmm_f32") else "TMA gather4 request rate (profiles/k_bspmm_mixture_1m.md)"}
+                            "(ncu: l1tex throughput 77 % of peak, DRAM 17 %)")
+                if kname.startswith("k_bspmm_f32") else "TMA gather4 request rate"}
     t_asm = statistics.mean(i["t_assemble_ms"] for i in infos)
     t_fill = statistics.mean(i["t_fill_kernel_ms"] for i in infos)
     t_adj = statistics.mean(i["t_adjoint_kernel_ms"] for i in infos)

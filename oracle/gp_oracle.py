@@ -22,8 +22,7 @@ Paper sections used (arXiv 2205.09070):
     estimator of Boutsidis et al., truncated Taylor series of ln(I - C) with
     Hutchinson probes, beside stochastic Lanczos quadrature).
 
-Readings where the paper is silent, garbled or inconsistent (each is listed in
-DESIGN.md as well):
+Readings where the paper is silent, garbled or inconsistent:
   * Eq. (eq:bump) prints the indicator as chi(r < |x - x0|); the text calls the
     bumps compactly supported, so the support is the open ball |x - x0| < r.
   * beta is a fixed shape constant (default 1), not a hyperparameter: the
