@@ -57,7 +57,7 @@ def args_parse():
     ap.add_argument("--cpu-sample", type=int, default=1200)
     ap.add_argument("--precond-block", type=int, default=None,
                     help="block-Jacobi block size of the preconditioned CG (default: the library's)")
-    ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide"],
+    ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide", "cpasync_wide"],
                     help="SpMM form: the library's autotuner (auto) or a forced form; profiling runs force "
                          "the form the plain run chose, since the tuner's timings are meaningless under ncu")
     return ap.parse_args()
@@ -128,7 +128,8 @@ def peaks() -> dict:
 
 
 SPMM_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "spmm.cu")
-SPMM_KERNELS = {0: "k_bspmm_f32<{kq}>", 1: "k_bspmm_tma<{kq},1>", 2: "k_bspmm_tma<{kq},{lw}>"}
+SPMM_KERNELS = {0: "k_bspmm_f32<{kq}>", 1: "k_bspmm_tma<{kq},1>", 2: "k_bspmm_tma<{kq},{lw}>",
+                3: "k_bspmm_f32w<{kq},{lw}>"}
 
 
 def spmm_kernel_name(variant: int, kp: int) -> str:
@@ -141,7 +142,9 @@ SPMM_REGIONS = {  # source region of each SpMM form in spmm.cu (first marker inc
     "k_bspmm_f32": ("// A: Q = Khat P on the 8x1 block CSR.",
                     "// ---------------------------------------------------------------- TMA form"),
     "k_bspmm_tma": ("// ---------------------------------------------------------------- TMA form",
-                    "// ---------------------------------------------------------------- host side"),
+                    "// ---------------------------------------------------------------- wide cp.async form"),
+    "k_bspmm_f32w": ("// ---------------------------------------------------------------- wide cp.async form",
+                     "// ---------------------------------------------------------------- host side"),
 }
 
 
@@ -356,8 +359,9 @@ def main():
                            "l2": "working set larger than L2 (CSR re-assembled every step)",
                            "n_active": n_act, "nnz": nnz, "kp": kp, "cg_iters": infos[-1]["iters"],
                 "lanczos_iters": infos[-1]["lanczos_iters"], "precond_block": infos[-1]["precond_block"],
-                "spmm_form": ["cp.async stage", "TMA gather4 stage", "TMA gather4 stage, wide lanes"][
-                    infos[-1]["spmm_variant"]] if infos[-1]["spmm_variant"] >= 0 else None},
+                "spmm_form": ["cp.async stage", "TMA gather4 stage", "TMA gather4 stage, wide lanes",
+                              "cp.async stage, wide lanes"][infos[-1]["spmm_variant"]]
+                if infos[-1]["spmm_variant"] >= 0 else None},
                 "lml": lml, "logdet_stderr": infos[-1]["logdet_stderr"],
                 "assembly": {"nnz_per_s": nnz / (t_asm * 1e-3), "ms": t_asm, "fill_kernel_ms": t_fill},
                 "adjoint_kernel_ms": t_adj,

@@ -105,6 +105,8 @@ typedef struct {
 #define GP_FLAG_SPMM_CPASYNC  2  /* stage filled by per-lane cp.async copies */
 #define GP_FLAG_SPMM_TMA      4  /* stage filled by TMA: tile::gather4 of P rows, bulk copy of values */
 #define GP_FLAG_SPMM_TMA_WIDE 8  /* TMA stage, 2 or 3 float4 columns per lane (else as GP_FLAG_SPMM_TMA) */
+#define GP_FLAG_SPMM_CPASYNC_WIDE 32  /* cp.async stage, 2 or 3 float4 columns per lane (else as
+                                         GP_FLAG_SPMM_CPASYNC) */
 
 /* gp_opts.flags: estimate ln|K| with the randomized estimator the paper cites
  * (Sec. 2.5, Boutsidis et al.) instead of stochastic Lanczos quadrature: on
@@ -122,6 +124,7 @@ typedef struct {
 #define GP_SPMM_CPASYNC  0
 #define GP_SPMM_TMA      1
 #define GP_SPMM_TMA_WIDE 2
+#define GP_SPMM_CPASYNC_WIDE 3
 
 typedef struct {
   int64_t n;              /* points */

@@ -15,7 +15,8 @@
 //     load/store unit then serves only the shared-memory reads of the
 //     arithmetic.  The wide form gives each lane LW float4 columns of P, so
 //     that one warp step applies ten blocks instead of three and the block
-//     values are read from shared memory a third as often.
+//     values are read from shared memory a third as often;
+//   * GP_SPMM_CPASYNC_WIDE: the per-lane cp.async stage with the wide lanes.
 // Every form computes, per output element, a sum of the same products; the
 // forms differ only in the order of the FP32 additions.
 #include <cuda.h>
@@ -543,6 +544,185 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_tma(int64_t n, int64_t n
   }
 }
 
+// ---------------------------------------------------------------- wide cp.async form
+// The per-lane cp.async stage of k_bspmm_f32 with the lane layout of the wide
+// TMA form: each lane holds LW float4 columns for the 8 rows of a block row,
+// so a warp step applies NG = 32 / (KQ / LW) blocks (10 at kp = 36) and the
+// block values are read from shared memory a third as often.  The groups'
+// partial rows are added through the stage buffer just consumed, RP rows per
+// pass (the buffer holds kChunk (KP + 8) floats).
+constexpr int cpw_rows_per_pass(int ng, int kq) {
+  return ng * 8 * kq * 4 <= kChunk * (4 * kq + kBR)   ? 8
+         : ng * 4 * kq * 4 <= kChunk * (4 * kq + kBR) ? 4
+         : ng * 2 * kq * 4 <= kChunk * (4 * kq + kBR) ? 2
+                                                       : 1;
+}
+
+template <int KQ, int LW>
+__global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t nblk,
+                                                             const int64_t* __restrict__ brp,
+                                                             const int32_t* __restrict__ bcol,
+                                                             const float4* __restrict__ bval,
+                                                             const float4* __restrict__ P, float4* __restrict__ Q,
+                                                             double* __restrict__ part, gp::CgState* st) {
+  const int it = st->iter;
+  if (st->fin[it & 1]) return;
+  static_assert(KQ % LW == 0 && LW > 1, "wide lanes");
+  constexpr int G = KQ / LW;
+  constexpr int NG = 32 / G;
+  constexpr int KP = 4 * KQ;
+  constexpr int kStage = kChunk * (KP + kBR);  // floats per stage buffer
+  constexpr int RP = cpw_rows_per_pass(NG, KQ);
+  constexpr int M = 32 / KQ;
+  extern __shared__ float4 smem_f4[];
+  float* stage = (float*)smem_f4 + (size_t)(threadIdx.x >> 5) * 2 * kStage;
+  __shared__ double shp[kSpmmWarps][32][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane - grp * G;
+  const bool act = grp < NG;
+  const int slot = lane < M * KQ ? lane % KQ : -1;
+  gpd::Dot2 pq0, pq1, pq2, pq3;
+  const int64_t nent = brp[nblk];
+  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * blockIdx.x / gridDim.x);
+  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (blockIdx.x + 1) / gridDim.x);
+  const int64_t b0 = cb0 + w;
+  if (b0 < b1) {
+    // stage a chunk as k_bspmm_f32 does: KQ 16-byte pieces per P row, then the
+    // chunk's block values
+    auto issue = [&](ChunkPos c, int jl, int buf) {
+      if (c.bb < b1) {
+        const int64_t e = __ldg(brp + c.bb + 1);
+        const int cnt = (int)min((int64_t)kChunk, e - c.base);
+        float* dst = stage + buf * kStage;
+#pragma unroll
+        for (int i = 0; i < KQ; ++i) {
+          const int q = lane + 32 * i;  // piece q: entry q / KQ, slot q % KQ
+          const int ent = q / KQ;
+          const int j = __shfl_sync(kFull, jl, ent < 32 ? ent : 31);
+          if (ent < cnt) cp_async16(dst + ent * KP + 4 * (q - ent * KQ), P + (int64_t)j * KQ + (q - ent * KQ));
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int q = lane + 32 * i;
+          if (q < 2 * cnt) cp_async16(dst + kChunk * KP + 4 * q, bval + 2 * c.base + q);
+        }
+      }
+      cp_async_commit();
+    };
+    auto col_of = [&](ChunkPos c) -> int {
+      if (c.bb >= b1) return 0;
+      const int64_t idx = c.base + lane;
+      return idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
+    };
+    ChunkPos cur{b0, __ldg(brp + b0)};
+    ChunkPos nx1 = next_chunk(cur, brp, b1);
+    issue(cur, col_of(cur), 0);
+    int j1 = col_of(nx1);
+    float2 acc[kBR][2 * LW];
+#pragma unroll
+    for (int r = 0; r < kBR; ++r)
+#pragma unroll
+      for (int u = 0; u < 2 * LW; ++u) acc[r][u] = make_float2(0.f, 0.f);
+    int buf = 0;
+    while (cur.bb < b1) {
+      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp, b1) : nx1;
+      issue(nx1, j1, buf ^ 1);            // copies of chunk c+1 in flight
+      const int j2 = col_of(nx2);          // indices of chunk c+2 in flight
+      cp_async_wait<1>();                  // chunk c has landed
+      __syncwarp();
+      const int64_t e = __ldg(brp + cur.bb + 1);
+      const int cnt = (int)min((int64_t)kChunk, e - cur.base);
+      const float* sp = stage + buf * kStage;
+      const float* sv = sp + kChunk * KP;
+      constexpr int kSteps = (kChunk + NG - 1) / NG;
+#pragma unroll 2
+      for (int t = 0; t < kSteps; ++t) {
+        const int src = t * NG + grp;
+        if (act && src < cnt) {
+          const float* prow = sp + src * KP + 4 * LW * gl;
+          float4 pj[LW];
+#pragma unroll
+          for (int u = 0; u < LW; ++u) pj[u] = *(const float4*)(prow + 4 * u);
+          const float4 v0 = *(const float4*)(sv + src * kBR);
+          const float4 v1 = *(const float4*)(sv + src * kBR + 4);
+          const float vv[kBR] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+          for (int r = 0; r < kBR; ++r) {
+            const float2 v2 = make_float2(vv[r], vv[r]);
+#pragma unroll
+            for (int u = 0; u < LW; ++u) {
+              acc[r][2 * u] = __ffma2_rn(v2, make_float2(pj[u].x, pj[u].y), acc[r][2 * u]);
+              acc[r][2 * u + 1] = __ffma2_rn(v2, make_float2(pj[u].z, pj[u].w), acc[r][2 * u + 1]);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (cur.base + kChunk >= e) {
+        // last chunk of block row cur.bb: groups write their partial rows to
+        // the consumed buffer, then lane l sums slot l % KQ of rows l / KQ + M i
+        float4* scr = (float4*)(stage + buf * kStage);
+#pragma unroll
+        for (int r0 = 0; r0 < kBR; r0 += RP) {
+          if (act) {
+#pragma unroll
+            for (int r = 0; r < RP; ++r)
+#pragma unroll
+              for (int u = 0; u < LW; ++u)
+                scr[(grp * RP + r) * KQ + gl * LW + u] = make_float4(
+                    acc[r0 + r][2 * u].x, acc[r0 + r][2 * u].y, acc[r0 + r][2 * u + 1].x, acc[r0 + r][2 * u + 1].y);
+          }
+          __syncwarp();
+          if (slot >= 0) {
+            for (int r = lane / KQ; r < RP; r += M) {
+              float4 sum = scr[r * KQ + slot];
+              for (int g2 = 1; g2 < NG; ++g2) {
+                const float4 t = scr[(g2 * RP + r) * KQ + slot];
+                sum.x += t.x;
+                sum.y += t.y;
+                sum.z += t.z;
+                sum.w += t.w;
+              }
+              const int64_t row = cur.bb * kBR + r0 + r;
+              if (row < n) {
+                Q[row * KQ + slot] = sum;
+                const float4 pp = __ldg(P + row * KQ + slot);
+                pq0.add(pp.x, sum.x);
+                pq1.add(pp.y, sum.y);
+                pq2.add(pp.z, sum.z);
+                pq3.add(pp.w, sum.w);
+              }
+            }
+          }
+          __syncwarp();
+        }
+#pragma unroll
+        for (int r = 0; r < kBR; ++r)
+#pragma unroll
+          for (int u = 0; u < 2 * LW; ++u) acc[r][u] = make_float2(0.f, 0.f);
+      }
+      cur = nx1;
+      nx1 = nx2;
+      j1 = j2;
+      buf ^= 1;
+    }
+    cp_async_wait<0>();
+  }
+  shp[w][lane][0] = slot >= 0 ? pq0.value() : 0.0;
+  shp[w][lane][1] = slot >= 0 ? pq1.value() : 0.0;
+  shp[w][lane][2] = slot >= 0 ? pq2.value() : 0.0;
+  shp[w][lane][3] = slot >= 0 ? pq3.value() : 0.0;
+  __syncthreads();
+  if (threadIdx.x < KP) {
+    const int q = threadIdx.x >> 2, cc = threadIdx.x & 3;
+    double t = 0.0;
+    for (int ww = 0; ww < kSpmmWarps; ++ww)
+      for (int l = 0; l < 32; ++l)
+        if ((l < M * KQ ? l % KQ : -1) == q) t += shp[ww][l][cc];
+    part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
+  }
+}
+
 // ---------------------------------------------------------------- host side
 typedef void (*CpAsyncFn)(int64_t, int64_t, const int64_t*, const int32_t*, const float4*, const float4*, float4*,
                           double*, gp::CgState*);
@@ -550,34 +730,38 @@ typedef void (*TmaFn)(int64_t, int64_t, const int64_t*, const int32_t*, const fl
                       const float4*, float4*, double*, gp::CgState*);
 
 template <int KQ>
-void fill_fns(CpAsyncFn* cp, TmaFn* tn, TmaFn* tw) {
+void fill_fns(CpAsyncFn* cp, TmaFn* tn, TmaFn* tw, CpAsyncFn* cw) {
   cp[KQ] = k_bspmm_f32<KQ>;
   tn[KQ] = k_bspmm_tma<KQ, 1>;
-  tw[KQ] = wide_lw(KQ) > 1 ? (TmaFn)k_bspmm_tma<KQ, wide_lw(KQ)> : nullptr;
+  if constexpr (wide_lw(KQ) > 1) {
+    tw[KQ] = k_bspmm_tma<KQ, wide_lw(KQ)>;
+    cw[KQ] = k_bspmm_f32w<KQ, wide_lw(KQ)>;
+  }
 }
 
 struct FnTable {
   CpAsyncFn cp[18] = {};
   TmaFn tn[18] = {};
   TmaFn tw[18] = {};
+  CpAsyncFn cw[18] = {};
   FnTable() {
-    fill_fns<1>(cp, tn, tw);
-    fill_fns<2>(cp, tn, tw);
-    fill_fns<3>(cp, tn, tw);
-    fill_fns<4>(cp, tn, tw);
-    fill_fns<5>(cp, tn, tw);
-    fill_fns<6>(cp, tn, tw);
-    fill_fns<7>(cp, tn, tw);
-    fill_fns<8>(cp, tn, tw);
-    fill_fns<9>(cp, tn, tw);
-    fill_fns<10>(cp, tn, tw);
-    fill_fns<11>(cp, tn, tw);
-    fill_fns<12>(cp, tn, tw);
-    fill_fns<13>(cp, tn, tw);
-    fill_fns<14>(cp, tn, tw);
-    fill_fns<15>(cp, tn, tw);
-    fill_fns<16>(cp, tn, tw);
-    fill_fns<17>(cp, tn, tw);
+    fill_fns<1>(cp, tn, tw, cw);
+    fill_fns<2>(cp, tn, tw, cw);
+    fill_fns<3>(cp, tn, tw, cw);
+    fill_fns<4>(cp, tn, tw, cw);
+    fill_fns<5>(cp, tn, tw, cw);
+    fill_fns<6>(cp, tn, tw, cw);
+    fill_fns<7>(cp, tn, tw, cw);
+    fill_fns<8>(cp, tn, tw, cw);
+    fill_fns<9>(cp, tn, tw, cw);
+    fill_fns<10>(cp, tn, tw, cw);
+    fill_fns<11>(cp, tn, tw, cw);
+    fill_fns<12>(cp, tn, tw, cw);
+    fill_fns<13>(cp, tn, tw, cw);
+    fill_fns<14>(cp, tn, tw, cw);
+    fill_fns<15>(cp, tn, tw, cw);
+    fill_fns<16>(cp, tn, tw, cw);
+    fill_fns<17>(cp, tn, tw, cw);
   }
 };
 const FnTable& fns() {
@@ -642,6 +826,7 @@ bool spmm_available(int variant, int kp) {
     case GP_SPMM_CPASYNC: return true;
     case GP_SPMM_TMA: return encode_fn() != nullptr;
     case GP_SPMM_TMA_WIDE: return encode_fn() != nullptr && fns().tw[kq] != nullptr;
+    case GP_SPMM_CPASYNC_WIDE: return fns().cw[kq] != nullptr;
     default: return false;
   }
 }
@@ -651,8 +836,8 @@ int spmm_plan(gp_ctx* c, int kp, int variant, SpmmPlan* p) {
   const int kq = kp / 4;
   p->variant = variant;
   p->kp = kp;
-  if (variant == GP_SPMM_CPASYNC) {
-    p->fn = (const void*)fns().cp[kq];
+  if (variant == GP_SPMM_CPASYNC || variant == GP_SPMM_CPASYNC_WIDE) {
+    p->fn = (const void*)(variant == GP_SPMM_CPASYNC ? fns().cp[kq] : fns().cw[kq]);
     p->smem = (size_t)kSpmmWarps * 2 * kChunk * (kp + kBR) * sizeof(float);
   } else {
     p->fn = (const void*)(variant == GP_SPMM_TMA ? fns().tn[kq] : fns().tw[kq]);
@@ -678,7 +863,7 @@ void spmm_launch(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st) {
   const float4* P = (const float4*)c->P.p;
   float4* Q = (float4*)c->Q.p;
   double* part = (double*)c->part_a.p;
-  if (p.variant == GP_SPMM_CPASYNC) {
+  if (p.variant == GP_SPMM_CPASYNC || p.variant == GP_SPMM_CPASYNC_WIDE) {
     void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st};
     cudaLaunchKernel(p.fn, dim3(p.grid), dim3(kSpmmThreads), args, p.smem, s);
   } else {
@@ -688,13 +873,15 @@ void spmm_launch(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st) {
 }
 
 int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan) {
-  const int forced = (flags & GP_FLAG_SPMM_CPASYNC)     ? GP_SPMM_CPASYNC
-                     : (flags & GP_FLAG_SPMM_TMA)       ? GP_SPMM_TMA
-                     : (flags & GP_FLAG_SPMM_TMA_WIDE)  ? GP_SPMM_TMA_WIDE
-                                                        : -1;
+  const int forced = (flags & GP_FLAG_SPMM_CPASYNC)        ? GP_SPMM_CPASYNC
+                     : (flags & GP_FLAG_SPMM_TMA)          ? GP_SPMM_TMA
+                     : (flags & GP_FLAG_SPMM_TMA_WIDE)     ? GP_SPMM_TMA_WIDE
+                     : (flags & GP_FLAG_SPMM_CPASYNC_WIDE) ? GP_SPMM_CPASYNC_WIDE
+                                                           : -1;
   if (forced >= 0) {
-    // a wide form that would hold one float4 per lane is the plain TMA form
-    const int v = forced == GP_SPMM_TMA_WIDE && !spmm_available(forced, kp) ? GP_SPMM_TMA : forced;
+    // a wide form that would hold one float4 per lane is its narrow form
+    int v = forced;
+    if (!spmm_available(v, kp)) v = v == GP_SPMM_TMA_WIDE ? GP_SPMM_TMA : v == GP_SPMM_CPASYNC_WIDE ? GP_SPMM_CPASYNC : v;
     return spmm_plan(c, kp, v, plan);
   }
   const TuneKey key{c->device, kp, c->n_act, c->nblk, c->nbent};
@@ -712,7 +899,7 @@ int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan) {
   int best = GP_SPMM_CPASYNC;
   float best_ms = 0.f;
   int status = GP_OK;
-  for (int v = GP_SPMM_CPASYNC; v <= GP_SPMM_TMA_WIDE && status == GP_OK; ++v) {
+  for (int v = GP_SPMM_CPASYNC; v <= GP_SPMM_CPASYNC_WIDE && status == GP_OK; ++v) {
     if (!spmm_available(v, kp)) continue;
     SpmmPlan p;
     status = spmm_plan(c, kp, v, &p);

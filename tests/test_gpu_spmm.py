@@ -1,6 +1,6 @@
-"""GPU parity of the three forms of the FP32 sparse product Q = Khat P (per-lane
-cp.async stage, TMA gather4 stage, TMA stage with several float4 columns per
-lane) and of the autotuner that picks one.  Each form is forced through
+"""GPU parity of the four forms of the FP32 sparse product Q = Khat P (per-lane
+cp.async stage, TMA gather4 stage, and either stage with several float4
+columns per lane) and of the autotuner that picks one.  Each form is forced through
 gp_opts.flags and checked through the C ABI against the oracle's dense
 evaluation of the same estimator (same probes, Sec. 2.5 solves), over column
 counts kp = 4 .. 68 that select every lane layout; on a clustered matrix the
@@ -15,7 +15,7 @@ from paper_2205_09070_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FORMS = ["cpasync", "tma", "tma_wide"]
+FORMS = ["cpasync", "tma", "tma_wide", "cpasync_wide"]
 
 
 @pytest.fixture(scope="module")
@@ -33,9 +33,12 @@ def wide_lw(kq):
 
 
 def expected_variant(G, form, kp):
-    if form == "cpasync":
+    wide = wide_lw(kp // 4) > 1
+    if form == "cpasync" or (form == "cpasync_wide" and not wide):
         return G.GP_SPMM_CPASYNC
-    if form == "tma" or wide_lw(kp // 4) == 1:
+    if form == "cpasync_wide":
+        return G.GP_SPMM_CPASYNC_WIDE
+    if form == "tma" or not wide:
         return G.GP_SPMM_TMA
     return G.GP_SPMM_TMA_WIDE
 
@@ -150,7 +153,8 @@ def test_autotuner_choice_is_stable_and_shared(lib):
     l2, g2, i2 = a.lml_grad(x, y, p.h, o)
     b = lib.GP(p.dim, p.n1, p.n2, p.beta)
     l3, g3, i3 = b.lml_grad(x, y, p.h, o)
-    assert i1["spmm_variant"] in (lib.GP_SPMM_CPASYNC, lib.GP_SPMM_TMA, lib.GP_SPMM_TMA_WIDE)
+    assert i1["spmm_variant"] in (lib.GP_SPMM_CPASYNC, lib.GP_SPMM_TMA, lib.GP_SPMM_TMA_WIDE,
+                                  lib.GP_SPMM_CPASYNC_WIDE)
     assert i1["spmm_variant"] == i2["spmm_variant"] == i3["spmm_variant"]
     assert l1 == l2 == l3
     assert np.array_equal(g1, g2) and np.array_equal(g1, g3)
