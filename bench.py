@@ -156,15 +156,15 @@ def spmm_source_sha(kernel: str) -> str:
 
 
 def traffic_record(kernel: str, kp: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current SpMM source; else None (the counters are stale)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the kernel's current source; else None (stale counters)."""
     path = os.path.join(ROOT, "profiles", "spmm_traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    if rec.get("kernel") != kernel or rec.get("kp") != kp or rec.get("source_sha256") != spmm_source_sha(kernel):
-        return None
-    return rec
+    for rec in json.load(open(path)).get("records", []):
+        if rec.get("kernel") == kernel and rec.get("kp") == kp and rec.get("source_sha256") == spmm_source_sha(kernel):
+            return rec
+    return None
 
 
 def workload(n: int):
