@@ -10,8 +10,6 @@
 // solves Khat u = b it feeds are the same.
 #include <math.h>
 
-#include <type_traits>
-
 #include "gp_internal.cuh"
 
 namespace {
@@ -21,16 +19,13 @@ namespace {
 // live in dynamic shared memory, B x (B+1) entries each (B <= 32; larger
 // blocks take the FP32 set-up below).
 template <int B>
-using PcY = double;
-
-template <int B>
 __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const float* __restrict__ val,
                                                 float* __restrict__ Mout, int* __restrict__ part,
                                                 gp::AsmScalars* s) {
   extern __shared__ double pc_sm[];
   double (*A)[B + 1] = (double (*)[B + 1])pc_sm;
-  PcY<B> (*Y)[B + 1] = (PcY<B> (*)[B + 1])(pc_sm + B * (B + 1));
+  double (*Y)[B + 1] = (double (*)[B + 1])(pc_sm + B * (B + 1));
   __shared__ int bad_any;
   const int t = threadIdx.x;
   if (t == 0) bad_any = 0;
@@ -71,8 +66,8 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
     if (t < nb) {
       for (int r = t; r < nb; ++r) {
         double v = r == t ? 1.0 : 0.0;
-        for (int k = t; k < r; ++k) v -= A[r][k] * (double)Y[k][t];
-        Y[r][t] = (PcY<B>)(v / A[r][r]);
+        for (int k = t; k < r; ++k) v -= A[r][k] * Y[k][t];
+        Y[r][t] = v / A[r][r];
       }
     }
     __syncthreads();
@@ -83,7 +78,7 @@ __global__ void __launch_bounds__(B) k_pc_setup(int64_t n, int64_t nblk, const i
       if (t < nb && jj < nb) {
         double v = 0.0;
         const int k0 = t > jj ? t : jj;
-        for (int k = k0; k < nb; ++k) v += (double)Y[k][t] * (double)Y[k][jj];
+        for (int k = k0; k < nb; ++k) v += Y[k][t] * Y[k][jj];
         m = (float)v;
       }
       Mb[t * B + jj] = m;
@@ -217,7 +212,7 @@ int launch_setup32(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
 
 template <int B>
 int launch_setup(gp_ctx* c, int64_t nblk, gp::AsmScalars* s) {
-  const size_t smem = (sizeof(double) + sizeof(PcY<B>)) * B * (B + 1);
+  const size_t smem = 2 * sizeof(double) * B * (B + 1);
   GP_CUDA(cudaFuncSetAttribute(k_pc_setup<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc_setup<B>, B, smem));
