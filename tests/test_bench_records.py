@@ -1,0 +1,27 @@
+"""CPU checks of bench.py's bookkeeping: every SpMM form maps to a kernel
+name whose source region exists in spmm.cu, and the committed DRAM-traffic
+records are keyed to the current source of their kernels."""
+
+import json
+import os
+
+import bench
+
+
+def test_spmm_kernel_names_and_source_regions():
+    names = {v: bench.spmm_kernel_name(v, 36) for v in range(4)}
+    assert names == {0: "k_bspmm_f32<9>", 1: "k_bspmm_tma<9,1>", 2: "k_bspmm_tma<9,3>", 3: "k_bspmm_f32w<9,3>"}
+    src = open(bench.SPMM_SOURCE).read()
+    for name in names.values():
+        a, b = bench.SPMM_REGIONS[name.split("<")[0]]
+        assert src.index(a) < src.index(b)
+        assert len(bench.spmm_source_sha(name)) == 64
+
+
+def test_committed_traffic_records_match_the_current_source():
+    path = os.path.join(bench.ROOT, "profiles", "spmm_traffic.json")
+    recs = json.load(open(path))["records"]
+    assert recs
+    for rec in recs:
+        assert bench.traffic_record(rec["kernel"], rec["kp"]) is not None, rec["kernel"]
+        assert rec["bytes_per_launch"] == rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
