@@ -66,3 +66,15 @@ def test_header_constants_and_info_layout_match_the_binding():
     body = text[text.index("typedef struct {\n  int64_t n;"):text.index("} gp_info;")]
     members = re.findall(r"^\s*(?:int64_t|int32_t|double)\s+(\w+);", body, re.M)
     assert members == [f for f, _ in G.Info._fields_]
+
+
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header must compile as C99 on its own
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-x", "c", "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", HEADER],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
