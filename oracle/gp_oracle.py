@@ -521,3 +521,28 @@ def sparsity_upper_bound(h, dim, n1, n2, domain_volume=1.0):
         v = [ball_volume(dim, r) for r in p["radii"][i]]
         total += sum(v) ** 2
     return total / domain_volume ** 2
+
+
+def sparsity_upper_bound_grad(h, dim, n1, n2, domain_volume=1.0):
+    """d s / d h for the bound above, differentiated by hand: only the bump
+    radii enter, with d Vol(dim, r) / d r = dim Vol(dim, r) / r, so
+      d s / d r_ij = 2 (sum_k Vol(r_ik)) dim Vol(r_ij) / r_ij / Vol(X)^2."""
+    p = unpack_h(h, dim, n1, n2)
+    g = np.zeros(n_params(dim, n1, n2))
+    for i in range(n1):
+        v = [ball_volume(dim, r) for r in p["radii"][i]]
+        tot = sum(v)
+        for j in range(n2):
+            r = p["radii"][i, j]
+            g[(i * n2 + j) * (dim + 2) + dim] = 2.0 * tot * dim * v[j] / r / domain_volume ** 2
+    return g
+
+
+def augmented_objective(lml, grad_lml, h, dim, n1, n2, domain_volume=1.0):
+    """Eq. (eq:augmented): ln L + (1 - s) ln L = (2 - s(h)) ln L(h) with s the
+    sparsity bound above, and its gradient by the product rule:
+      (2 - s) d ln L / d h - ln L d s / d h.
+    Returns (value, gradient, s)."""
+    s = sparsity_upper_bound(h, dim, n1, n2, domain_volume)
+    ds = sparsity_upper_bound_grad(h, dim, n1, n2, domain_volume)
+    return (2.0 - s) * lml, (2.0 - s) * np.asarray(grad_lml, dtype=np.float64) - lml * ds, s

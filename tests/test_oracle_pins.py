@@ -430,3 +430,37 @@ def test_taylor_logdet_same_probes_split_and_statistics():
     exact = np.linalg.slogdet(O.dense_K(x, h, dim, n1, n2))[1]
     se = np.std(gam, ddof=1) / math.sqrt(len(gam))
     assert abs(ld - exact) <= 5 * se + 1e-3 * abs(exact)
+
+
+# --------------------------------------------------------------------- augmented objective
+
+def test_sparsity_gradient_and_augmented_objective_against_finite_differences():
+    # d s / d h by central differences of the bound (only radii move it), and
+    # the augmented objective's product rule on a smooth stand-in for ln L
+    rng = np.random.default_rng(61)
+    for dim in (1, 2, 3):
+        n1, n2 = 3, 4
+        h = W.pack_h(rng.uniform(0, 1, (n1, n2, dim)), rng.uniform(0.05, 0.3, (n1, n2)),
+                     rng.normal(0, 1, (n1, n2)), 0.1, 1.0, 1e-3)
+        vol = 1.7
+        g = O.sparsity_upper_bound_grad(h, dim, n1, n2, vol)
+        eps = 1e-6
+        for q in range(len(h)):
+            hp, hm = h.copy(), h.copy()
+            hp[q] += eps
+            hm[q] -= eps
+            fd = (O.sparsity_upper_bound(hp, dim, n1, n2, vol) - O.sparsity_upper_bound(hm, dim, n1, n2, vol)) / (2 * eps)
+            assert g[q] == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+        def f(hh):  # smooth stand-in for ln L with a known gradient
+            return -float(np.sum(hh ** 2)) - 3.0, -2.0 * hh
+
+        val, gr, s = O.augmented_objective(*f(h), h, dim, n1, n2, vol)
+        assert val == pytest.approx((2 - s) * f(h)[0], rel=1e-15)
+        for q in range(len(h)):
+            hp, hm = h.copy(), h.copy()
+            hp[q] += eps
+            hm[q] -= eps
+            vp = O.augmented_objective(*f(hp), hp, dim, n1, n2, vol)[0]
+            vm = O.augmented_objective(*f(hm), hm, dim, n1, n2, vol)[0]
+            assert gr[q] == pytest.approx((vp - vm) / (2 * eps), rel=1e-6, abs=1e-9)
