@@ -156,6 +156,29 @@ typedef struct {
 /* Number of hyperparameters: n_funcs*n_bumps*(dim+2) + 3. */
 int64_t gp_n_params(const gp_kernel_desc* desc);
 
+/* Sparsity bound of Sec. 2.2 (Eq. eq:sparsity_estimate and the two equations
+ * after it): for uniformly distributed points the fraction of non-zero
+ * covariances is at most
+ *   s(h) = sum_i sum_j sum_k Vol(dim, r_ij) Vol(dim, r_ik) / domain_volume^2,
+ *   Vol(dim, r) = pi^(dim/2) / Gamma(dim/2 + 1) r^dim,
+ * over the bump radii r_ij of h (layout as for gp_assemble).  Writes s and,
+ * if grad is not NULL, d s / d h (gp_n_params doubles; only the radius
+ * entries are non-zero).  Host arrays; no device work.  GP_ERR_INVALID_ARG
+ * for a non-positive or non-finite radius or domain volume. */
+int gp_sparsity_estimate(const gp_kernel_desc* desc, const double* h, double domain_volume, double* s,
+                         double* grad);
+
+/* Augmented objective of Sec. 2.4 (Eq. eq:augmented): ln L + (1 - s) ln L =
+ * (2 - s(h)) ln L(h), which prefers sparse covariance matrices while the
+ * likelihood keeps priority (s in [0, 1]), and its gradient by the product
+ * rule, (2 - s) d ln L / d h - ln L d s / d h.  lml and lml_grad are what
+ * gp_lml_grad returned for h; grad (gp_n_params doubles) may be NULL, and
+ * then lml_grad may be NULL too.  s_out (may be NULL) receives s(h), which
+ * is also what a caller compares with its sparsity requirement for the
+ * constrained form (Eq. eq:constrained).  Host arrays; no device work. */
+int gp_augmented(const gp_kernel_desc* desc, const double* h, double domain_volume, double lml,
+                 const double* lml_grad, double* value, double* grad, double* s_out);
+
 /* Default options: FP32_MIXED, 32 probes, 50 Lanczos steps, 10000 iterations,
  * rtol 1e-6, seed 0x5eed, check every 16 iterations, precond_block 128. */
 void gp_default_opts(gp_opts* opts);

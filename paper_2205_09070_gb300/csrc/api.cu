@@ -312,6 +312,49 @@ int64_t gp_n_params(const gp_kernel_desc* d) {
   return (int64_t)d->n_funcs * d->n_bumps * (d->dim + 2) + 3;
 }
 
+int gp_sparsity_estimate(const gp_kernel_desc* d, const double* h, double domain_volume, double* s, double* grad) {
+  GP_CHECK(check_desc(d));
+  if (!h || !s || !(domain_volume > 0.0) || !isfinite(domain_volume)) return GP_ERR_INVALID_ARG;
+  const int dim = d->dim, n1 = d->n_funcs, n2 = d->n_bumps, np = dim + 2;
+  // Vol(dim, r) = pi^(dim/2) / Gamma(dim/2 + 1) r^dim
+  const double unit = pow(M_PI, 0.5 * dim) / tgamma(0.5 * dim + 1.0);
+  const double inv_v2 = 1.0 / (domain_volume * domain_volume);
+  for (int b = 0; b < n1 * n2; ++b) {
+    const double r = h[b * np + dim];
+    if (!(r > 0.0) || !isfinite(r)) return GP_ERR_INVALID_ARG;
+  }
+  if (grad)
+    for (int64_t q = 0; q < gp_n_params(d); ++q) grad[q] = 0.0;
+  double total = 0.0;
+  for (int i = 0; i < n1; ++i) {
+    double vsum = 0.0;  // sum over the bumps of f_i of their ball volumes
+    for (int j = 0; j < n2; ++j) vsum += unit * pow(h[(i * n2 + j) * np + dim], dim);
+    total += vsum * vsum;  // = sum_j sum_k Vol(r_ij) Vol(r_ik)
+    if (grad)
+      for (int j = 0; j < n2; ++j) {
+        const double r = h[(i * n2 + j) * np + dim];
+        grad[(i * n2 + j) * np + dim] = 2.0 * vsum * dim * unit * pow(r, dim) / r * inv_v2;
+      }
+  }
+  *s = total * inv_v2;
+  return GP_OK;
+}
+
+int gp_augmented(const gp_kernel_desc* d, const double* h, double domain_volume, double lml, const double* lml_grad,
+                 double* value, double* grad, double* s_out) {
+  if (!value || (grad && !lml_grad) || !isfinite(lml)) return GP_ERR_INVALID_ARG;
+  GP_CHECK(check_desc(d));
+  const int64_t np = gp_n_params(d);
+  std::vector<double> ds(grad ? (size_t)np : 0);
+  double s = 0.0;
+  GP_CHECK(gp_sparsity_estimate(d, h, domain_volume, &s, grad ? ds.data() : nullptr));
+  *value = (2.0 - s) * lml;
+  if (grad)
+    for (int64_t q = 0; q < np; ++q) grad[q] = (2.0 - s) * lml_grad[q] - lml * ds[q];
+  if (s_out) *s_out = s;
+  return GP_OK;
+}
+
 void gp_default_opts(gp_opts* o) {
   if (!o) return;
   o->precision = GP_FP32_MIXED;

@@ -48,7 +48,7 @@ SPMM_FLAGS = {"cpasync": GP_FLAG_SPMM_CPASYNC, "tma": GP_FLAG_SPMM_TMA, "tma_wid
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
             "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_predict", "gp_lml", "gp_lml_grad",
-            "gp_lml_grad_batched", "gp_status_string"]
+            "gp_lml_grad_batched", "gp_status_string", "gp_sparsity_estimate", "gp_augmented"]
 
 
 class KernelDesc(ctypes.Structure):
@@ -120,10 +120,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                 ctypes.POINTER(Info)]
     lib.gp_lml_grad_batched.argtypes = [vp, i32, dp, dp, dp, dp, ctypes.POINTER(Opts), dp, dp,
                                         ctypes.POINTER(Info)]
+    lib.gp_sparsity_estimate.argtypes = [ctypes.POINTER(KernelDesc), dp, ctypes.c_double, dp, dp]
+    lib.gp_augmented.argtypes = [ctypes.POINTER(KernelDesc), dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
     lib.gp_status_string.argtypes = [ctypes.c_int]
     lib.gp_status_string.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_destroy", "gp_set_stream", "gp_assemble", "gp_get_csr", "gp_get_csr_noalloc",
-                 "gp_solve", "gp_predict", "gp_lml",
+                 "gp_solve", "gp_predict", "gp_lml", "gp_sparsity_estimate", "gp_augmented",
                  "gp_lml_grad", "gp_lml_grad_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -132,6 +134,35 @@ def load(path: str | None = None) -> ctypes.CDLL:
 
 def status_string(status: int) -> str:
     return load().gp_status_string(status).decode()
+
+
+def sparsity_estimate(dim: int, n_funcs: int, n_bumps: int, h, domain_volume: float, beta: float = 1.0):
+    """(s, d s / d h): the sparsity bound of the paper's kernel (host-side)."""
+    d = KernelDesc(dim, n_funcs, n_bumps, beta)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    s = ctypes.c_double()
+    g = np.zeros(hh.shape[0], np.float64)
+    st = load().gp_sparsity_estimate(ctypes.byref(d), hh.ctypes.data, float(domain_volume), ctypes.byref(s),
+                                     g.ctypes.data)
+    if st != GP_OK:
+        raise GPError(st, "gp_sparsity_estimate")
+    return s.value, g
+
+
+def augmented_objective(dim: int, n_funcs: int, n_bumps: int, h, domain_volume: float, lml: float, lml_grad,
+                        beta: float = 1.0):
+    """(value, gradient, s) of (2 - s(h)) ln L(h) given ln L and its gradient."""
+    d = KernelDesc(dim, n_funcs, n_bumps, beta)
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    lg = np.ascontiguousarray(lml_grad, dtype=np.float64)
+    v = ctypes.c_double()
+    s = ctypes.c_double()
+    g = np.zeros(hh.shape[0], np.float64)
+    st = load().gp_augmented(ctypes.byref(d), hh.ctypes.data, float(domain_volume), float(lml), lg.ctypes.data,
+                             ctypes.byref(v), g.ctypes.data, ctypes.byref(s))
+    if st != GP_OK:
+        raise GPError(st, "gp_augmented")
+    return v.value, g, s.value
 
 
 def default_opts(**kw) -> Opts:
