@@ -53,6 +53,7 @@ output sequence.
 from __future__ import annotations
 
 import math
+from decimal import Decimal, getcontext, localcontext
 
 import numpy as np
 
@@ -254,6 +255,170 @@ def dense_K(x, h, dim, n1, n2, beta=1.0, chunk=1024):
 
 
 # ----------------------------------------------------------------------------
+# The same entries to full accuracy (decimal arithmetic)
+# ----------------------------------------------------------------------------
+#
+# Evaluated in float64, the printed Eq. (eq:kstat) cancels as rho -> 1: its
+# two terms are of order s = sqrt(1 - rho^2) while their sum is of order s^5,
+# so an entry near the edge of the stationary support keeps only a few
+# correct digits.  A bump of Eq. (eq:bump) is steep near its own edge, and a
+# sum over bumps or functions may cancel as well.  The functions below take
+# every float64 input as the exact number it represents, evaluate the same
+# printed expressions with HP_DIGITS significant decimal digits (Python's
+# decimal module), and round only the finished entry to float64.  They are the
+# reference for element-wise value parity.  Which pairs are stored is still
+# decided by the float64 predicates above (support tests d^2 < r_s^2 and
+# |x - c|^2 / r^2 < 1), exactly as the plain definition is written.
+
+HP_DIGITS = 60
+
+
+def _hp_pi():
+    """pi to the working precision by Machin's formula
+    pi = 16 arctan(1/5) - 4 arctan(1/239), arctan(1/q) = sum_k (-1)^k / ((2k+1) q^(2k+1))."""
+    def arctan_inv(q):
+        q = Decimal(q)
+        total, power, k = Decimal(0), 1 / q, 0
+        eps = Decimal(10) ** (-(getcontext().prec + 5))
+        while power > eps:
+            term = power / (2 * k + 1)
+            total += term if k % 2 == 0 else -term
+            power /= q * q
+            k += 1
+        return total
+    return 16 * arctan_inv(5) - 4 * arctan_inv(239)
+
+
+def _hp_constants():
+    """C = sqrt(2) / (3 sqrt(pi)) of Eq. (eq:kstat) at the working precision."""
+    return Decimal(2).sqrt() / (3 * _hp_pi().sqrt())
+
+
+def kstat_hp(rho2, C=None):
+    """Eq. (eq:kstat) exactly as printed, as a function of rho^2 = d^2 / r^2
+    (a Decimal), evaluated at the context's precision:
+        C (3 rho^2 log(rho / (1 + s)) + (2 rho^2 + 1) s),  s = sqrt(1 - rho^2),
+    for rho < 1, and 0 otherwise; at rho = 0 the term rho^2 log(rho) is taken
+    at its limit, 0."""
+    C = _hp_constants() if C is None else C
+    if rho2 >= 1:
+        return Decimal(0)
+    s = (1 - rho2).sqrt()
+    if rho2 == 0:
+        return C * s
+    rho = rho2.sqrt()
+    return C * (3 * rho2 * (rho / (1 + s)).ln() + (2 * rho2 + 1) * s)
+
+
+def _hp_candidate_bumps(x, h, dim, n1, n2):
+    """For each point of x, the bumps (m, b) whose float64 support test is
+    close to passing (q < 1 + 1e-9); the exact evaluation then decides with
+    u > 0.  Returns (unpacked h, list of bump lists, one per point)."""
+    p = unpack_h(h, dim, n1, n2)
+    x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
+    near = np.zeros((x.shape[0], n1 * n2), dtype=bool)
+    for m in range(n1):
+        for b in range(n2):
+            q = np.sum((x - p["centres"][m, b]) ** 2, axis=1) / (p["radii"][m, b] ** 2)
+            near[:, m * n2 + b] = q < 1.0 + 1e-9
+    return p, [[(int(t) // n2, int(t) % n2) for t in np.nonzero(row)[0]] for row in near]
+
+
+def bump_sums_hp(point, p, dim, n1, n2, beta, bumps):
+    """f_m(point) for m < n1 (Eq. eq:bump) in decimal: the sum over the listed
+    bumps (m, b) of a exp(beta - beta / u), u = 1 - |x - c|^2 / r^2 > 0."""
+    f = [Decimal(0)] * n1
+    xb = [Decimal(float(point[k])) for k in range(dim)]
+    B = Decimal(float(beta))
+    for m, b in bumps:
+        c = p["centres"][m, b]
+        d2 = sum((xb[k] - Decimal(float(c[k]))) ** 2 for k in range(dim))
+        u = 1 - d2 / Decimal(float(p["radii"][m, b])) ** 2
+        if u > 0:
+            f[m] += Decimal(float(p["amps"][m, b])) * (B - B / u).exp()
+    return f
+
+
+def entries_hp(x, h, dim, n1, n2, rows, cols, beta=1.0, digits=HP_DIGITS):
+    """K_ij = A k~(|x_i - x_j| / r_s) sum_m f_m(x_i) f_m(x_j) + sigma_n^2 [i = j]
+    (Eq. eq:bump_kernel with Eq. eq:kstat and Eq. eq:bump) for the listed pairs
+    (i, j) = (rows[t], cols[t]), evaluated to `digits` significant digits and
+    rounded to float64.  The caller lists pairs of the pattern; a pair whose
+    exact distance reaches r_s (possible only at a float64 tie) gets k~ = 0."""
+    x = np.asarray(x, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    out = np.empty(rows.shape[0])
+    pts = np.unique(np.concatenate([rows, cols]))      # only the points the pairs touch
+    with localcontext() as ctx:
+        ctx.prec = digits
+        p, cand = _hp_candidate_bumps(x[pts], h, dim, n1, n2)
+        slot = {int(i): t for t, i in enumerate(pts)}
+        C = _hp_constants()
+        A = Decimal(p["A"])
+        s2 = Decimal(p["sigma2"])
+        rs2 = Decimal(p["r_s"]) ** 2
+        fcache, memo = {}, {}
+
+        def F(i):
+            if i not in fcache:
+                fcache[i] = bump_sums_hp(x[i], p, dim, n1, n2, beta, cand[slot[i]])
+            return fcache[i]
+
+        for t in range(rows.shape[0]):
+            i, j = int(rows[t]), int(cols[t])
+            key = (min(i, j), max(i, j))
+            if key not in memo:
+                Fi, Fj = F(i), F(j)
+                S = sum(Fi[m] * Fj[m] for m in range(n1))
+                if i == j:
+                    v = A * C * S + s2
+                else:
+                    d2 = sum((Decimal(float(x[i, k])) - Decimal(float(x[j, k]))) ** 2 for k in range(dim))
+                    v = A * kstat_hp(d2 / rs2, C) * S
+                memo[key] = float(v)
+            out[t] = memo[key]
+    return out
+
+
+def cross_K_hp(xs, x, h, dim, n1, n2, beta=1.0, digits=HP_DIGITS):
+    """kappa[a, i] = k(xs_a, x_i) as cross_K computes it, with every pair in
+    support (float64 test d^2 < r_s^2) evaluated by the decimal route of
+    entries_hp; pairs out of support are exactly 0."""
+    p = unpack_h(h, dim, n1, n2)
+    xs = np.asarray(xs, dtype=np.float64).reshape(-1, dim)
+    x = np.asarray(x, dtype=np.float64)
+    d2 = np.sum((xs[:, None, :] - x[None, :, :]) ** 2, axis=2)
+    insup = d2 < p["r_s"] ** 2
+    kappa = np.zeros(d2.shape)
+    if not np.any(insup):
+        return kappa
+    with localcontext() as ctx:
+        ctx.prec = digits
+        pq, cand_q = _hp_candidate_bumps(xs, h, dim, n1, n2)
+        touched = np.nonzero(np.any(insup, axis=0))[0]
+        _, cand_x = _hp_candidate_bumps(x[touched], h, dim, n1, n2)
+        slot = {int(i): t for t, i in enumerate(touched)}
+        C = _hp_constants()
+        A = Decimal(p["A"])
+        rs2 = Decimal(p["r_s"]) ** 2
+        fx = {}
+        for a in np.nonzero(np.any(insup, axis=1))[0]:
+            fq = bump_sums_hp(xs[a], pq, dim, n1, n2, beta, cand_q[a])
+            if all(v == 0 for v in fq):
+                continue
+            for i in np.nonzero(insup[a])[0]:
+                if i not in fx:
+                    fx[i] = bump_sums_hp(x[i], pq, dim, n1, n2, beta, cand_x[slot[int(i)]])
+                S = sum(fq[m] * fx[i][m] for m in range(n1))
+                if S == 0:
+                    continue
+                dd = sum((Decimal(float(xs[a, k])) - Decimal(float(x[i, k]))) ** 2 for k in range(dim))
+                kappa[a, i] = float(A * kstat_hp(dd / rs2, C) * S)
+    return kappa
+
+
+# ----------------------------------------------------------------------------
 # Sec. 2.1: posterior mean at test points, kappa^T (K + V)^-1 y (prior mean 0)
 # ----------------------------------------------------------------------------
 
@@ -452,7 +617,7 @@ def logdet_taylor_same_probes(x, h, dim, n1, n2, n_probes, m, seed, beta=1.0):
 
 
 def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
-                         beta=1.0, with_grad=True):
+                         beta=1.0, with_grad=True, with_bounds=False):
     """The stochastic LML and gradient the GPU path estimates, computed densely.
 
     K splits into the active block K_a (rows inside some bump) and
@@ -464,7 +629,21 @@ def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
       tr(K^-1 K_theta) ~ (1/nv) sum_l z_l^T Khat^-1 Khat_theta z_l
                          + [inactive rows, exact: N_inact / sigma_n^2 for noise]
     where Khat_theta = D^-1/2 K_theta D^-1/2 (D held fixed).
-    Returns (lml, grad or None, info dict with the pieces)."""
+    Returns (lml, grad or None, info dict with the pieces).
+
+    with_bounds=True adds, per parameter, what bounds the gradient's change
+    when the solves stop early.  If ahat = Khat^-1 yhat is replaced by
+    ahat + Khat^-1 r (residual r) and u_l = Khat^-1 z_l by u_l + Khat^-1 r_l,
+    the gradient moves, to first order, by
+      r^T Khat^-1 Khat_theta ahat  -  (1/2nv) sum_l r_l^T Khat^-1 Khat_theta z_l,
+    so with |r| <= eps |yhat| and |r_l| <= eps |z_l| its change is at most
+      eps * (sens_quad + sens_trace / 2),
+      sens_quad  = |yhat| |Khat^-1 Khat_theta ahat|,
+      sens_trace = (1/nv) sum_l |z_l| |Khat^-1 Khat_theta z_l|.
+    It also adds the standard error of the Hutchinson trace over the probes
+    (sample standard deviation of z_l^T Khat^-1 Khat_theta z_l over l, / sqrt(nv)),
+    which bounds the distance to the exact gradient statistically (the
+    estimate's trace part enters the gradient with weight 1/2)."""
     p = unpack_h(h, dim, n1, n2)
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
@@ -493,13 +672,27 @@ def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
         return lml, None, info
     # U_hat = Khat^-1 Z; the estimator per parameter is (1/nv) tr(U_hat^T Khat_theta Z).
     Uhat = np.linalg.solve(Khat, Z) if act.size else np.zeros((0, n_probes))
-    grad = np.zeros(n_params(dim, n1, n2))
+    npar = n_params(dim, n1, n2)
+    grad = np.zeros(npar)
+    if with_bounds:
+        Kinv = np.linalg.inv(Khat) if act.size else np.zeros((0, 0))
+        yhat = y[act] * Dm
+        ahat = Kinv @ yhat
+        sens_q, sens_t, tr_se = np.zeros(npar), np.zeros(npar), np.zeros(npar)
     for i, dK in dK_dtheta_all(x, h, dim, n1, n2, beta):
         dKa = dK[np.ix_(act, act)]
         dKhat = dKa * Dm[:, None] * Dm[None, :]
         tr_act = float(np.sum(Uhat * (dKhat @ Z))) / n_probes if act.size else 0.0
         tr_inact = float(np.sum(np.diag(dK)[inact])) / s2
         grad[i] = 0.5 * float(alpha @ (dK @ alpha)) - 0.5 * (tr_act + tr_inact)
+        if with_bounds and act.size:
+            W = Kinv @ (dKhat @ np.column_stack([ahat, Z]))
+            sens_q[i] = float(np.linalg.norm(yhat) * np.linalg.norm(W[:, 0]))
+            sens_t[i] = float(np.mean(np.linalg.norm(Z, axis=0) * np.linalg.norm(W[:, 1:], axis=0)))
+            per_probe = np.sum(Uhat * (dKhat @ Z), axis=0)
+            tr_se[i] = float(np.std(per_probe, ddof=1) / math.sqrt(n_probes)) if n_probes > 1 else 0.0
+    if with_bounds:
+        info.update({"grad_sens_quad": sens_q, "grad_sens_trace": sens_t, "grad_trace_se": tr_se})
     return lml, grad, info
 
 

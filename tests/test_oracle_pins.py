@@ -62,6 +62,105 @@ def test_kstat_matches_independent_series():
     assert np.max(np.abs(got[mid] / ref[mid] - 1.0)) < 1e-12
 
 
+def decimal_series_kstat(s2, digits=50):
+    """k~/C as the positive series in s (Decimal, `digits` digits):
+    sum_{n>=2} 6 s^(2n+1) / ((2n-1)(2n+1)), summed until the terms vanish."""
+    from decimal import Decimal, localcontext
+    with localcontext() as ctx:
+        ctx.prec = digits
+        s2 = Decimal(s2)
+        s = s2.sqrt()
+        total, n, power = Decimal(0), 2, s ** 5
+        while True:
+            term = 6 * power / ((2 * n - 1) * (2 * n + 1))
+            if term < total * Decimal(10) ** (-digits - 2) or term == 0:
+                break
+            total += term
+            power *= s2
+            n += 1
+        return total
+
+
+def test_kstat_hp_matches_series_up_to_the_support_edge():
+    # the printed form evaluated with 60 digits against the independently
+    # derived positive series (no cancellation) for rho in [0.5, 1), down to
+    # s^2 = 1 - rho^2 = 1e-14 where the float64 printed form has no digit left
+    from decimal import Decimal, localcontext
+    C = O.KSTAT_PREFACTOR
+    for s2 in [0.75, 0.5, 0.1, 1e-2, 1.99e-2, 1e-3, 1e-4, 1e-6, 1e-8, 1e-10, 1e-12, 1e-14]:
+        with localcontext() as ctx:
+            ctx.prec = O.HP_DIGITS
+            got = O.kstat_hp(1 - Decimal(s2))
+        ref = float(decimal_series_kstat(s2)) * C
+        assert float(got) == pytest.approx(ref, rel=1e-14), s2
+    # where the float64 printed form does not cancel, it agrees to rounding
+    rho = np.linspace(0.0, 0.5, 51)
+    with localcontext() as ctx:
+        ctx.prec = O.HP_DIGITS
+        hp = np.array([float(O.kstat_hp(Decimal(float(r)) ** 2)) for r in rho])
+    assert np.allclose(hp, O.kstat(rho), rtol=1e-14, atol=0)
+    assert hp[0] == pytest.approx(golden()["kstat_at_zero"], rel=1e-15)
+
+
+def test_entries_hp_match_float64_where_well_conditioned():
+    # full-accuracy entries against the float64 brute force: equal to a few
+    # ulps away from the support edges; everywhere within the float64 form's
+    # absolute cancellation error (a few ulps of its O(1) terms, times A C
+    # sum_m |f_m f_m|) plus the float64 bump's relative error near its own
+    # edge (beta ulp / u^2, below 1e-11 while the bump is a normal number);
+    # diagonal A C sum F^2 + s2
+    x, y, h, dim, n1, n2 = small_problem(seed=61, n=120, dim=3, n1=2, n2=3, r_s=0.45, radii=(0.3, 0.6))
+    p = O.unpack_h(h, dim, n1, n2)
+    rp, col, val = O.assemble_csr(x, h, dim, n1, n2)
+    rows = np.repeat(np.arange(len(x)), np.diff(rp))
+    hp = O.entries_hp(x, h, dim, n1, n2, rows, col)
+    d2 = np.sum((x[rows] - x[col]) ** 2, axis=1)
+    F, mask = O.bump_table(x, h, dim, n1, n2)
+    S_abs = np.sum(np.abs(F[rows] * F[col]), axis=1)
+    assert np.all(np.abs(hp - val) <= 1e-14 * p["A"] * O.KSTAT_PREFACTOR * S_abs + 1e-11 * np.abs(val))
+    # away from every edge (rho < 0.9, each point well inside its bumps or
+    # outside all) the float64 form is accurate to rounding
+    def deep(i):
+        ok = True
+        for m in range(n1):
+            for b in range(n2):
+                q = np.sum((x[i] - p["centres"][m, b]) ** 2) / p["radii"][m, b] ** 2
+                ok = ok and (q < 0.8 or q > 1.0)
+        return ok
+    good = (d2 < (0.9 * p["r_s"]) ** 2) & np.array([deep(i) and deep(j) for i, j in zip(rows, col)]) \
+        & (S_abs > 0) & (np.abs(val) > 1e-3 * p["A"] * O.KSTAT_PREFACTOR * S_abs)
+    assert good.sum() > 50
+    assert np.allclose(hp[good], val[good], rtol=1e-13, atol=0)
+    # symmetric and the diagonal closed form
+    hp_t = O.entries_hp(x, h, dim, n1, n2, col, rows)
+    assert np.array_equal(hp, hp_t)
+    dg = rows == col
+    assert np.allclose(hp[dg], p["A"] * O.KSTAT_PREFACTOR * np.sum(F ** 2, axis=1)[rows[dg]] + p["sigma2"],
+                       rtol=1e-14)
+
+
+def test_bump_sums_hp_match_float64_inside_and_the_edge_series():
+    # f_m in decimal against the float64 bump table well inside the support,
+    # and against exp(beta - beta/u) with u from an exact rational near the edge
+    from decimal import Decimal, localcontext
+    x, y, h, dim, n1, n2 = small_problem(seed=62, n=200, dim=2, n1=2, n2=2)
+    F, mask = O.bump_table(x, h, dim, n1, n2)
+    p, cand = O._hp_candidate_bumps(x, h, dim, n1, n2)
+    with localcontext() as ctx:
+        ctx.prec = O.HP_DIGITS
+        for i in range(len(x)):
+            f = O.bump_sums_hp(x[i], p, dim, n1, n2, 1.0, cand[i])
+            for m in range(n1):
+                assert float(f[m]) == pytest.approx(F[i, m], rel=1e-12, abs=1e-300)
+        # a point at distance r (1 - 2^-30) from a unit bump: u = 2^-29 - 2^-60
+        pt = np.array([1.0 - 2.0 ** -30, 0.0])
+        hh = W.pack_h(np.zeros((1, 1, 2)), np.array([[1.0]]), np.array([[1.0]]), 0.1, 1.0, 1e-2)
+        pp, cc = O._hp_candidate_bumps(pt[None, :], hh, 2, 1, 1)
+        val = O.bump_sums_hp(pt, pp, 2, 1, 1, 1.0, cc[0])[0]
+        u = 1 - (Decimal(1) - Decimal(2) ** -30) ** 2
+        assert val == (1 - 1 / u).exp()
+
+
 def test_kstat_support_and_monotone():
     rho = np.linspace(0.0, 1.5, 3001)
     k = O.kstat(rho)
@@ -350,20 +449,24 @@ def test_cross_K_matches_pure_python_brute_force():
                 tot += p["amps"][m, b] * math.exp(1.0 - 1.0 / (1.0 - q))
         return tot
 
+    kappa_hp = O.cross_K_hp(xs, x, h, dim, n1, n2)
     checked = 0
     for a in range(len(xs)):
         for i in range(len(x)):
             d = math.dist(xs[a], x[i])
             S = sum(f(xs[a], m) * f(x[i], m) for m in range(n1))
             if d >= p["r_s"] or S == 0.0:
-                assert kappa[a, i] == 0.0
+                assert kappa[a, i] == 0.0 and kappa_hp[a, i] == 0.0
                 continue
             rho = d / p["r_s"]
+            # k~ from the independent positive series where it has converged
+            # (no cancellation), the printed form nearer the centre
             k = series_kstat(np.array([rho]), terms=4000)[0] if rho >= 0.3 else O.kstat(np.array([rho]))[0]
-            # the printed form of Eq. eq:kstat cancels as rho -> 1: entries
-            # there are tiny and carry an absolute error of order 1e-12 k~(0)
-            floor = 1e-12 * p["A"] * O.KSTAT_PREFACTOR * abs(S)
-            assert kappa[a, i] == pytest.approx(p["A"] * k * S, rel=1e-9, abs=floor)
+            # the full-accuracy route agrees everywhere; the float64 printed
+            # form only where it does not cancel
+            assert kappa_hp[a, i] == pytest.approx(p["A"] * k * S, rel=1e-9)
+            if rho < 0.9:
+                assert kappa[a, i] == pytest.approx(p["A"] * k * S, rel=1e-9)
             checked += 1
     assert checked > 20
 
