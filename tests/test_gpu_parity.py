@@ -10,15 +10,15 @@ import pytest
 from oracle import gp_oracle as O
 from paper_2205_09070_gb300 import workloads as W
 
-from helpers import canonical_gpu_csr, canonical_oracle_csr, value_tol_ok
+from helpers import canonical_gpu_csr, canonical_oracle_csr, grad_ok, value_tol_ok
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {  # (rtol, scaled floor) for K entries, see helpers.value_tol_ok
-    "fp64": (1e-12, 1e-14),
-    "fp32": (1e-5, 1e-7),
-}
+# relative tolerance of every stored entry against the oracle's full-accuracy
+# value (helpers.value_tol_ok): the FP32 bound is the one the method's FP32
+# path is held to; FP64 leaves three decades over its rounding (~1e-15)
+RTOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +52,7 @@ def test_assembly_pattern_bit_exact_and_values(lib, case, prec):
     info = gp.assemble(x, p.h, precision=prec)
     csr = gp.get_csr()
     r, c, v = canonical_gpu_csr(csr)
-    ro, co, vo, mask = canonical_oracle_csr(p.x, p.h, p.dim, p.n1, p.n2, p.beta)
+    ro, co, vo, mask = canonical_oracle_csr(p.x, p.h, p.dim, p.n1, p.n2, p.beta, key=case)
     assert info["n_active"] == int(np.sum(mask != 0))
     assert info["nnz"] == len(ro)
     assert np.array_equal(r, ro) and np.array_equal(c, co)          # bit-exact pattern
@@ -63,7 +63,8 @@ def test_assembly_pattern_bit_exact_and_values(lib, case, prec):
     diag = np.zeros(p.n)
     dm = ro == co
     diag[ro[dm]] = vo[dm]
-    ok, worst = value_tol_ok(v, vo, diag, ro, co, *TOL[prec])
+    ok, worst = value_tol_ok(v, vo, diag, ro, co, RTOL[prec], prec)
+    print(case, prec, "nnz", len(ro), "worst relative error", worst)
     assert ok, worst
     gp.close()
 
@@ -105,15 +106,31 @@ def test_lml_and_grad_same_probes(lib, prec, B):
     opts = lib.default_opts(precision=prec, n_probes=nv, lanczos_steps=m, cg_rtol=rtol, seed=seed,
                             precond_block=B)
     lml, grad, info = gp.lml_grad(x, y, p.h, opts)
-    ref, gref, rinfo = O.lml_grad_same_probes(p.x, p.y, p.h, p.dim, p.n1, p.n2, nv, m, seed)
+    ref, gref, rinfo = same_probe_reference(p, nv, m, seed)
     print(prec, B, "lml", lml, ref, "logdet", info["logdet"], rinfo["logdet"], "quad", info["quad_form"],
           rinfo["quad_form"], "iters", info["iters"])
     assert info["quad_form"] == pytest.approx(rinfo["quad_form"], rel=1e-9 if prec == "fp64" else 1e-5)
     assert info["logdet"] == pytest.approx(rinfo["logdet"], rel=1e-7 if prec == "fp64" else 1e-5)
-    err = np.abs(grad - gref) / (np.abs(gref) + 1e-3 * np.abs(gref).max())
-    print(prec, "grad worst rel", err.max())
-    assert err.max() < (1e-5 if prec == "fp64" else 1e-3)
+    # every component within the first-order effect of stopping the solves at
+    # rtol (helpers.grad_solver_bound)
+    ok, worst = grad_ok(grad, gref, rinfo, rtol, GRAD_SAFETY[prec])
+    print(prec, B, "grad |dg| / (rtol (sens_quad + sens_trace / 2))", worst)
+    assert ok, worst
     gp.close()
+
+
+# safety factor over the first-order solver bound (helpers.grad_solver_bound):
+# the bound itself held with ratios <= 0.15 on GB300 for every block size and
+# both precisions; 2 leaves room for the rounding the first-order model omits
+GRAD_SAFETY = {"fp64": 2.0, "fp32": 2.0}
+_REF = {}
+
+
+def same_probe_reference(p, nv, m, seed):
+    key = (p.name, p.n, nv, m, seed)
+    if key not in _REF:
+        _REF[key] = O.lml_grad_same_probes(p.x, p.y, p.h, p.dim, p.n1, p.n2, nv, m, seed, with_bounds=True)
+    return _REF[key]
 
 
 def test_gradient_identities_hold_on_gpu(lib):

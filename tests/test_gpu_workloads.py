@@ -9,6 +9,8 @@ import pytest
 from oracle import gp_oracle as O
 from paper_2205_09070_gb300 import workloads as W
 
+from helpers import grad_ok, grad_solver_bound
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -37,20 +39,24 @@ def test_gradient_163_parameters(G):
     for prec, rtol in (("fp64", 1e-10), ("fp32", 1e-6)):
         o = G.default_opts(precision=prec, n_probes=nv, lanczos_steps=m, cg_rtol=rtol, seed=seed, precond_block=0)
         res[prec] = gp.lml_grad(dev(p.x), dev(p.y), p.h, o)
-    ref, gref, rinfo = O.lml_grad_same_probes(p.x, p.y, p.h, p.dim, p.n1, p.n2, nv, m, seed)
-    scale = np.abs(gref) + 1e-3 * np.abs(gref).max()
-    for prec, tol in (("fp64", 1e-6), ("fp32", 2e-3)):
+    ref, gref, rinfo = O.lml_grad_same_probes(p.x, p.y, p.h, p.dim, p.n1, p.n2, nv, m, seed, with_bounds=True)
+    for prec, rtol, safety in (("fp64", 1e-10, 2.0), ("fp32", 1e-6, 2.0)):
         lml, g, info = res[prec]
         assert info["quad_form"] == pytest.approx(rinfo["quad_form"], rel=1e-8 if prec == "fp64" else 1e-5)
         assert info["logdet"] == pytest.approx(rinfo["logdet"], rel=1e-7 if prec == "fp64" else 1e-5)
-        assert np.max(np.abs(g - gref) / scale) < tol, prec
-    # exact gradient: the deterministic part (1/2 a^T dK a) is shared, the
-    # trace part is a 16-probe Hutchinson estimate; most components agree to
-    # within a few estimator standard errors
+        # every component within the first-order solver bound (helpers.grad_solver_bound)
+        ok, worst = grad_ok(g, gref, rinfo, rtol, safety)
+        print(prec, "grad |dg| / (rtol (sens_quad + sens_trace / 2))", worst)
+        assert ok, (prec, worst)
+    # exact gradient: the quadratic part is shared, the trace part is a
+    # 16-probe Hutchinson estimate whose trace enters with weight 1/2: every
+    # component within 6 of its standard errors (plus the solver bound)
     _, gx = O.lml_grad_exact(p.x, p.y, p.h, p.dim, p.n1, p.n2)
     g = res["fp64"][1]
-    rel = np.abs(g - gx) / (np.abs(gx) + 1e-2 * np.abs(gx).max())
-    assert np.median(rel) < 0.1
+    tol = 6.0 * 0.5 * rinfo["grad_trace_se"] + grad_solver_bound(rinfo, 1e-10, 2.0)
+    z = np.abs(g - gx) / np.where(tol > 0, tol, 1.0)
+    print("exact gradient: worst |g - g_exact| / (6 SE / 2 + solver bound)", float(z.max()))
+    assert np.all((np.abs(g - gx) <= tol) | ((tol == 0) & (np.abs(g - gx) <= 1e-12 * np.abs(gx).max())))
     gp.close()
 
 
@@ -90,7 +96,6 @@ def test_bench_workload_sampled_rows(G):
     csr = gp.get_csr()
     table = O.bump_table(p.x, p.h, p.dim, p.n1, p.n2)
     P = O.unpack_h(p.h, p.dim, p.n1, p.n2)
-    kdiag = P["A"] * O.KSTAT_PREFACTOR * np.sum(table[0] ** 2, axis=1) + P["sigma2"]
     assert info["n_active"] == int(np.sum(table[1] != 0))
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(len(csr.perm), 48, replace=False))
@@ -104,11 +109,14 @@ def test_bench_workload_sampled_rows(G):
         pat, v = O.pair_rows(p.x, p.h, p.dim, p.n1, p.n2, [i], table=table)
         ref_cols = np.nonzero(pat[0])[0]
         assert np.array_equal(cols[order], ref_cols), r
-        ref_v = v[0, ref_cols]
-        # |dK_ij| <= 1e-5 |K_ij| + 1e-7 sqrt(K_ii K_jj) (Cauchy-Schwarz scale of a PSD matrix)
+        # values: every entry of the row within 1e-5 relative of the oracle's
+        # full-accuracy value (floor: one FP32 denormal step of Khat)
+        ref_v = O.entries_hp(p.x, p.h, p.dim, p.n1, p.n2, np.full(len(ref_cols), i), ref_cols)
+        kdiag = O.entries_hp(p.x, p.h, p.dim, p.n1, p.n2, ref_cols, ref_cols)
+        kii = kdiag[ref_cols == i][0]
         err = np.abs(vals[order] - ref_v)
-        scale = np.sqrt(kdiag[i] * kdiag[ref_cols])
-        assert np.all(err <= 1e-5 * np.abs(ref_v) + 1e-7 * scale), r
+        floor = 2.0 ** -149 * np.sqrt(kii * kdiag)
+        assert np.all(err <= 1e-5 * np.abs(ref_v) + floor), (r, float(np.max(err / np.abs(ref_v))))
     # Euler identities of the estimator (exact for any probes, see the oracle pins)
     assert P["A"] * g[-2] + P["sigma2"] * g[-1] == pytest.approx(0.5 * info["quad_form"] - 0.5 * p.n, rel=1e-4)
     amp = [b * (p.dim + 2) + p.dim + 1 for b in range(p.n1 * p.n2)]
