@@ -107,6 +107,9 @@ typedef struct {
 #define GP_FLAG_SPMM_TMA_WIDE 8  /* TMA stage, 2 or 3 float4 columns per lane (else as GP_FLAG_SPMM_TMA) */
 #define GP_FLAG_SPMM_CPASYNC_WIDE 32  /* cp.async stage, 2 or 3 float4 columns per lane (else as
                                          GP_FLAG_SPMM_CPASYNC) */
+#define GP_FLAG_SPMM_WINDOW 64  /* column windows: tiles of 8 block rows stream the union of their
+                                   columns through a shared-memory ring filled by TMA bulk copies
+                                   (one persistent CTA per SM); the product also forms the CG step */
 
 /* gp_opts.flags: estimate ln|K| with the randomized estimator the paper cites
  * (Sec. 2.5, Boutsidis et al.) instead of stochastic Lanczos quadrature: on
@@ -125,6 +128,7 @@ typedef struct {
 #define GP_SPMM_TMA      1
 #define GP_SPMM_TMA_WIDE 2
 #define GP_SPMM_CPASYNC_WIDE 3
+#define GP_SPMM_WINDOW 4
 
 typedef struct {
   int64_t n;              /* points */

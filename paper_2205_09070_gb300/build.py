@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgpsparse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "scan.cu", "assemble.cu", "solve.cu", "spmm.cu", "adjoint.cu", "noalloc.cu", "precond.cu", "predict.cu", "logdet.cu"]
+SOURCES = ["api.cu", "scan.cu", "assemble.cu", "solve.cu", "spmm.cu", "adjoint.cu", "noalloc.cu", "precond.cu", "predict.cu", "logdet.cu", "window.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-pthread",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -228,15 +228,16 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
   } else {
     // SLQ needs the Lanczos coefficients of Khat itself from the probes: a
     // short plain run of lanczos_steps iterations (expected not to converge),
-    // reduced to SLQ terms before the preconditioned run resets the CG state
+    // reduced to SLQ terms before the preconditioned run reuses the CG state
     double lanczos_rel = 0.0;
     const int lst = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->lanczos_steps, o->cg_rtol,
                                o->check_every, &lanczos_iters, &lanczos_rel, false);
     if (lst != GP_OK && lst != GP_ERR_NOT_CONVERGED) return lst;
     // the eigen-solves overlap the preconditioned run (side stream)
     GP_CHECK(gp::slq(c, nv, kp, true));
+    // the preconditioned solves start from the Lanczos run's iterate
     cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters,
-                           &max_rel, true);
+                           &max_rel, true, true);
     const int jst = gp::slq_join(c);
     if (jst != GP_OK) return jst;
   }
@@ -411,13 +412,15 @@ int gp_destroy(gp_ctx* c) {
   gp::DevBuf* bufs[] = {&c->x_in,   &c->y_in,   &c->out_tmp,    &c->bump,      &c->mask0,     &c->F0,
                         &c->pos,    &c->keys,   &c->vals,       &c->keys2,     &c->vals2,     &c->hist,
                         &c->hist_scan, &c->scan_part, &c->cells, &c->perm,     &c->skey,      &c->cellc,
-                        &c->xr,     &c->xs,     &c->Fs,         &c->smask,     &c->dinv,      &c->dinv64,
+                        &c->xr,     &c->xs,     &c->Fs,  &c->Fs64,  &c->smask,     &c->dinv,      &c->dinv64,
                         &c->cnt,    &c->row_ptr, &c->col,       &c->val,       &c->X,         &c->R,
                         &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,
                         &c->asm_s,  &c->csr_tmp, &c->bcnt,     &c->brp,       &c->bcol,      &c->bmask,
                         &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z,
-                        &c->xstar_in, &c->pred_tmp, &c->slq_steps, &c->taylor};
+                        &c->xstar_in, &c->pred_tmp, &c->slq_steps, &c->taylor,
+                        &c->w_cnt,  &c->w_tseg, &c->w_trun,     &c->w_trec,    &c->w_segd,    &c->w_runs,
+                        &c->w_rec};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restric
     }
     uint32_t mask = 0;
     for (int m = 0; m < n1; ++m) {
-      double f = 0.0;
+      double f = 0.0, fc = 0.0;  // compensated sum f + fc over the bumps of f_m
       bool in_m = false;
       for (int j = 0; j < n2; ++j) {
         const gp::BumpParam& bp = sb[m * n2 + j];
@@ -120,6 +120,8 @@ __global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restric
         }
         q32 *= bp.inv_r2_32;
         if (q32 < 1.0f + bp.margin) {
+          // the support test exactly as the plain definition (FP64, this
+          // operation order); the value from u = 1 - q without cancellation
           double d2 = 0.0;
           for (int k = 0; k < dim; ++k) {
             double t = __dsub_rn(xi[k], bp.c[k]);
@@ -127,13 +129,18 @@ __global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restric
           }
           double q = __ddiv_rn(d2, bp.r2);
           if (q < 1.0) {
-            double u = 1.0 - q;
-            f += bp.a * exp(beta - beta / u);
+            const double u = gpd::one_minus_ratio(xi, bp.c, dim, bp.r2, bp.r2l);
+            if (u > 0.0) {
+              double t, e;
+              gpd::two_sum(f, bp.a * exp(beta - beta / u), t, e);
+              f = t;
+              fc += e;
+            }
             in_m = true;
           }
         }
       }
-      F0[i * n1 + m] = f;
+      F0[i * n1 + m] = f + fc;
       if (in_m) mask |= 1u << m;
     }
     mask0[i] = mask;
@@ -266,7 +273,8 @@ __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ 
                                                      const uint32_t* __restrict__ mask0, int n1, double AC,
                                                      double sigma2, int4* __restrict__ cellc,
                                                      float4* __restrict__ xr, double* __restrict__ xs,
-                                                     T* __restrict__ Fs, uint32_t* __restrict__ smask,
+                                                     T* __restrict__ Fs, double* __restrict__ Fs64,
+                                                     uint32_t* __restrict__ smask,
                                                      T* __restrict__ dinv, double* __restrict__ dinv64,
                                                      int2* __restrict__ cells, double* __restrict__ part,
                                                      gp::AsmScalars* s) {
@@ -289,6 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ 
     for (int m = 0; m < n1; ++m) {
       double f = F0[(int64_t)i * n1 + m];
       Fs[p * n1 + m] = (T)f;
+      if (Fs64) Fs64[p * n1 + m] = f;
       sF += f * f;
     }
     smask[p] = mask0[i];
@@ -336,14 +345,18 @@ struct PairArgs {
   const float4* xr;
   const double* xs;
   const void* Fs;
+  const double* Fs64;   // the sorted bump table in FP64 (entry values)
   const void* dinv;
+  const double* dinv64; // D^-1/2 in FP64 (entry values)
   const int64_t* row_ptr;
   int32_t* cnt;
   int32_t* col;
   void* val;
   float scale;   // (h / r_s)^2
   float guard;   // |rho^2 - 1| below this: decide in FP64
-  double rs2;    // r_s^2
+  double rs2;    // r_s^2 rounded to FP64 (the support test d^2 < r_s^2)
+  double rs2l;   // r_s * r_s - rs2 exactly
+  double inv_rs2;
   double AC;     // A * C
   double sigma2;
 };
@@ -380,8 +393,6 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
   __shared__ int sh_pre[kWarps][32];
   __shared__ int sh_off[kWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const T* Fs = (const T*)a.Fs;
-  const T* dinv = (const T*)a.dinv;
   T* val = (T*)a.val;
   const int G[3] = {a.G0, a.G1, a.G2};
   for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < a.n; p += (int64_t)gridDim.x * kWarps) {
@@ -433,11 +444,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
 
     const float4 xi = a.xr[p];
     int64_t out = 0;
-    T di = 0;
-    if (FILL) {
-      out = a.row_ptr[p];
-      di = dinv[p];
-    }
+    if (FILL) out = a.row_ptr[p];
     int count = 0;
     for (int base = 0; base < total; base += 32) {
       const int f = base + lane;
@@ -451,7 +458,9 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
         j = sh_start[w][r] + (f - sh_pre[w][r]);
         const uint32_t mj = a.mask[j];
         if ((mi & mj) != 0u) {
-          T rho2, s2;
+          // support test: FP32 on cell-relative coordinates, decided in FP64
+          // (the plain definition's arithmetic) inside the guard band
+          double e2 = -1.0;
           if (sizeof(T) == 4) {
             const float4 xj = a.xr[j];
             const int op = sh_off[w][r];
@@ -460,38 +469,46 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
             const float dz = (xj.z + (float)(((op >> 4) & 3) - 1)) - xi.z;
             float r2 = (dx * dx + dy * dy + dz * dz) * a.scale;
             if (fabsf(r2 - 1.0f) < a.guard) {
-              const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+              e2 = dist2_fp64(a.xs, a.dim, p, j);
               hit = e2 < a.rs2;
-              rho2 = (T)(e2 / a.rs2);
-              s2 = (T)((a.rs2 - e2) / a.rs2);
             } else {
               hit = r2 < 1.0f;
-              rho2 = (T)r2;
-              s2 = (T)(1.0f - r2);
-              if (FILL && hit && s2 < (T)0.1) {
-                // near the support edge 1 - rho^2 cancels: take it from FP64
-                const double e2 = dist2_fp64(a.xs, a.dim, p, j);
-                rho2 = (T)(e2 / a.rs2);
-                s2 = (T)((a.rs2 - e2) / a.rs2);
-              }
             }
           } else {
-            const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+            e2 = dist2_fp64(a.xs, a.dim, p, j);
             hit = e2 < a.rs2;
-            rho2 = (T)(e2 / a.rs2);
-            s2 = (T)((a.rs2 - e2) / a.rs2);
           }
           if (FILL && hit) {
-            T S = 0;
-            uint32_t common = mi & mj;
-            while (common) {
-              const int m = __ffs(common) - 1;
-              common &= common - 1u;
-              S += Fs[p * a.n1 + m] * Fs[(int64_t)j * a.n1 + m];
+            // the entry's value from the FP64 inputs: rho^2 and s^2 = 1 - rho^2
+            // in FP64 (s^2 without cancellation near the edge), the sum over
+            // the shared functions in FP64 (compensated on the FP64 path),
+            // one rounding to T at the end
+            if (e2 < 0.0) e2 = dist2_fp64(a.xs, a.dim, p, j);
+            double s2 = (a.rs2 - e2) * a.inv_rs2;
+            if (s2 < (sizeof(T) == 4 ? 1e-6 : 1e-2))
+              s2 = gpd::one_minus_ratio(a.xs + p * a.dim, a.xs + (int64_t)j * a.dim, a.dim, a.rs2, a.rs2l);
+            const double rho2 = e2 * a.inv_rs2;
+            double kst = 0.0;
+            if (s2 > 0.0) {
+              if (sizeof(T) == 4) kst = (double)gpd::kstat_unit_f((float)rho2, (float)s2);
+              else kst = gpd::kstat_unit_d(rho2, s2);
             }
-            v = (T)a.AC * gpd::Real<T>::kstat(rho2, s2) * S;
-            if (j == p) v += (T)a.sigma2;
-            v = v * di * dinv[j];
+            const double* Fp = a.Fs64 + p * a.n1;
+            const double* Fj = a.Fs64 + (int64_t)j * a.n1;
+            double S = 0.0;
+            if (sizeof(T) == 4) {
+              uint32_t common = mi & mj;
+              while (common) {
+                const int m = __ffs(common) - 1;
+                common &= common - 1u;
+                S = fma(Fp[m], Fj[m], S);
+              }
+            } else {
+              S = gpd::dot2_bits(Fp, Fj, mi & mj);
+            }
+            double vv = a.AC * kst * S;
+            if (j == p) vv += a.sigma2;
+            v = (T)(vv * a.dinv64[p] * a.dinv64[j]);
           }
         }
       }
@@ -769,7 +786,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
         }
         const double r = q[dim];
         bp.r = r;
-        bp.r2 = r * r;
+        gpd::two_prod(r, r, bp.r2, bp.r2l);
         bp.a = q[dim + 1];
         bp.m = m;
         bp.inv_r2_32 = (float)(1.0 / (r * r));
@@ -848,6 +865,10 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   GP_CHECK(gp::ensure(c, c->xr, (size_t)n_act * sizeof(float4)));
   GP_CHECK(gp::ensure(c, c->xs, (size_t)n_act * dim * sizeof(double)));
   GP_CHECK(gp::ensure(c, c->Fs, (size_t)n_act * n1 * sizeof(T)));
+  // FP32 path: an FP64 copy of the sorted bump table for the entry values
+  // (the FP64 path reads Fs itself)
+  if (sizeof(T) == 4) GP_CHECK(gp::ensure(c, c->Fs64, (size_t)n_act * n1 * sizeof(double)));
+  double* Fs64 = sizeof(T) == 4 ? (double*)c->Fs64.p : nullptr;
   GP_CHECK(gp::ensure(c, c->smask, (size_t)n_act * sizeof(uint32_t)));
   GP_CHECK(gp::ensure(c, c->dinv, (size_t)n_act * sizeof(T)));
   GP_CHECK(gp::ensure(c, c->dinv64, (size_t)n_act * sizeof(double)));
@@ -858,7 +879,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     k_sorted<T><<<gb, kThreads, 0, c->stream>>>(x, n_act, (const uint32_t*)c->keys.p, (const uint32_t*)c->vals.p, g,
                                                 (const double*)c->F0.p, (const uint32_t*)c->mask0.p, n1, AC,
                                                 c->sigma2, (int4*)c->cellc.p, (float4*)c->xr.p, (double*)c->xs.p,
-                                                (T*)c->Fs.p, (uint32_t*)c->smask.p, (T*)c->dinv.p,
+                                                (T*)c->Fs.p, Fs64, (uint32_t*)c->smask.p, (T*)c->dinv.p,
                                                 (double*)c->dinv64.p, (int2*)c->cells.p, (double*)c->part_b.p, s);
     GP_LAUNCH_CHECK();
     c->launches += 1;
@@ -879,12 +900,15 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   pa.xr = (const float4*)c->xr.p;
   pa.xs = (const double*)c->xs.p;
   pa.Fs = c->Fs.p;
+  pa.Fs64 = sizeof(T) == 4 ? (const double*)Fs64 : (const double*)c->Fs.p;
   pa.dinv = c->dinv.p;
+  pa.dinv64 = (const double*)c->dinv64.p;
   pa.cnt = (int32_t*)c->cnt.p;
   const double sc = (g.h / c->r_s) * (g.h / c->r_s);
   pa.scale = (float)sc;
   pa.guard = (float)(1e-4 * sc);
-  pa.rs2 = c->r_s * c->r_s;
+  gpd::two_prod(c->r_s, c->r_s, pa.rs2, pa.rs2l);
+  pa.inv_rs2 = 1.0 / pa.rs2;
   pa.AC = AC;
   pa.sigma2 = c->sigma2;
   const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
@@ -942,6 +966,8 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
                                                         (float*)c->bval.p);
     GP_LAUNCH_CHECK();
     c->launches += 1;
+    // the regrouping for the column-window SpMM form is built on first use
+    // (window.cu), only when that form is timed, forced or chosen
   }
   return GP_OK;
 }
@@ -961,6 +987,8 @@ int assemble(gp_ctx* c, const double* x, int64_t n, const double* h, int precisi
   if (n > (int64_t)INT32_MAX - 1) return GP_ERR_UNSUPPORTED;
   c->n_act = 0;
   c->nnz = 0;
+  c->nblk = 0;
+  c->w_ntiles = 0;
   if (n > 0) {
     int st = precision == GP_FP64 ? assemble_t<double>(c, x, n, h) : assemble_t<float>(c, x, n, h);
     if (st != GP_OK) return st;

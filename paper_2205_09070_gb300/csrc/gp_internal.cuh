@@ -29,6 +29,7 @@ struct BumpParam {
   double r2;           // radius^2
   double a;            // amplitude
   double r;            // radius
+  double r2l;          // radius^2 - r2 exactly (r2 + r2l = radius * radius)
   float c32[kMaxDim];  // centre - lo, FP32 (for the pre-filter)
   float inv_r2_32;     // 1 / r^2, FP32
   float margin;        // pre-filter accepts q32 < 1 + margin, then re-tests in FP64
@@ -109,6 +110,9 @@ struct SpmmPlan {
   const void* fn = nullptr;
   size_t smem = 0;
   unsigned grid = 0;
+  int stages = 0;            // GP_SPMM_WINDOW: shared-memory stages of the segment ring
+  bool fused_alpha = false;  // the product also forms the CG step alpha (its last CTA)
+  int k = 0, m_hist = 0;     // columns of the run and Lanczos steps recorded (fused alpha)
   alignas(64) unsigned char tmap[128] = {};
 };
 
@@ -136,11 +140,17 @@ struct gp_ctx {
   gp::DevBuf mask0, F0, pos;
   gp::DevBuf keys, vals, keys2, vals2, hist, hist_scan, scan_part;
   gp::DevBuf cells;
-  gp::DevBuf perm, skey, cellc, xr, xs, Fs, smask, dinv, dinv64;
+  gp::DevBuf perm, skey, cellc, xr, xs, Fs, Fs64, smask, dinv, dinv64;
   gp::DevBuf cnt, row_ptr, col, val;
   // 8x1 block CSR of the FP32 path (rows 8b..8b+7 per block row)
   gp::DevBuf bcnt, brp, bcol, bmask, bval;
   int64_t nblk = 0, nbent = 0;
+  // the same blocks regrouped for GP_SPMM_WINDOW (window.cu): per tile of
+  // block rows its segments (descriptors), the segments' runs of P rows and
+  // their records (block counts, positions, values); per-tile counts and the
+  // scans of those counts
+  gp::DevBuf w_cnt, w_tseg, w_trun, w_trec, w_segd, w_runs, w_rec;
+  int64_t w_ntiles = 0, w_nseg = 0, w_nrun = 0;
   // block-Jacobi preconditioner (FP32 path): M^-1 per block of pc_block rows
   // (FP32, pc_block^2 each); Z = M^-1 R of the preconditioned CG
   gp::DevBuf pc_Minv, pc_part, Z;
@@ -173,7 +183,7 @@ struct gp_ctx {
   // default stream) and launched on `stream`
   struct CgGraph {
     cudaGraphExec_t exec = nullptr;
-    uint64_t key[32] = {};
+    uint64_t key[48] = {};
   } cg_graph[2];
   cudaStream_t cap_stream = nullptr;
   // side stream for work that overlaps the CG loop (the SLQ eigen-solves):
@@ -212,9 +222,11 @@ int precond_setup(gp_ctx* c, int pc_block);
 int csr_unscaled(gp_ctx* c, double* val_out_dev);
 
 // solve.cu (cg_run: FP32 batched CG on the 8x1 block CSR)
+// warm: keep X from the previous run on the same block and start from the
+// residual B - Khat X (one extra product) instead of X = 0
 int cg_run(gp_ctx* c, int k, int kp, const double* y_dev, int n_probes, uint64_t seed,
            int lanczos_steps, int max_iter, double rtol, int check_every,
-           int* iters_out, double* max_rel_resid, bool use_pc);
+           int* iters_out, double* max_rel_resid, bool use_pc, bool warm = false);
 int cg_run_fp64(gp_ctx* c, int k, const double* y_dev, int n_probes, uint64_t seed,
                 int lanczos_steps, int max_iter, double rtol, int check_every,
                 int* iters_out, double* max_rel_resid);
@@ -243,9 +255,21 @@ int predict_mean(gp_ctx* c, const double* xstar, int64_t ns, const double* alpha
 bool spmm_available(int variant, int kp);
 int spmm_plan(gp_ctx* c, int kp, int variant, SpmmPlan* plan);
 // the form forced by GP_FLAG_SPMM_* in flags, else the autotuner's choice for
-// this matrix shape (timed once per process, needs the CG state of iteration 0)
-int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan);
+// this matrix shape (timed once per process, needs the CG state of iteration
+// 0); k columns of the run and m_hist recorded Lanczos steps, for the forms
+// that also form alpha
+int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan, int k, int m_hist);
 void spmm_launch(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st);
+// window.cu: the column-window form (GP_SPMM_WINDOW): regrouping of the 8x1
+// block CSR built by the assembly, and the product itself (which also forms
+// alpha in its last CTA)
+int window_build(gp_ctx* c);
+bool window_available(gp_ctx* c, int kp);
+int window_plan(gp_ctx* c, int kp, SpmmPlan* plan);
+void window_launch(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st, int k, int m_hist);
+// the same product with another input / output block (cp.async forms only:
+// the TMA forms carry a tensor map of P)
+void spmm_launch_io(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st, const float* in, float* out);
 
 }  // namespace gp
 
@@ -339,6 +363,58 @@ __device__ inline double atanh_minus_s_d(double rho2, double s2) {
   return log((1.0 + s) / sqrt(rho2)) - s;
 }
 
+// ---------------------------------------------------------------- error-free FP64
+// Knuth's TwoSum and the FMA form of Dekker's TwoProduct: a + b = s + e and
+// a * b = p + e exactly, with s = fl(a + b), p = fl(a * b).
+__host__ __device__ inline void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+__host__ __device__ inline void two_prod(double a, double b, double& p, double& e) {
+  p = a * b;
+  e = fma(a, b, -p);
+}
+
+// 1 - |x - c|^2 / r^2 for FP64 points x, c (dim coordinates each) and
+// radius^2 given exactly as r2h + r2l, with a relative error of a
+// few units in the last place however close |x - c| is to r: each difference
+// is split exactly into t + e (TwoSum), each square into p + pe
+// (TwoProduct), the squared distance is carried as a double-double, and the
+// cancelling subtraction r^2 - |x - c|^2 is done on the double-double pair.
+__device__ inline double one_minus_ratio(const double* x, const double* c, int dim, double r2h, double r2l) {
+  double hi = 0.0, lo = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    double t, e, p, pe, s, se;
+    two_sum(x[k], -c[k], t, e);
+    two_prod(t, t, p, pe);
+    two_sum(hi, p, s, se);
+    hi = s;
+    lo += se + pe + 2.0 * t * e;
+  }
+  double nh, nl;
+  two_sum(r2h, -hi, nh, nl);
+  nl += r2l - lo;
+  return (nh + nl) / r2h * (1.0 - r2l / r2h);
+}
+
+// Sum of products a[m] b[m] over the set bits m of `bits`, compensated
+// (TwoProduct + TwoSum, Ogita-Rump-Oishi Dot2): as accurate as if computed in
+// twice the precision and rounded, so a sum that cancels keeps its digits.
+__device__ inline double dot2_bits(const double* a, const double* b, uint32_t bits) {
+  double s = 0.0, c = 0.0;
+  while (bits) {
+    const int m = __ffs(bits) - 1;
+    bits &= bits - 1u;
+    double p, pe, t, te;
+    two_prod(a[m], b[m], p, pe);
+    two_sum(s, p, t, te);
+    s = t;
+    c += te + pe;
+  }
+  return s + c;
+}
+
 template <typename T> struct Real;
 template <> struct Real<float> {
   __device__ static float kstat(float r2, float s2) { return kstat_unit_f(r2, s2); }
@@ -365,6 +441,62 @@ struct Dot2 {
   }
   __device__ inline double value() const { return (double)s + (double)c; }
 };
+
+// Sum partials part[b * stride + t] over blocks b < nblk for t < width with all
+// threads of the block, in a fixed order; result in out[t] (shared).  Each
+// thread keeps 16 predicated L2 loads in flight per round (no dependent tail).
+__device__ inline void block_sum_partials(const double* part, int nblk, int width, int stride, double* out,
+                                   double* scratch /* >= blockDim.x doubles */) {
+  const int groups = blockDim.x / width;  // width <= 2 kMaxCols < blockDim.x
+  const int t = threadIdx.x % width, grp = threadIdx.x / width;
+  double a[4] = {0, 0, 0, 0};
+  if (grp < groups) {
+    for (int b0 = grp; b0 < nblk; b0 += 16 * groups) {
+      double v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int b = b0 + u * groups;
+        v[u] = b < nblk ? __ldcg(part + (int64_t)b * stride + t) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) a[u & 3] += v[u];
+    }
+  }
+  scratch[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
+  __syncthreads();
+  if (threadIdx.x < width) {
+    double s = 0.0;
+    for (int g2 = 0; g2 < groups; ++g2) s += scratch[g2 * width + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// alpha_c = rho_c / p_c^T q_c of iteration it for the columns still running
+// (Saad, Alg. 6.18; rho = r^T M^-1 r, = |r|^2 without a preconditioner), with
+// pq = p^T q per column already summed; threads c < kp of the calling block
+// each finish one column.  A non-positive or non-finite p^T q is a breakdown.
+__device__ inline void cg_alpha_finish(gp::CgState* st, int it, const double* pq, int k, int kp,
+                                       double* hist_alpha, int m_hist) {
+  if (threadIdx.x < kp) {
+    const int c = threadIdx.x;
+    double a = 0.0;
+    if (c < k && !st->donep[it & 1][c]) {
+      const double d = pq[c];
+      if (!(d > 0.0) || !isfinite(d)) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = c;
+      } else {
+        a = st->rrp[it & 1][c] / d;
+        if (it < m_hist) {
+          hist_alpha[it * gp::kMaxCols + c] = a;
+          st->steps[c] = it + 1;
+        }
+      }
+    }
+    st->alpha[c] = a;
+  }
+}
 
 __device__ inline unsigned lanemask_lt() {
   unsigned m;

@@ -200,7 +200,8 @@ int taylor_logdet(gp_ctx* c, int nv, int kp, int m) {
   GP_LAUNCH_CHECK();
   c->launches += 3;
   SpmmPlan plan;
-  GP_CHECK(spmm_select(c, kp, c->flags, st, &plan));
+  // k = 0: a form that also finishes a CG step leaves every column's state alone
+  GP_CHECK(spmm_select(c, kp, c->flags, st, &plan, 0, 0));
   for (int k = 1; k <= m; ++k) {
     spmm_launch(plan, c->stream, c, st);  // Q = Khat V_{k-1}
     k_taylor_update<<<nb_u, kUpdThreads, 0, c->stream>>>(n, kq, nv, (const float4*)c->Q.p, (float4*)c->P.p,

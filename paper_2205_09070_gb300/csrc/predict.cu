@@ -8,8 +8,9 @@
 // 3^dim cells around its own cell in the assembled cell list (edge >= r_s,
 // Morton-sorted active points).  A test point is not an observation: no noise
 // term.  Everything here is FP64: the support tests use the same operation
-// order as the assembly's FP64 test, f_m(x*) follows Eq. eq:bump bump by bump,
-// and the training side uses the FP64 bump table of the assembly.
+// order as the assembly's FP64 test; values take 1 - rho^2 and each bump's
+// 1 - |x - c|^2 / r^2 without cancellation and sum f_m and sum_m f_m f_m
+// compensated; the training side uses the FP64 bump table of the assembly.
 #include "gp_internal.cuh"
 
 namespace {
@@ -31,14 +32,14 @@ __global__ void __launch_bounds__(kThreads) k_predict(const double* __restrict__
                                                       const uint32_t* __restrict__ perm,
                                                       const double* __restrict__ F0,
                                                       const double* __restrict__ alpha, double AC, double rs2,
-                                                      double* __restrict__ mean) {
+                                                      double rs2l, double* __restrict__ mean) {
   __shared__ double sF[kWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int dim = g.dim;
   for (int64_t q = (int64_t)blockIdx.x * kWarps + w; q < ns; q += (int64_t)gridDim.x * kWarps) {
     double xq[gp::kMaxDim] = {0.0, 0.0, 0.0};
     for (int k = 0; k < dim; ++k) xq[k] = xstar[q * dim + k];
-    double f = 0.0;
+    double f = 0.0, fc = 0.0;
     bool in_m = false;
     if (lane < n1) {
       for (int j = 0; j < n2; ++j) {
@@ -50,11 +51,19 @@ __global__ void __launch_bounds__(kThreads) k_predict(const double* __restrict__
         }
         const double qq = __ddiv_rn(d2, bp.r2);
         if (qq < 1.0) {
-          f += bp.a * exp(beta - beta / (1.0 - qq));
+          // value from u = 1 - q without cancellation, summed compensated
+          const double u = gpd::one_minus_ratio(xq, bp.c, dim, bp.r2, bp.r2l);
+          if (u > 0.0) {
+            double t, e;
+            gpd::two_sum(f, bp.a * exp(beta - beta / u), t, e);
+            f = t;
+            fc += e;
+          }
           in_m = true;
         }
       }
     }
+    f += fc;
     const uint32_t mq = __ballot_sync(kFull, in_m);  // bit m: x*_q inside some bump of f_m
     sF[w][lane] = f;
     __syncwarp();
@@ -87,13 +96,10 @@ __global__ void __launch_bounds__(kThreads) k_predict(const double* __restrict__
           }
           if (!(d2 < rs2)) continue;
           const uint32_t i = perm[j];
-          double S = 0.0;
-          while (common) {
-            const int m = __ffs(common) - 1;
-            common &= common - 1u;
-            S += sF[w][m] * F0[(int64_t)i * n1 + m];
-          }
-          const double kst = gpd::kstat_unit_d(d2 / rs2, (rs2 - d2) / rs2);
+          const double S = gpd::dot2_bits(sF[w], F0 + (int64_t)i * n1, common);
+          double s2 = (rs2 - d2) / rs2;
+          if (s2 < 1e-2) s2 = gpd::one_minus_ratio(xq, xs + (int64_t)j * dim, dim, rs2, rs2l);
+          const double kst = s2 > 0.0 ? gpd::kstat_unit_d(d2 / rs2, s2) : 0.0;
           acc += AC * kst * S * alpha[i];
         }
       }
@@ -115,12 +121,14 @@ int predict_mean(gp_ctx* c, const double* xstar, int64_t ns, const double* alpha
     GP_CUDA(cudaMemsetAsync(mean, 0, (size_t)ns * sizeof(double), c->stream));
     return GP_OK;
   }
+  double rs2, rs2l;
+  gpd::two_prod(c->r_s, c->r_s, rs2, rs2l);
   int64_t blocks = (ns + kWarps - 1) / kWarps;
   if (blocks > (int64_t)c->num_sms * 16) blocks = (int64_t)c->num_sms * 16;
   k_predict<<<(unsigned)blocks, kThreads, 0, c->stream>>>(
       xstar, ns, (const gp::BumpParam*)c->bump.p, c->n1, c->n2, c->beta, c->grid, (const int2*)c->cells.p,
       (const double*)c->xs.p, (const uint32_t*)c->smask.p, (const uint32_t*)c->vals.p, (const double*)c->F0.p,
-      alpha, c->A * kStatPrefactor, c->r_s * c->r_s, mean);
+      alpha, c->A * kStatPrefactor, rs2, rs2l, mean);
   GP_LAUNCH_CHECK();
   c->launches += 1;
   return GP_OK;

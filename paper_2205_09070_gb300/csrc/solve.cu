@@ -28,35 +28,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Sum partials part[b * stride + t] over blocks b < nblk for t < width with all
-// threads of the block, in a fixed order; result in out[t] (shared).  Each
-// thread keeps 16 predicated L2 loads in flight per round (no dependent tail).
-__device__ void block_sum_partials(const double* part, int nblk, int width, int stride, double* out,
-                                   double* scratch /* >= blockDim.x doubles */) {
-  const int groups = blockDim.x / width;  // width <= 2 kMaxCols < blockDim.x
-  const int t = threadIdx.x % width, grp = threadIdx.x / width;
-  double a[4] = {0, 0, 0, 0};
-  if (grp < groups) {
-    for (int b0 = grp; b0 < nblk; b0 += 16 * groups) {
-      double v[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int b = b0 + u * groups;
-        v[u] = b < nblk ? __ldcg(part + (int64_t)b * stride + t) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) a[u & 3] += v[u];
-    }
-  }
-  scratch[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
-  __syncthreads();
-  if (threadIdx.x < width) {
-    double s = 0.0;
-    for (int g2 = 0; g2 < groups; ++g2) s += scratch[g2 * width + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
+using gpd::block_sum_partials;
 
 __device__ inline bool last_block(unsigned* ticket) {
   __shared__ bool is_last;
@@ -122,12 +94,17 @@ __device__ void finish_beta(gp::CgState* st, const double* rr_new, int k, int co
 }
 
 // ---------------------------------------------------------------- FP32 batched
-// Initial block: R = P = [yhat, z_1..z_nv, 0 pad], X = 0, probe sign bits.
+// Initial block B = [yhat, z_1..z_nv, 0 pad] and probe sign bits.
+// Cold start (KX == nullptr): X = 0, R = P = B.  Warm start: X is kept and
+// KX = Khat X was just computed, so R = P = B - Khat X (the true residual of
+// the kept iterate).  Either way |r_0|^2 of the convergence test is |B|^2 per
+// column, so |r| <= rtol |r_0| means the same at any starting point.
 __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp, const double* __restrict__ y,
                                                        const uint32_t* __restrict__ perm,
                                                        const double* __restrict__ dinv64, uint64_t seed, int nv,
                                                        float* __restrict__ X, float* __restrict__ R,
-                                                       float* __restrict__ P, uint32_t* __restrict__ zbits,
+                                                       float* __restrict__ P, const float* __restrict__ KX,
+                                                       uint32_t* __restrict__ zbits,
                                                        double* __restrict__ part, gp::CgState* st, double tol2,
                                                        int max_iter) {
   double acc = 0.0;
@@ -139,16 +116,19 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
     float* xrow = X + p * kp;
     float* rrow = R + p * kp;
     float* prow = P + p * kp;
-    xrow[0] = 0.f;
-    rrow[0] = yh;
-    prow[0] = yh;
+    const float* kxrow = KX ? KX + p * kp : nullptr;
+    const float r0 = KX ? yh - kxrow[0] : yh;
+    if (!KX) xrow[0] = 0.f;
+    rrow[0] = r0;
+    prow[0] = r0;
     for (int l = 0; l < nv; ++l) {
       const unsigned b = gpd::probe_bit(seed, l, (long long)i);
       zb[l >> 5] |= b << (l & 31);
       const float z = b ? -1.f : 1.f;
-      xrow[1 + l] = 0.f;
-      rrow[1 + l] = z;
-      prow[1 + l] = z;
+      const float rl = KX ? z - kxrow[1 + l] : z;
+      if (!KX) xrow[1 + l] = 0.f;
+      rrow[1 + l] = rl;
+      prow[1 + l] = rl;
     }
     for (int c = 1 + nv; c < kp; ++c) {
       xrow[c] = 0.f;
@@ -216,24 +196,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restri
   __shared__ double scratch[kRedThreads];
   __shared__ double pq[gp::kMaxCols];
   block_sum_partials(part_pq, npq, kp, kp, pq, scratch);
-  if (threadIdx.x < kp) {
-    const int c = threadIdx.x;
-    double a = 0.0;
-    if (c < k && !st->donep[it & 1][c]) {
-      const double d = pq[c];
-      if (!(d > 0.0) || !isfinite(d)) {
-        st->status = GP_ERR_NOT_SPD;
-        st->bad_col = c;
-      } else {
-        a = st->rrp[it & 1][c] / d;
-        if (it < m_hist) {
-          hist_alpha[it * gp::kMaxCols + c] = a;
-          st->steps[c] = it + 1;
-        }
-      }
-    }
-    st->alpha[c] = a;
-  }
+  gpd::cg_alpha_finish(st, it, pq, k, kp, hist_alpha, m_hist);
 }
 
 // B: R -= alpha Q with per-block partial sums of |r_c|^2.  A thread owns one
@@ -661,8 +624,8 @@ UpdPcFn upd_pc_fn(int B) {
   }
 }
 
-// Preconditioned start: rho_0 = r^T M^-1 r drives alpha / beta, |r_0|^2 the
-// convergence test (|r| <= rtol |r_0| on the true residual).
+// Preconditioned start: rho_0 = r^T M^-1 r drives alpha / beta; a column whose
+// starting residual already meets |r| <= rtol |B| is done.
 __global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restrict__ part, int np, int k, int kp,
                                                           gp::CgState* st) {
   __shared__ double scratch[kRedThreads];
@@ -675,12 +638,12 @@ __global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restri
     const int c = threadIdx.x;
     const double p0 = c < k ? sums[c] : 0.0;
     const double r0 = c < k ? sums[kp + c] : 0.0;
-    st->rr0[c] = r0;
+    // rr0 stays |B|^2 from the init (the right-hand side, whatever the start)
     st->crr[0][c] = r0;
     st->crr[1][c] = r0;
     st->rrp[0][c] = p0;
     st->rrp[1][c] = p0;
-    const bool done = !(r0 > 0.0) || !(p0 > 0.0);
+    const bool done = !(r0 > 0.0) || !(p0 > 0.0) || r0 <= st->tol2 * st->rr0[c];
     st->donep[0][c] = done;
     st->donep[1][c] = done;
     if (c < k && !done) atomicOr(&any_running, 1);
@@ -1150,7 +1113,7 @@ int read_state(gp_ctx* c, gp::CgState* host) {
 namespace gp {
 
 int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
-           int check_every, int* iters_out, double* max_rel, bool use_pc) {
+           int check_every, int* iters_out, double* max_rel, bool use_pc, bool warm) {
   const int64_t n = c->n_act;
   *iters_out = 0;
   *max_rel = 0.0;
@@ -1167,12 +1130,27 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   GP_CHECK(ensure(c, c->hist_alpha, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
   GP_CHECK(ensure(c, c->hist_beta, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
   CgState* st = (CgState*)c->cg.p;
+  // the warm start keeps rr0 = |B|^2 and relies on the preconditioned start
+  // to set rho_0 from the new residual
+  if (warm && !(use_pc && c->pc_block > 0)) return GP_ERR_INVALID_ARG;
+  if (warm) {
+    // continue from the iterate X of the previous run on the same block:
+    // Q = Khat X (the product runs while the state says iteration 0 of an
+    // unfinished run), then the init forms R = B - Q
+    GP_CUDA(cudaMemsetAsync(&st->iter, 0, sizeof(st->iter), c->stream));
+    GP_CUDA(cudaMemsetAsync(&st->fin[0], 0, sizeof(st->fin), c->stream));
+    SpmmPlan wp;
+    GP_CHECK(spmm_plan(c, kp, GP_SPMM_CPASYNC, &wp));
+    spmm_launch_io(wp, c->stream, c, st, (const float*)c->X.p, (float*)c->Q.p);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+  }
   {
     unsigned gb = grid_for(n, kThreads, maxb);
     k_init_f32<<<gb, kThreads, 0, c->stream>>>(n, k, kp, y, (const uint32_t*)c->vals.p, (const double*)c->dinv64.p,
                                                seed, nv, (float*)c->X.p, (float*)c->R.p, (float*)c->P.p,
-                                               (uint32_t*)c->zbits.p, (double*)c->part_a.p, st, rtol * rtol,
-                                               max_iter);
+                                               warm ? (const float*)c->Q.p : nullptr, (uint32_t*)c->zbits.p,
+                                               (double*)c->part_a.p, st, rtol * rtol, max_iter);
     GP_LAUNCH_CHECK();
     c->launches += 1;
   }
@@ -1207,7 +1185,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   const int64_t nblk = c->nblk;
   // the SpMM form: forced by the flags, else the autotuner's for this shape
   SpmmPlan plan;
-  GP_CHECK(spmm_select(c, kp, c->flags, st, &plan));
+  GP_CHECK(spmm_select(c, kp, c->flags, st, &plan, k, m_hist));
   c->spmm_variant = plan.variant;
   const unsigned g_spmm = plan.grid;
   const int ny = kUpdThreads / kq;
@@ -1227,8 +1205,9 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     if (ev0) cudaEventRecordWithFlags(ev0, sm, evf);
     spmm_launch(plan, sm, c, st);
     if (ev1) cudaEventRecordWithFlags(ev1, sm, evf);
-    k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
-                                          (double*)c->hist_alpha.p, m_hist);
+    if (!plan.fused_alpha)
+      k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
+                                            (double*)c->hist_alpha.p, m_hist);
     if (pc) {
       upd_pc<<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, (const float4*)c->Q.p,
                                                               (float4*)c->R.p, (float4*)c->Z.p,
@@ -1248,7 +1227,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   // (with GP_FLAG_TIME_KERNELS the graph also records the SpMM events)
   cudaGraphExec_t exec = nullptr;
   {
-    const uint64_t key[32] = {(uint64_t)n, (uint64_t)nblk, (uint64_t)k, (uint64_t)kp, (uint64_t)pc,
+    const uint64_t key[48] = {(uint64_t)n, (uint64_t)nblk, (uint64_t)k, (uint64_t)kp, (uint64_t)pc,
                               (uint64_t)c->pc_block, (uint64_t)g_spmm, (uint64_t)g_pc, (uint64_t)g_upd,
                               (uint64_t)g_upd_r, (uint64_t)m_hist, (uint64_t)check_every, (uint64_t)plan.smem,
                               (uint64_t)pc_smem, (uint64_t)(uintptr_t)plan.fn, (uint64_t)(uintptr_t)c->brp.p,
@@ -1258,7 +1237,11 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
                               (uint64_t)(uintptr_t)c->part_a.p, (uint64_t)(uintptr_t)c->part_b.p,
                               (uint64_t)(uintptr_t)c->hist_alpha.p, (uint64_t)(uintptr_t)c->hist_beta.p,
                               (uint64_t)(uintptr_t)st, (uint64_t)(uintptr_t)c->pc_Minv.p, (uint64_t)timed,
-                              (uint64_t)(uintptr_t)(timed ? c->kev[0] : nullptr), 0};
+                              (uint64_t)(uintptr_t)(timed ? c->kev[0] : nullptr), (uint64_t)plan.variant,
+                              (uint64_t)plan.stages, (uint64_t)plan.grid, (uint64_t)c->w_ntiles,
+                              (uint64_t)c->w_nrun, (uint64_t)(uintptr_t)c->w_tseg.p,
+                              (uint64_t)(uintptr_t)c->w_segd.p, (uint64_t)(uintptr_t)c->w_runs.p,
+                              (uint64_t)(uintptr_t)c->w_rec.p, 0};
     gp_ctx::CgGraph& gr = c->cg_graph[pc ? 1 : 0];
     if (gr.exec && memcmp(gr.key, key, sizeof(key)) != 0) {
       GP_CUDA(cudaGraphExecDestroy(gr.exec));
@@ -1290,7 +1273,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
       for (int t = 0; t < check_every; ++t) launch_iteration(c->stream, c->kev[2 * t], c->kev[2 * t + 1]);
       GP_LAUNCH_CHECK();
     }
-    c->launches += 5 * check_every;
+    c->launches += (plan.fused_alpha ? 4 : 5) * check_every;
     GP_CHECK(read_state(c, &hs));
     if (timed) {
       // launches after convergence return at once: time only the ones that worked

@@ -26,6 +26,7 @@
 #include <tuple>
 
 #include "gp_internal.cuh"
+#include "async.cuh"
 
 namespace {
 
@@ -227,62 +228,6 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
 
 
 // ---------------------------------------------------------------- TMA form
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-// orders this thread's generic-proxy accesses to shared memory before later
-// async-proxy (TMA) accesses
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// one arrival that also announces `bytes` of copies completing on the barrier
-__device__ __forceinline__ void mbar_arrive_expect(uint64_t* b, unsigned bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(b)),
-      "r"(bytes)
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for phase `parity` of the barrier to complete, for about two seconds
-// of SM clock at most; false if it gave up.
-constexpr long long kWaitCycles = 4000000000ll;
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-  if (mbar_test(b, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test(b, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
-  return true;
-}
-// Rows r0..r3 of the 2-D tensor `map` (box: one row of every column) into
-// four consecutive rows at dst (128-byte aligned).
-__device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, int r0, int r1, int r2, int r3,
-                                            uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
-      "l"(map), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(b))
-      : "memory");
-}
-// `bytes` (a multiple of 16) from 16-byte aligned global src to shared dst.
-__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, uint64_t* b) {
-  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(b))
-               : "memory");
-}
-
 // Stage layout of one buffer: the chunk's P rows in groups of four (one
 // gather4 each, padded to 128 bytes), then its 32 blocks' values.
 constexpr int tma_group_bytes(int kq) { return (64 * kq + 127) / 128 * 128; }
@@ -832,6 +777,7 @@ bool spmm_available(int variant, int kp) {
 }
 
 int spmm_plan(gp_ctx* c, int kp, int variant, SpmmPlan* p) {
+  if (variant == GP_SPMM_WINDOW) return window_plan(c, kp, p);
   if (!spmm_available(variant, kp)) return GP_ERR_UNSUPPORTED;
   const int kq = kp / 4;
   p->variant = variant;
@@ -856,6 +802,10 @@ int spmm_plan(gp_ctx* c, int kp, int variant, SpmmPlan* p) {
 }
 
 void spmm_launch(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st) {
+  if (p.variant == GP_SPMM_WINDOW) {
+    window_launch(p, s, c, st, p.k, p.m_hist);
+    return;
+  }
   int64_t n = c->n_act, nblk = c->nblk;
   const int64_t* brp = (const int64_t*)c->brp.p;
   const int32_t* bcol = (const int32_t*)c->bcol.p;
@@ -872,23 +822,45 @@ void spmm_launch(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st) {
   }
 }
 
-int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan) {
+void spmm_launch_io(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st, const float* in, float* out) {
+  int64_t n = c->n_act, nblk = c->nblk;
+  const int64_t* brp = (const int64_t*)c->brp.p;
+  const int32_t* bcol = (const int32_t*)c->bcol.p;
+  const float4* bval = (const float4*)c->bval.p;
+  const float4* P = (const float4*)in;
+  float4* Q = (float4*)out;
+  double* part = (double*)c->part_a.p;
+  void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st};
+  cudaLaunchKernel(p.fn, dim3(p.grid), dim3(kSpmmThreads), args, p.smem, s);
+}
+
+int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan, int k, int m_hist) {
   const int forced = (flags & GP_FLAG_SPMM_CPASYNC)        ? GP_SPMM_CPASYNC
                      : (flags & GP_FLAG_SPMM_TMA)          ? GP_SPMM_TMA
                      : (flags & GP_FLAG_SPMM_TMA_WIDE)     ? GP_SPMM_TMA_WIDE
                      : (flags & GP_FLAG_SPMM_CPASYNC_WIDE) ? GP_SPMM_CPASYNC_WIDE
+                     : (flags & GP_FLAG_SPMM_WINDOW)       ? GP_SPMM_WINDOW
                                                            : -1;
+  plan->k = k;
+  plan->m_hist = m_hist;
   if (forced >= 0) {
-    // a wide form that would hold one float4 per lane is its narrow form
+    // a wide form that would hold one float4 per lane is its narrow form; the
+    // window form needs the regrouped matrix
     int v = forced;
-    if (!spmm_available(v, kp)) v = v == GP_SPMM_TMA_WIDE ? GP_SPMM_TMA : v == GP_SPMM_CPASYNC_WIDE ? GP_SPMM_CPASYNC : v;
+    if (v == GP_SPMM_WINDOW && !window_available(c, kp)) v = GP_SPMM_CPASYNC_WIDE;
+    if (v != GP_SPMM_WINDOW && !spmm_available(v, kp))
+      v = v == GP_SPMM_TMA_WIDE ? GP_SPMM_TMA : v == GP_SPMM_CPASYNC_WIDE ? GP_SPMM_CPASYNC : v;
     return spmm_plan(c, kp, v, plan);
   }
   const TuneKey key{c->device, kp, c->n_act, c->nblk, c->nbent};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto f = g_tuned.find(key);
-    if (f != g_tuned.end()) return spmm_plan(c, kp, f->second, plan);
+    if (f != g_tuned.end()) {
+      int v = f->second;
+      if (v == GP_SPMM_WINDOW && !window_available(c, kp)) v = GP_SPMM_CPASYNC_WIDE;
+      return spmm_plan(c, kp, v, plan);
+    }
   }
   // time every available form on this matrix: one warm-up launch, then
   // three timed ones (the state is that of iteration 0, so the launches
@@ -899,9 +871,11 @@ int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan) {
   int best = GP_SPMM_CPASYNC;
   float best_ms = 0.f;
   int status = GP_OK;
-  for (int v = GP_SPMM_CPASYNC; v <= GP_SPMM_CPASYNC_WIDE && status == GP_OK; ++v) {
-    if (!spmm_available(v, kp)) continue;
+  for (int v = GP_SPMM_CPASYNC; v <= GP_SPMM_WINDOW && status == GP_OK; ++v) {
+    if (v == GP_SPMM_WINDOW ? !window_available(c, kp) : !spmm_available(v, kp)) continue;
     SpmmPlan p;
+    p.k = k;
+    p.m_hist = m_hist;
     status = spmm_plan(c, kp, v, &p);
     if (status != GP_OK) break;
     spmm_launch(p, c->stream, c, st);
@@ -932,5 +906,6 @@ int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan) {
   }
   return spmm_plan(c, kp, best, plan);
 }
+
 
 }  // namespace gp

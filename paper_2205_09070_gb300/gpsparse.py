@@ -38,13 +38,15 @@ GP_FLAG_SPMM_TMA = 4
 GP_FLAG_SPMM_TMA_WIDE = 8
 GP_FLAG_LOGDET_TAYLOR = 16
 GP_FLAG_SPMM_CPASYNC_WIDE = 32
+GP_FLAG_SPMM_WINDOW = 64
 
 GP_SPMM_CPASYNC = 0
 GP_SPMM_TMA = 1
 GP_SPMM_TMA_WIDE = 2
 GP_SPMM_CPASYNC_WIDE = 3
+GP_SPMM_WINDOW = 4
 SPMM_FLAGS = {"cpasync": GP_FLAG_SPMM_CPASYNC, "tma": GP_FLAG_SPMM_TMA, "tma_wide": GP_FLAG_SPMM_TMA_WIDE,
-              "cpasync_wide": GP_FLAG_SPMM_CPASYNC_WIDE}
+              "cpasync_wide": GP_FLAG_SPMM_CPASYNC_WIDE, "window": GP_FLAG_SPMM_WINDOW}
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
             "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_predict", "gp_lml", "gp_lml_grad",

@@ -1,6 +1,6 @@
 """CPU checks of bench.py's bookkeeping: every SpMM form maps to a kernel
-name whose source region exists in spmm.cu, and the committed DRAM-traffic
-records are keyed to the current source of their kernels."""
+name whose source region exists in its source file, and the committed
+DRAM-traffic records are keyed to the current source of their kernels."""
 
 import json
 import os
@@ -9,11 +9,12 @@ import bench
 
 
 def test_spmm_kernel_names_and_source_regions():
-    names = {v: bench.spmm_kernel_name(v, 36) for v in range(4)}
-    assert names == {0: "k_bspmm_f32<9>", 1: "k_bspmm_tma<9,1>", 2: "k_bspmm_tma<9,3>", 3: "k_bspmm_f32w<9,3>"}
-    src = open(bench.SPMM_SOURCE).read()
+    names = {v: bench.spmm_kernel_name(v, 36) for v in range(5)}
+    assert names == {0: "k_bspmm_f32<9>", 1: "k_bspmm_tma<9,1>", 2: "k_bspmm_tma<9,3>", 3: "k_bspmm_f32w<9,3>",
+                     4: "k_wspmm<9,3>"}
     for name in names.values():
-        a, b = bench.SPMM_REGIONS[name.split("<")[0]]
+        path, a, b = bench.SPMM_REGIONS[name.split("<")[0]]
+        src = open(path).read()
         assert src.index(a) < src.index(b)
         assert len(bench.spmm_source_sha(name)) == 64
 

@@ -17,7 +17,7 @@ from helpers import grad_ok
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FORMS = ["cpasync", "tma", "tma_wide", "cpasync_wide"]
+FORMS = ["cpasync", "tma", "tma_wide", "cpasync_wide", "window"]
 
 
 @pytest.fixture(scope="module")
@@ -35,6 +35,8 @@ def wide_lw(kq):
 
 
 def expected_variant(G, form, kp):
+    if form == "window":
+        return G.GP_SPMM_WINDOW
     wide = wide_lw(kp // 4) > 1
     if form == "cpasync" or (form == "cpasync_wide" and not wide):
         return G.GP_SPMM_CPASYNC
@@ -158,7 +160,7 @@ def test_autotuner_choice_is_stable_and_shared(lib):
     b = lib.GP(p.dim, p.n1, p.n2, p.beta)
     l3, g3, i3 = b.lml_grad(x, y, p.h, o)
     assert i1["spmm_variant"] in (lib.GP_SPMM_CPASYNC, lib.GP_SPMM_TMA, lib.GP_SPMM_TMA_WIDE,
-                                  lib.GP_SPMM_CPASYNC_WIDE)
+                                  lib.GP_SPMM_CPASYNC_WIDE, lib.GP_SPMM_WINDOW)
     assert i1["spmm_variant"] == i2["spmm_variant"] == i3["spmm_variant"]
     assert l1 == l2 == l3
     assert np.array_equal(g1, g2) and np.array_equal(g1, g3)
