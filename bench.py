@@ -55,9 +55,10 @@ def args_parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1200)
+    ap.add_argument("--n5m", type=int, default=1, help="add the 5M-point leg to the 1M line (0: skip)")
     ap.add_argument("--precond-block", type=int, default=None,
                     help="block-Jacobi block size of the preconditioned CG (default: the library's)")
-    ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide", "cpasync_wide"],
+    ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide", "cpasync_wide", "window"],
                     help="SpMM form: the library's autotuner (auto) or a forced form; profiling runs force "
                          "the form the plain run chose, since the tuner's timings are meaningless under ncu")
     return ap.parse_args()
@@ -129,7 +130,7 @@ def peaks() -> dict:
 
 SPMM_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "spmm.cu")
 SPMM_KERNELS = {0: "k_bspmm_f32<{kq}>", 1: "k_bspmm_tma<{kq},1>", 2: "k_bspmm_tma<{kq},{lw}>",
-                3: "k_bspmm_f32w<{kq},{lw}>"}
+                3: "k_bspmm_f32w<{kq},{lw}>", 4: "k_wspmm<{kq},{lw}>"}
 
 
 def spmm_kernel_name(variant: int, kp: int) -> str:
@@ -138,20 +139,23 @@ def spmm_kernel_name(variant: int, kp: int) -> str:
     return SPMM_KERNELS.get(variant, "k_bspmm_?<{kq}>").format(kq=kq, lw=lw)
 
 
-SPMM_REGIONS = {  # source region of each SpMM form in spmm.cu (first marker inclusive, second exclusive)
-    "k_bspmm_f32": ("// A: Q = Khat P on the 8x1 block CSR.",
+WINDOW_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "window.cu")
+SPMM_REGIONS = {  # source file and region of each SpMM form (first marker inclusive, second exclusive)
+    "k_bspmm_f32": (SPMM_SOURCE, "// A: Q = Khat P on the 8x1 block CSR.",
                     "// ---------------------------------------------------------------- TMA form"),
-    "k_bspmm_tma": ("// ---------------------------------------------------------------- TMA form",
+    "k_bspmm_tma": (SPMM_SOURCE, "// ---------------------------------------------------------------- TMA form",
                     "// ---------------------------------------------------------------- wide cp.async form"),
-    "k_bspmm_f32w": ("// ---------------------------------------------------------------- wide cp.async form",
+    "k_bspmm_f32w": (SPMM_SOURCE, "// ---------------------------------------------------------------- wide cp.async form",
                      "// ---------------------------------------------------------------- host side"),
+    "k_wspmm": (WINDOW_SOURCE, "// ------------------------------------------------------------------ SpMM",
+                "typedef void (*WinFn)"),
 }
 
 
 def spmm_source_sha(kernel: str) -> str:
     """sha256 of the source region of the SpMM form `kernel` (its kernel and helpers)."""
-    src = open(SPMM_SOURCE).read()
-    a, b = SPMM_REGIONS[kernel.split("<")[0]]
+    path, a, b = SPMM_REGIONS[kernel.split("<")[0]]
+    src = open(path).read()
     return hashlib.sha256(src[src.index(a):src.index(b)].encode()).hexdigest()
 
 
@@ -217,6 +221,66 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def fp64_leg(gp, x, y, p, steps, lml, grad, ms_fp32, stream):
+    """The plain FP64 single-RHS path on the same assembled workload: its
+    evaluations/s, assembly nnz/s, and its distance to the FP32-mixed result
+    against the SLQ standard error of the log-determinant."""
+    import torch
+    from paper_2205_09070_gb300 import default_opts
+    o64 = default_opts(precision="fp64", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022, max_iter=20000)
+    gp.lml_grad(x, y, p.h, o64)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(steps):
+        lml64, grad64, info64 = gp.lml_grad(x, y, p.h, o64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1) / steps
+    return {"value": 1e3 / ms64, "unit": UNIT, "ms_per_eval": ms64, "lml": lml64,
+            "iters": info64["iters"], "lml_minus_fp32": lml - lml64,
+            "lml_stderr_fp64": 0.5 * info64["logdet_stderr"],
+            "grad_rel_diff_max": float(np.max(np.abs(grad - grad64)) / np.max(np.abs(grad64))),
+            "assembly": {"nnz_per_s": info64["nnz"] / (info64["t_assemble_ms"] * 1e-3),
+                         "ms": info64["t_assemble_ms"]},
+            "speedup_fp32_mixed": ms64 / ms_fp32}
+
+
+def leg_5m(GP, default_opts, spmm_flag, pc_kw, dev, local, stream, a):
+    """N = 5,000,000 mixture (the literal configuration: r_s = 0.005, 8 x 16
+    bumps, 32 probes, 50 Lanczos steps, rtol 1e-6): FP32-mixed evaluations/s
+    over 2 timed steps after 1 warm-up, assembly nnz/s, and one evaluation of
+    the plain FP64 path on the same points."""
+    import torch
+    from paper_2205_09070_gb300 import workloads as W
+    p = W.mixture_3d(seed=5, n=5_000_000)
+    x = torch.as_tensor(p.x, device=dev)
+    y = torch.as_tensor(p.y, device=dev)
+    gp = GP(p.dim, p.n1, p.n2, p.beta, device=local)
+    o = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
+                     max_iter=20000, flags=spmm_flag, **pc_kw)
+    gp.lml_grad(x, y, p.h, o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 2
+    e0.record(stream)
+    for _ in range(steps):
+        lml, grad, info = gp.lml_grad(x, y, p.h, o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": "mixture_3d", "n": p.n, "n_active": info["n_active"], "nnz": info["nnz"],
+           "value": 1e3 / ms, "unit": UNIT, "ms_per_eval": ms, "steps": steps, "cg_iters": info["iters"],
+           "lml": lml, "lml_stderr": 0.5 * info["logdet_stderr"],
+           "assembly": {"nnz_per_s": info["nnz"] / (info["t_assemble_ms"] * 1e-3), "ms": info["t_assemble_ms"]}}
+    if a.fp64_steps > 0:
+        out["fp64_path"] = fp64_leg(gp, x, y, p, 1, lml, grad, ms, stream)
+    gp.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     a = args_parse()
@@ -248,8 +312,12 @@ def main():
     from paper_2205_09070_gb300.gpsparse import SPMM_FLAGS
     spmm_flag = SPMM_FLAGS.get(a.spmm, 0)
     pc_kw = {} if a.precond_block is None else {"precond_block": a.precond_block}
+    # the timed steps run without per-kernel events; a separate instrumented
+    # pass afterwards gives the per-kernel times the rooflines use
     opts = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
-                        max_iter=20000, flags=GP_FLAG_TIME_KERNELS | spmm_flag, **pc_kw)
+                        max_iter=20000, flags=spmm_flag, **pc_kw)
+    opts_timed = default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
+                              max_iter=20000, flags=GP_FLAG_TIME_KERNELS | spmm_flag, **pc_kw)
 
     for _ in range(a.warmup):
         gp.lml_grad(x, y, p.h, opts)
@@ -277,32 +345,57 @@ def main():
     clocks = clk.summary()
     value = world * a.steps / (ms / 1e3)
 
-    # per-kernel roofline of the SpMM (dominant kernel) from the timed steps
+    launches = sum(i["launches"] for i in infos)
+    t_asm = statistics.mean(i["t_assemble_ms"] for i in infos)
+
+    # instrumented pass (outside the timed region): per-launch CUDA-event times
+    # of the SpMM, the pair fill and the adjoint, recorded on the context stream
+    tinfos = [gp.lml_grad(x, y, p.h, opts_timed)[2] for _ in range(2)]
+    torch.cuda.synchronize()
     nnz = infos[-1]["nnz"]
     n_act = infos[-1]["n_active"]
     kp = infos[-1]["kp"]
-    t_spmm = sum(i["t_spmm_kernel_ms"] for i in infos)
-    n_spmm = sum(i["n_spmm"] for i in infos)
+    t_spmm = sum(i["t_spmm_kernel_ms"] for i in tinfos)
+    n_spmm = sum(i["n_spmm"] for i in tinfos)
     spmm_ms = t_spmm / max(n_spmm, 1)
-    bytes_spmm = 8 * nnz + 8 * n_act * kp + 8 * (n_act + 1)
-    achieved = bytes_spmm / (spmm_ms * 1e-3) / 1e9
+    t_fill = statistics.mean(i["t_fill_kernel_ms"] for i in tinfos)
+    t_adj = statistics.mean(i["t_adjoint_kernel_ms"] for i in tinfos)
     pk = peaks()
+    peak_src = (f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)" if pk["source"] == "measured"
+                else "fallback 6.8 TB/s")
     kname = spmm_kernel_name(infos[-1]["spmm_variant"], kp)
     trec = traffic_record(kname, kp)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": trec["bytes_per_launch"] if trec else None,
-                "kernel": kname, "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
-                if pk["source"] == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": bytes_spmm, "avg_launch_ms": spmm_ms,
-                "launches_timed": n_spmm,
-                "share_of_step": t_spmm / ms,
-                "limiter": ("L1/shared data pipe: gathers of 144-byte P rows staged through shared memory "
-                            "(ncu: l1tex throughput 77 % of peak, DRAM 17 %)")
-                if kname.startswith("k_bspmm_f32") else "TMA gather4 request rate"}
-    t_asm = statistics.mean(i["t_assemble_ms"] for i in infos)
-    t_fill = statistics.mean(i["t_fill_kernel_ms"] for i in infos)
-    t_adj = statistics.mean(i["t_adjoint_kernel_ms"] for i in infos)
-    launches = sum(i["launches"] for i in infos)
+    # algorithmic bytes (each input read once, each output written once):
+    #   SpMM: 8 nnz (FP32 value + int32 column) + 4 kp N_act read (P) + 4 kp N_act
+    #         written (Q) + 8 (N_act + 1) row pointers
+    #   fill: 8 nnz written (column + FP32 value) + per active point its row
+    #         pointer, cell, coordinates (FP32 cell-relative, FP64), mask, FP64
+    #         bump row and D^-1/2 (76 + 8 n1 bytes) + the cell table (8 per cell)
+    #   adjoint: 4 nnz columns (values recomputed) + per active point its row
+    #         pointer, X row (4 kp), probe bits, cell, coordinates, mask, FP32
+    #         bump row and D^-1/2, and the written g row (4 n1)
+    n1 = p.n1
+    bytes_spmm = 8 * nnz + 8 * n_act * kp + 8 * (n_act + 1)
+    bytes_fill = 8 * nnz + n_act * (76 + 8 * n1) + 8 * infos[-1]["n_cells"]
+    bytes_adj = 4 * nnz + n_act * (8 + 4 * kp + 8 + 16 + 16 + 24 + 4 + 4 * n1 + 4 + 4 * n1)
+
+    def roof(kernel, nbytes, t_ms, **extra):
+        ach = nbytes / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+        return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "kernel": kernel, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": t_ms, **extra}
+
+    roofline = roof(kname, bytes_spmm, spmm_ms, traffic=trec["bytes_per_launch"] if trec else None,
+                    launches_timed=n_spmm, share_of_step=(t_spmm / len(tinfos)) / (ms / a.steps),
+                    limiter=("L1/shared data pipe: gathers of 144-byte P rows staged through shared memory "
+                             "(ncu: l1tex throughput 66-77 % of peak, DRAM 17 %)")
+                    if kname.startswith("k_bspmm_f32") else
+                    ("latency: one persistent CTA of 8 consumer warps per SM, warps paced by the slowest "
+                     "block row of each tile") if kname.startswith("k_wspmm") else "TMA gather4 request rate")
+    rooflines = {"fill": roof("k_pair<float,FILL>", bytes_fill, t_fill, traffic=None,
+                              limiter="candidate tests (about 6.4 per stored entry) and FP64 entry values"),
+                 "adjoint": roof("k_adjoint<float>", bytes_adj, t_adj, traffic=None,
+                                 limiter="gathers of the neighbours' X rows and coordinates per stored entry")}
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.as_tensor(p.x).pin_memory()
@@ -324,24 +417,13 @@ def main():
                "d2h_bytes_per_step": int(8 + 8 * gp.n_params), "steps": a.e2e_steps}
 
     # plain FP64 single-RHS path on the same workload (same probes, rtol, steps)
-    fp64 = None
-    if a.fp64_steps > 0:
-        o64 = default_opts(precision="fp64", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022,
-                           max_iter=20000)
-        gp.lml_grad(x, y, p.h, o64)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(a.fp64_steps):
-            lml64, grad64, info64 = gp.lml_grad(x, y, p.h, o64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1) / a.fp64_steps
-        fp64 = {"value": 1e3 / ms64, "unit": UNIT, "ms_per_eval": ms64, "lml": lml64,
-                "iters": info64["iters"], "lml_minus_fp32": lml - lml64,
-                "lml_stderr_fp64": 0.5 * info64["logdet_stderr"],
-                "grad_rel_diff_max": float(np.max(np.abs(grad - grad64)) / np.max(np.abs(grad64))),
-                "speedup_fp32_mixed": (1e3 / (ms / a.steps)) / (1e3 / ms64)}
+    fp64 = fp64_leg(gp, x, y, p, a.fp64_steps, lml, grad, ms / a.steps, stream) if a.fp64_steps > 0 else None
+
+    # the literal 5M-point configuration: FP32-mixed evaluations, assembly and
+    # the plain FP64 path on the same points
+    scale5m = None
+    if a.n5m and p.n == 1_000_000:
+        scale5m = leg_5m(GP, default_opts, spmm_flag, pc_kw, dev, local, stream, a)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -360,13 +442,13 @@ def main():
                            "n_active": n_act, "nnz": nnz, "kp": kp, "cg_iters": infos[-1]["iters"],
                 "lanczos_iters": infos[-1]["lanczos_iters"], "precond_block": infos[-1]["precond_block"],
                 "spmm_form": ["cp.async stage", "TMA gather4 stage", "TMA gather4 stage, wide lanes",
-                              "cp.async stage, wide lanes"][infos[-1]["spmm_variant"]]
+                              "cp.async stage, wide lanes", "column windows, TMA bulk runs"][infos[-1]["spmm_variant"]]
                 if infos[-1]["spmm_variant"] >= 0 else None},
                 "lml": lml, "logdet_stderr": infos[-1]["logdet_stderr"],
                 "assembly": {"nnz_per_s": nnz / (t_asm * 1e-3), "ms": t_asm, "fill_kernel_ms": t_fill},
                 "adjoint_kernel_ms": t_adj,
-                "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-                "fp64_path": fp64, "cpu_baseline": cpu}
+                "roofline": roofline, "rooflines": rooflines, "clocks": clocks, "gpu_launches": launches,
+                "e2e": e2e, "fp64_path": fp64, "scale_5m": scale5m, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     gp.close()
     if dist:
