@@ -41,6 +41,10 @@ Readings where the paper is silent, garbled or inconsistent:
 
 Hyperparameter vector layout, P = n1*n2*(dim+2) + 3 doubles:
   for m < n1, b < n2: [centre_mb[0..dim-1], r_mb, a_mb]; then r_s, A, sigma_n^2.
+  A vector with one more entry carries the length scale l of a squared-
+  exponential core kernel k_c = exp(-|x1 - x2|^2 / (2 l^2)) multiplying k_s
+  (Sec. 2.2: kernels can be multiplied, k_c * k_s, with no restriction on the
+  core; the paper's kernel figure shows a squared-exponential core).
 
 Parity pins (tests/test_oracle_pins.py) tie every function here to something
 other than itself: an independently derived power series and its derivative,
@@ -65,16 +69,18 @@ KSTAT_PREFACTOR = math.sqrt(2.0) / (3.0 * math.sqrt(math.pi))
 # hyperparameters
 # ----------------------------------------------------------------------------
 
-def n_params(dim: int, n1: int, n2: int) -> int:
+def n_params(dim: int, n1: int, n2: int, core: bool = False) -> int:
     """Number of hyperparameters: per bump a centre, a radius and an amplitude
-    (Eq. eq:bump), then the stationary radius r_s, amplitude A and noise."""
-    return n1 * n2 * (dim + 2) + 3
+    (Eq. eq:bump), then the stationary radius r_s, amplitude A and noise, and
+    the core length scale l when there is a core kernel."""
+    return n1 * n2 * (dim + 2) + 3 + (1 if core else 0)
 
 
 def unpack_h(h, dim: int, n1: int, n2: int):
-    """Split the flat hyperparameter vector into its named parts."""
+    """Split the flat hyperparameter vector into its named parts; "ell" is the
+    core kernel's length scale, or None without a core kernel."""
     h = np.asarray(h, dtype=np.float64)
-    if h.shape != (n_params(dim, n1, n2),):
+    if h.shape not in ((n_params(dim, n1, n2),), (n_params(dim, n1, n2, True),)):
         raise ValueError("hyperparameter vector has the wrong length")
     nb = n1 * n2 * (dim + 2)
     b = h[:nb].reshape(n1, n2, dim + 2)
@@ -85,7 +91,14 @@ def unpack_h(h, dim: int, n1: int, n2: int):
         "r_s": float(h[nb]),
         "A": float(h[nb + 1]),
         "sigma2": float(h[nb + 2]),
+        "ell": float(h[nb + 3]) if h.shape[0] == nb + 4 else None,
     }
+
+
+def core_kernel(d2, ell):
+    """k_c at squared distance d2: exp(-d2 / (2 l^2)), or 1 without a core."""
+    d2 = np.asarray(d2, dtype=np.float64)
+    return np.ones_like(d2) if ell is None else np.exp(-d2 / (2.0 * ell * ell))
 
 
 # ----------------------------------------------------------------------------
@@ -214,7 +227,7 @@ def pair_rows(x, h, dim, n1, n2, rows, beta=1.0, table=None):
     S = np.zeros(d2.shape)
     for m in range(n1):                       # sum_m f_m(x_i) f_m(x_j), term by term
         S += F[rows, m][:, None] * F[:, m][None, :]
-    vals = p["A"] * kstat(rho) * S + p["sigma2"] * diag
+    vals = p["A"] * kstat(rho) * core_kernel(d2, p["ell"]) * S + p["sigma2"] * diag
     vals = np.where(pattern, vals, 0.0)
     return pattern, vals
 
@@ -340,8 +353,9 @@ def bump_sums_hp(point, p, dim, n1, n2, beta, bumps):
 
 
 def entries_hp(x, h, dim, n1, n2, rows, cols, beta=1.0, digits=HP_DIGITS):
-    """K_ij = A k~(|x_i - x_j| / r_s) sum_m f_m(x_i) f_m(x_j) + sigma_n^2 [i = j]
-    (Eq. eq:bump_kernel with Eq. eq:kstat and Eq. eq:bump) for the listed pairs
+    """K_ij = A k~(|x_i - x_j| / r_s) k_c(x_i, x_j) sum_m f_m(x_i) f_m(x_j)
+    + sigma_n^2 [i = j] (Eq. eq:bump_kernel with Eq. eq:kstat and Eq. eq:bump;
+    k_c = 1 without a core kernel) for the listed pairs
     (i, j) = (rows[t], cols[t]), evaluated to `digits` significant digits and
     rounded to float64.  The caller lists pairs of the pattern; a pair whose
     exact distance reaches r_s (possible only at a float64 tie) gets k~ = 0."""
@@ -358,6 +372,7 @@ def entries_hp(x, h, dim, n1, n2, rows, cols, beta=1.0, digits=HP_DIGITS):
         A = Decimal(p["A"])
         s2 = Decimal(p["sigma2"])
         rs2 = Decimal(p["r_s"]) ** 2
+        ell = Decimal(p["ell"]) if p["ell"] is not None else None
         fcache, memo = {}, {}
 
         def F(i):
@@ -376,6 +391,8 @@ def entries_hp(x, h, dim, n1, n2, rows, cols, beta=1.0, digits=HP_DIGITS):
                 else:
                     d2 = sum((Decimal(float(x[i, k])) - Decimal(float(x[j, k]))) ** 2 for k in range(dim))
                     v = A * kstat_hp(d2 / rs2, C) * S
+                    if ell is not None:
+                        v *= (-d2 / (2 * ell * ell)).exp()
                 memo[key] = float(v)
             out[t] = memo[key]
     return out
@@ -414,7 +431,10 @@ def cross_K_hp(xs, x, h, dim, n1, n2, beta=1.0, digits=HP_DIGITS):
                 if S == 0:
                     continue
                 dd = sum((Decimal(float(xs[a, k])) - Decimal(float(x[i, k]))) ** 2 for k in range(dim))
-                kappa[a, i] = float(A * kstat_hp(dd / rs2, C) * S)
+                v = A * kstat_hp(dd / rs2, C) * S
+                if p["ell"] is not None:
+                    v *= (-dd / (2 * Decimal(p["ell"]) ** 2)).exp()
+                kappa[a, i] = float(v)
     return kappa
 
 
@@ -435,7 +455,8 @@ def cross_K(xs, x, h, dim, n1, n2, beta=1.0):
     S = np.zeros(d2.shape)
     for m in range(n1):
         S += Fq[:, m][:, None] * F[:, m][None, :]
-    return np.where(d2 < p["r_s"] ** 2, p["A"] * kstat(np.sqrt(d2) / p["r_s"]) * S, 0.0)
+    return np.where(d2 < p["r_s"] ** 2, p["A"] * kstat(np.sqrt(d2) / p["r_s"]) * core_kernel(d2, p["ell"]) * S,
+                    0.0)
 
 
 def predict_mean(x, y, h, xs, dim, n1, n2, beta=1.0):
@@ -464,9 +485,11 @@ def dK_dtheta_all(x, h, dim, n1, n2, beta=1.0):
     x = np.asarray(x, dtype=np.float64)
     n = x.shape[0]
     F, _ = bump_table(x, h, dim, n1, n2, beta)
-    d = np.sqrt(np.sum((x[:, None, :] - x[None, :, :]) ** 2, axis=2))
+    d2 = np.sum((x[:, None, :] - x[None, :, :]) ** 2, axis=2)
+    d = np.sqrt(d2)
     rho = d / p["r_s"]
-    kt = kstat(rho)
+    kc = core_kernel(d2, p["ell"])
+    kt = kstat(rho) * kc          # the core multiplies every term
     A = p["A"]
     idx = 0
     for m in range(n1):
@@ -479,9 +502,11 @@ def dK_dtheta_all(x, h, dim, n1, n2, beta=1.0):
     S = np.zeros((n, n))
     for m in range(n1):
         S += np.outer(F[:, m], F[:, m])
-    yield idx, A * (kstat_drho(rho) * (-rho / p["r_s"])) * S      # r_s
+    yield idx, A * (kstat_drho(rho) * (-rho / p["r_s"])) * kc * S  # r_s
     yield idx + 1, kt * S                                          # A
     yield idx + 2, np.eye(n)                                       # sigma_n^2
+    if p["ell"] is not None:                                       # l: d k_c / d l = k_c d^2 / l^3
+        yield idx + 3, A * kt * S * d2 / p["ell"] ** 3
 
 
 def lml_grad_exact(x, y, h, dim, n1, n2, beta=1.0):
@@ -494,7 +519,7 @@ def lml_grad_exact(x, y, h, dim, n1, n2, beta=1.0):
     Kinv = Linv.T @ Linv
     alpha = Kinv @ y
     lml = -0.5 * float(y @ alpha) - float(np.sum(np.log(np.diag(L))))
-    grad = np.zeros(n_params(dim, n1, n2))
+    grad = np.zeros(len(np.asarray(h)))
     for i, dK in dK_dtheta_all(x, h, dim, n1, n2, beta):
         grad[i] = 0.5 * float(alpha @ (dK @ alpha)) - 0.5 * float(np.sum(Kinv * dK))
     return lml, grad
@@ -672,7 +697,7 @@ def lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed,
         return lml, None, info
     # U_hat = Khat^-1 Z; the estimator per parameter is (1/nv) tr(U_hat^T Khat_theta Z).
     Uhat = np.linalg.solve(Khat, Z) if act.size else np.zeros((0, n_probes))
-    npar = n_params(dim, n1, n2)
+    npar = len(np.asarray(h))
     grad = np.zeros(npar)
     if with_bounds:
         Kinv = np.linalg.inv(Khat) if act.size else np.zeros((0, 0))
@@ -721,7 +746,7 @@ def sparsity_upper_bound_grad(h, dim, n1, n2, domain_volume=1.0):
     radii enter, with d Vol(dim, r) / d r = dim Vol(dim, r) / r, so
       d s / d r_ij = 2 (sum_k Vol(r_ik)) dim Vol(r_ij) / r_ij / Vol(X)^2."""
     p = unpack_h(h, dim, n1, n2)
-    g = np.zeros(n_params(dim, n1, n2))
+    g = np.zeros(len(np.asarray(h)))        # a core length scale, if any, does not enter the bound
     for i in range(n1):
         v = [ball_volume(dim, r) for r in p["radii"][i]]
         tot = sum(v)

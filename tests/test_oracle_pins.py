@@ -107,7 +107,7 @@ def test_entries_hp_match_float64_where_well_conditioned():
     # ulps away from the support edges; everywhere within the float64 form's
     # absolute cancellation error (a few ulps of its O(1) terms, times A C
     # sum_m |f_m f_m|) plus the float64 bump's relative error near its own
-    # edge (beta ulp / u^2, below 1e-11 while the bump is a normal number);
+    # edge (beta ulp / u^2, below 1e-10 while the bump is a normal number, u > 1/708);
     # diagonal A C sum F^2 + s2
     x, y, h, dim, n1, n2 = small_problem(seed=61, n=120, dim=3, n1=2, n2=3, r_s=0.45, radii=(0.3, 0.6))
     p = O.unpack_h(h, dim, n1, n2)
@@ -117,7 +117,7 @@ def test_entries_hp_match_float64_where_well_conditioned():
     d2 = np.sum((x[rows] - x[col]) ** 2, axis=1)
     F, mask = O.bump_table(x, h, dim, n1, n2)
     S_abs = np.sum(np.abs(F[rows] * F[col]), axis=1)
-    assert np.all(np.abs(hp - val) <= 1e-14 * p["A"] * O.KSTAT_PREFACTOR * S_abs + 1e-11 * np.abs(val))
+    assert np.all(np.abs(hp - val) <= 1e-14 * p["A"] * O.KSTAT_PREFACTOR * S_abs + 1e-10 * np.abs(val))
     # away from every edge (rho < 0.9, each point well inside its bumps or
     # outside all) the float64 form is accurate to rounding
     def deep(i):
@@ -353,8 +353,11 @@ def test_all_inactive_is_exact_noise_model():
     assert np.all(grad[:-1] == 0.0)
 
 
-def test_exact_gradient_matches_central_fd():
+@pytest.mark.parametrize("core", [False, True])
+def test_exact_gradient_matches_central_fd(core):
     x, y, h, dim, n1, n2 = small_problem(n=120)
+    if core:
+        h = np.append(h, 0.2)     # squared-exponential core, l = 0.2 against r_s = 0.35
     lml, grad = O.lml_grad_exact(x, y, h, dim, n1, n2)
     eps = 1e-6
     for i in range(len(h)):
@@ -567,3 +570,70 @@ def test_sparsity_gradient_and_augmented_objective_against_finite_differences():
             vp = O.augmented_objective(*f(hp), hp, dim, n1, n2, vol)[0]
             vm = O.augmented_objective(*f(hm), hm, dim, n1, n2, vol)[0]
             assert gr[q] == pytest.approx((vp - vm) / (2 * eps), rel=1e-6, abs=1e-9)
+
+
+# --------------------------------------------------------------------- core kernel k_c * k_s
+
+def test_core_kernel_entries_psd_and_limits():
+    # K with a squared-exponential core: pair by pair against plain loops
+    # (math.exp, the independent k~ series where it has converged), symmetric
+    # and PSD (a Schur product of PSD kernels), the diagonal untouched, and
+    # the plain kernel recovered as l -> infinity
+    for dim in (1, 2, 3):
+        x, y, h, _, n1, n2 = small_problem(seed=70 + dim, n=160, dim=dim, r_s=0.4)
+        hc = np.append(h, 0.15)
+        p = O.unpack_h(hc, dim, n1, n2)
+        assert p["ell"] == 0.15 and O.unpack_h(h, dim, n1, n2)["ell"] is None
+        K = O.dense_K(x, hc, dim, n1, n2)
+        K0 = O.dense_K(x, h, dim, n1, n2)
+        assert np.array_equal(K, K.T)
+        ev = np.linalg.eigvalsh(K)
+        assert ev[0] > -1e-12 * ev[-1]
+        assert np.array_equal(np.diag(K), np.diag(K0))
+        F, _ = O.bump_table(x, h, dim, n1, n2)
+        checked = 0
+        for i in range(0, len(x), 7):
+            for j in range(len(x)):
+                if i == j or K0[i, j] == 0.0:
+                    assert K[i, j] == K0[i, j]
+                    continue
+                d2 = sum((x[i][k] - x[j][k]) ** 2 for k in range(dim))
+                rho = math.sqrt(d2) / p["r_s"]
+                if rho < 0.3:
+                    continue
+                kt = series_kstat(np.array([rho]), terms=4000)[0]
+                S = sum(F[i, m] * F[j, m] for m in range(n1))
+                expect = p["A"] * kt * math.exp(-d2 / (2 * 0.15 ** 2)) * S
+                assert K[i, j] == pytest.approx(expect, rel=1e-9, abs=1e-15 * abs(p["A"] * S)), (i, j)
+                checked += 1
+        assert checked > 50
+        Kinf = O.dense_K(x, np.append(h, 1e9), dim, n1, n2)
+        assert np.allclose(Kinf, K0, rtol=1e-15, atol=1e-300)
+
+
+def test_core_kernel_full_accuracy_entries_and_cross_covariance():
+    # the decimal route with the core against the float64 brute force where
+    # neither cancels, and the test-point cross-covariance likewise
+    x, y, h, dim, n1, n2 = small_problem(seed=81, n=100, dim=2, r_s=0.45)
+    hc = np.append(h, 0.2)
+    rp, col, val = O.assemble_csr(x, hc, dim, n1, n2)
+    rows = np.repeat(np.arange(len(x)), np.diff(rp))
+    hp = O.entries_hp(x, hc, dim, n1, n2, rows, col)
+    d2 = np.sum((x[rows] - x[col]) ** 2, axis=1)
+    F, _ = O.bump_table(x, h, dim, n1, n2)
+    S_abs = np.sum(np.abs(F[rows] * F[col]), axis=1)
+    p = O.unpack_h(hc, dim, n1, n2)
+    assert np.all(np.abs(hp - val) <= 1e-14 * p["A"] * O.KSTAT_PREFACTOR * S_abs + 1e-10 * np.abs(val))
+    # away from every edge (rho < 0.9, both points well inside their bumps or
+    # outside all) the float64 form is accurate to rounding
+    q = np.stack([np.sum((x - p["centres"][m, b]) ** 2, axis=1) / p["radii"][m, b] ** 2
+                  for m in range(n1) for b in range(n2)], axis=1)
+    deep = np.all((q < 0.8) | (q > 1.0), axis=1)
+    good = (d2 < (0.9 * p["r_s"]) ** 2) & deep[rows] & deep[col] \
+        & (np.abs(val) > 1e-3 * p["A"] * O.KSTAT_PREFACTOR * S_abs)
+    assert good.sum() > 50
+    assert np.allclose(hp[good], val[good], rtol=1e-12, atol=0)
+    xs = np.random.default_rng(82).uniform(0, 1, (20, dim))
+    k64, khp = O.cross_K(xs, x, hc, dim, n1, n2), O.cross_K_hp(xs, x, hc, dim, n1, n2)
+    assert np.array_equal(k64 == 0, khp == 0)
+    assert np.allclose(khp, k64, rtol=1e-9, atol=1e-15 * np.abs(k64).max())
