@@ -24,7 +24,8 @@
  *  - Hyperparameters h: host array of gp_n_params() doubles laid out as
  *      for m < n_funcs, b < n_bumps: [centre (dim), radius r_mb, amplitude a_mb]
  *      then r_s (stationary support radius), A (stationary amplitude),
- *      sigma_n^2 (noise variance).
+ *      sigma_n^2 (noise variance), and with GP_CORE_SQEXP the core length
+ *      scale l.
  *    This is the hyperparameter set of Eq. eq:bump / eq:kstat; the bump shape
  *    beta is a fixed constant of the context (Sec. 3 counts 42 parameters for
  *    n_funcs = 2, n_bumps = 4, dim = 3: no beta among them).
@@ -65,13 +66,26 @@ extern "C" {
 
 typedef struct gp_ctx gp_ctx; /* opaque: owns the CSR matrix and all device workspaces */
 
+/* Core kernel k_c multiplying the sparsity-discovering kernel (Sec. 2.2: any
+ * kernel k_c may be combined as k_c * k_s; the paper's figure shows a squared
+ * exponential core):
+ *   GP_CORE_NONE   K = A k~ sum_m f_m f_m + sigma_n^2 I
+ *   GP_CORE_SQEXP  K = A k~ exp(-|x_i - x_j|^2 / (2 l^2)) sum_m f_m f_m + sigma_n^2 I,
+ *                  with the length scale l > 0 one more hyperparameter, the
+ *                  last entry of h.  k_c(x, x) = 1, so the diagonal, the
+ *                  pattern and the sparsity bound do not depend on l. */
+#define GP_CORE_NONE  0
+#define GP_CORE_SQEXP 1
+
 /* Kernel family (Eq. eq:bump_kernel): dim in 1..3, n_funcs (n1) in 1..32,
- * n_bumps (n2) >= 1 with n_funcs*n_bumps <= 512, beta > 0 (shape of every bump). */
+ * n_bumps (n2) >= 1 with n_funcs*n_bumps <= 512, beta > 0 (shape of every
+ * bump), core one of GP_CORE_*. */
 typedef struct {
   int32_t dim;
   int32_t n_funcs;
   int32_t n_bumps;
   double beta;
+  int32_t core;
 } gp_kernel_desc;
 
 typedef struct {
@@ -157,7 +171,7 @@ typedef struct {
   int32_t spmm_variant;   /* GP_SPMM_* form of the FP32 sparse product, -1 if none ran */
 } gp_info;
 
-/* Number of hyperparameters: n_funcs*n_bumps*(dim+2) + 3. */
+/* Number of hyperparameters: n_funcs*n_bumps*(dim+2) + 3, plus 1 with GP_CORE_SQEXP. */
 int64_t gp_n_params(const gp_kernel_desc* desc);
 
 /* Sparsity bound of Sec. 2.2 (Eq. eq:sparsity_estimate and the two equations
@@ -172,14 +186,21 @@ int64_t gp_n_params(const gp_kernel_desc* desc);
 int gp_sparsity_estimate(const gp_kernel_desc* desc, const double* h, double domain_volume, double* s,
                          double* grad);
 
-/* Augmented objective of Sec. 2.4 (Eq. eq:augmented): ln L + (1 - s) ln L =
- * (2 - s(h)) ln L(h), which prefers sparse covariance matrices while the
- * likelihood keeps priority (s in [0, 1]), and its gradient by the product
- * rule, (2 - s) d ln L / d h - ln L d s / d h.  lml and lml_grad are what
- * gp_lml_grad returned for h; grad (gp_n_params doubles) may be NULL, and
- * then lml_grad may be NULL too.  s_out (may be NULL) receives s(h), which
- * is also what a caller compares with its sparsity requirement for the
- * constrained form (Eq. eq:constrained).  Host arrays; no device work. */
+/* Augmented objective of Sec. 2.4 (Eq. eq:augmented) exactly as printed:
+ * ln L + (1 - s) ln L = (2 - s(h)) ln L(h), with s the sparsity bound of
+ * gp_sparsity_estimate, and its gradient by the product rule,
+ * (2 - s) d ln L / d h - ln L d s / d h.  Two properties a caller should know:
+ *  - s is the uncapped upper bound of Sec. 2.2; it exceeds 1 when the bumps'
+ *    balls overlap enough (it is a bound, not a fraction), and for s > 2 the
+ *    weight (2 - s) on ln L changes sign;
+ *  - d value / d s = -ln L, so for ln L < 0 (the usual case) a larger s (a
+ *    denser K) raises the value: the objective favours sparsity only where
+ *    ln L > 0.
+ * lml and lml_grad are what gp_lml_grad returned for h; grad (gp_n_params
+ * doubles) may be NULL, and then lml_grad may be NULL too.  s_out (may be
+ * NULL) receives s(h), which is also what a caller compares with its sparsity
+ * requirement for the constrained form (Eq. eq:constrained).  Host arrays; no
+ * device work. */
 int gp_augmented(const gp_kernel_desc* desc, const double* h, double domain_volume, double lml,
                  const double* lml_grad, double* value, double* grad, double* s_out);
 
@@ -213,14 +234,14 @@ int gp_get_csr(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
                int32_t* perm, int64_t sizes[2]);
 
 /* Copy-out that allocates no device memory.  No counterpart in the paper.
- * For callers that cannot call cudaMalloc at this point: code that runs while
- * a CUDA graph is being captured on the device, or a process whose device
- * memory is entirely handed out by another allocator (a serving runtime's
- * memory pool), still need the assembled matrix.  Same outputs and
- * conventions as gp_get_csr, but the unscaled values are staged in a
- * fixed area of static device memory inside the library
- * (GP_NOALLOC_MAX_NNZ doubles, 8 MiB, held by every device that loads the
- * library until the process exits) instead of a context buffer.
+ * For callers that must not call cudaMalloc at this point: a process whose
+ * device memory is entirely handed out by another allocator (a serving
+ * runtime's memory pool), or one already at its device-memory limit, still
+ * needs the assembled matrix, and gp_get_csr would grow a context buffer for
+ * the unscaled values.  Same outputs and conventions as gp_get_csr, but the
+ * unscaled values are staged in a fixed area of static device memory inside
+ * the library (GP_NOALLOC_MAX_NNZ doubles, 8 MiB, held by every device that
+ * loads the library until the process exits) instead of a context buffer.
  *  - If val is not NULL and nnz > GP_NOALLOC_MAX_NNZ: returns
  *    GP_ERR_UNSUPPORTED and copies nothing (use gp_get_csr).
  *  - The first call on a device looks up the staging area's device address
@@ -230,7 +251,8 @@ int gp_get_csr(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
  *    each call overwrites every entry it copies out, so nothing needs
  *    clearing.  Two calls whose GPU work overlaps (different streams or host
  *    threads on the same device) race on the area: order them on one stream.
- *  - Synchronises the context stream before returning. */
+ *  - Synchronises the context stream before returning, so the context stream
+ *    must not be a stream that is being captured into a CUDA graph. */
 #define GP_NOALLOC_MAX_NNZ (1 << 20)
 int gp_get_csr_noalloc(gp_ctx* ctx, int64_t* row_ptr, int32_t* col, double* val,
                        int32_t* perm, int64_t sizes[2]);

@@ -45,6 +45,8 @@ struct AdjArgs {
   float scale;           // (h / r_s)^2
   double rs2, AC, dk_coef;  // r_s^2, A C, A (6 C / r_s)
   double C;
+  double inv2l2;            // 1 / (2 l^2) of the squared-exponential core, 0 without one
+  double inv_l;             // 1 / l
 };
 
 __device__ inline double warp_sum_d(double v) {
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
   const T* Fs = (const T*)a.Fs;
   const T* dinv = (const T*)a.dinv;
   T* g = (T*)a.g;
-  double accA = 0.0, accR = 0.0, accS = 0.0;
+  double accA = 0.0, accR = 0.0, accS = 0.0, accL = 0.0;
   for (int q = lane; q < 32 * a.n1; q += 32) slot[q] = 0;
   for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < a.n; p += (int64_t)gridDim.x * kWarps) {
     const uint32_t mi = a.mask[p];
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
     const int4 ci = a.cellc[p];
     const float4 xi = a.xr[p];
     __syncwarp();
-    T rA = 0, rR = 0, rS = 0;
+    T rA = 0, rR = 0, rS = 0, rL = 0;
     for (int64_t e = a.rp[p] + lane; e < a.rp[p + 1]; e += 32) {
       const int j = a.col[e];
       const uint32_t mj = a.mask[j];
@@ -114,8 +116,18 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
         s2 = (T)((a.rs2 - e2) / a.rs2);
       }
       if (s2 <= (T)0) s2 = (T)0;
-      const T kt = s2 > (T)0 ? gpd::Real<T>::kstat(rho2, s2) : (T)0;
-      const T dk = s2 > (T)0 ? gpd::Real<T>::dk(rho2, s2) : (T)0;
+      T kt = s2 > (T)0 ? gpd::Real<T>::kstat(rho2, s2) : (T)0;
+      T dk = s2 > (T)0 ? gpd::Real<T>::dk(rho2, s2) : (T)0;
+      // squared-exponential core: every term of dK carries k_c, and
+      // dK/dl = K_s d^2 / l^3 (d^2 = rho^2 r_s^2)
+      T kc = (T)1, d2l3 = (T)0;
+      if (a.inv2l2 > 0.0) {
+        const double d2 = (double)rho2 * a.rs2;
+        kc = (T)gpd::sqexp_core<T>(d2 * a.inv2l2);
+        d2l3 = (T)(d2 * a.inv_l * a.inv_l * a.inv_l);
+        kt *= kc;
+        dk *= kc;
+      }
       const T dj = dinv[j];
       const T al_j = dj * xval<T, COLMAJOR>(X, a.ld, j, 0);
       const uint32_t zj0 = a.zbits[2 * (int64_t)j], zj1 = a.zbits[2 * (int64_t)j + 1];
@@ -140,11 +152,13 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
       }
       rA += W * (T)a.C * kt * S;
       rR += W * (T)a.dk_coef * rho2 * dk * S;
+      rL += W * (T)a.AC * kt * S * d2l3;
       if (j == p) rS += W;
     }
     accA += warp_sum_d((double)rA);
     accR += warp_sum_d((double)rR);
     accS += warp_sum_d((double)rS);
+    accL += warp_sum_d((double)rL);
     __syncwarp();
     for (int m = lane; m < a.n1; m += 32) {
       T t = 0;
@@ -156,18 +170,19 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
     }
     __syncwarp();
   }
-  __shared__ double red[kWarps][3];
+  __shared__ double red[kWarps][4];
   __shared__ bool last;
   if (lane == 0) {
     red[w][0] = accA;
     red[w][1] = accR;
     red[w][2] = accS;
+    red[w][3] = accL;
   }
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 4) {
     double t = 0.0;
     for (int ww = 0; ww < kWarps; ++ww) t += red[ww][threadIdx.x];
-    a.part[blockIdx.x * 3 + threadIdx.x] = t;
+    a.part[blockIdx.x * 4 + threadIdx.x] = t;
     __threadfence();
   }
   __syncthreads();
@@ -176,13 +191,14 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
     last = atomicInc(&a.s->ticket0, gridDim.x - 1) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x < 3) {
+  if (last && threadIdx.x < 4) {
     __threadfence();
     double t = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(a.part + b * 3 + threadIdx.x);
+    for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(a.part + b * 4 + threadIdx.x);
     if (threadIdx.x == 0) a.s->grad_A = t;
     if (threadIdx.x == 1) a.s->grad_rs = t;
     if (threadIdx.x == 2) a.s->grad_s2 = t;
+    if (threadIdx.x == 3) a.s->grad_l = t;
   }
 }
 
@@ -292,7 +308,7 @@ int run_adjoint(gp_ctx* c, int nv, int64_t ld) {
   const int nb = c->nb, np = c->dim + 2;
   GP_CHECK(gp::ensure(c, c->g, (size_t)n * c->n1 * sizeof(T)));
   const unsigned gw = grid_for(n, kWarps, c->num_sms * 4);
-  GP_CHECK(gp::ensure(c, c->part_c, (size_t)gw * 3 * sizeof(double)));
+  GP_CHECK(gp::ensure(c, c->part_c, (size_t)gw * 4 * sizeof(double)));
   AdjArgs a{};
   a.n = n;
   a.dim = c->dim;
@@ -318,6 +334,8 @@ int run_adjoint(gp_ctx* c, int nv, int64_t ld) {
   a.C = kPrefactor;
   a.AC = c->A * kPrefactor;
   a.dk_coef = c->A * 6.0 * kPrefactor / c->r_s;
+  a.inv2l2 = c->core == GP_CORE_SQEXP ? 1.0 / (2.0 * c->ell * c->ell) : 0.0;
+  a.inv_l = c->core == GP_CORE_SQEXP ? 1.0 / c->ell : 0.0;
   const size_t smem = (size_t)kWarps * (gp::kMaxProbes + 32 * c->n1) * sizeof(T);
   GP_CUDA(cudaFuncSetAttribute(k_adjoint<T, COLMAJOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;

@@ -103,6 +103,7 @@ int check_desc(const gp_kernel_desc* d) {
   if (!d) return GP_ERR_INVALID_ARG;
   if (d->dim < 1 || d->n_funcs < 1 || d->n_bumps < 1 || !(d->beta > 0.0) || !isfinite(d->beta))
     return GP_ERR_INVALID_ARG;
+  if (d->core != GP_CORE_NONE && d->core != GP_CORE_SQEXP) return GP_ERR_INVALID_ARG;
   if (d->dim > gp::kMaxDim || d->n_funcs > gp::kMaxFuncs || (int64_t)d->n_funcs * d->n_bumps > gp::kMaxBumps)
     return GP_ERR_UNSUPPORTED;
   return GP_OK;
@@ -119,6 +120,10 @@ int check_h(const gp_ctx* c, const double* h) {
   const double rs = h[c->nb * np], A = h[c->nb * np + 1], s2 = h[c->nb * np + 2];
   if (!isfinite(rs) || !isfinite(A) || !isfinite(s2)) return GP_ERR_INVALID_ARG;
   if (!(rs > 0.0) || !(A >= 0.0) || !(s2 > 0.0)) return GP_ERR_INVALID_ARG;
+  if (c->core == GP_CORE_SQEXP) {
+    const double l = h[c->nb * np + 3];
+    if (!isfinite(l) || !(l > 0.0)) return GP_ERR_INVALID_ARG;
+  }
   return GP_OK;
 }
 
@@ -266,12 +271,14 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
       GP_CUDA(cudaStreamSynchronize(c->stream));
       memcpy(gb.data(), c->pinned, nbp * sizeof(double));
     }
-    std::vector<double> out(nbp + 3);
+    const bool core = c->core == GP_CORE_SQEXP;
+    std::vector<double> out(nbp + 3 + (core ? 1 : 0));
     for (size_t q = 0; q < nbp; ++q) out[q] = gb[q];
     const bool act = c->n_act > 0;
     out[nbp] = act ? hs.grad_rs : 0.0;
     out[nbp + 1] = act ? hs.grad_A : 0.0;
     out[nbp + 2] = (act ? hs.grad_s2 : 0.0) + 0.5 * hs.inact_y2 / (s2 * s2) - 0.5 * n_in / s2;
+    if (core) out[nbp + 3] = act ? hs.grad_l : 0.0;
     if (gp::is_device_ptr(grad)) {
       GP_CHECK(gp::ensure_pinned(c, out.size() * sizeof(double)));
       memcpy(c->pinned, out.data(), out.size() * sizeof(double));
@@ -310,7 +317,7 @@ extern "C" {
 
 int64_t gp_n_params(const gp_kernel_desc* d) {
   if (!d) return -1;
-  return (int64_t)d->n_funcs * d->n_bumps * (d->dim + 2) + 3;
+  return (int64_t)d->n_funcs * d->n_bumps * (d->dim + 2) + 3 + (d->core == GP_CORE_SQEXP ? 1 : 0);
 }
 
 int gp_sparsity_estimate(const gp_kernel_desc* d, const double* h, double domain_volume, double* s, double* grad) {
@@ -384,6 +391,7 @@ int gp_create(gp_ctx** out, const gp_kernel_desc* desc, int device, void* stream
   c->n2 = desc->n_bumps;
   c->nb = desc->n_funcs * desc->n_bumps;
   c->beta = desc->beta;
+  c->core = desc->core;
   int st = GP_OK;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) st = GP_ERR_CUDA;
@@ -619,14 +627,14 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
   for (int32_t q = 0; q < n_inst; ++q)
     if (offsets[q] < 0 || offsets[q + 1] < offsets[q]) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
-  const int64_t P = (int64_t)c->nb * (c->dim + 2) + 3;
+  const int64_t P = (int64_t)c->nb * (c->dim + 2) + 3 + (c->core == GP_CORE_SQEXP ? 1 : 0);
   int nw = o->batch_workers > 0 ? o->batch_workers : 4;
   if (nw > n_inst) nw = n_inst;
   // worker contexts: own stream, workspace and CG graphs; kept for later calls
   while ((int)c->workers.size() < nw) {
     cudaStream_t s = nullptr;
     GP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    const gp_kernel_desc d{c->dim, c->n1, c->n2, c->beta};
+    const gp_kernel_desc d{c->dim, c->n1, c->n2, c->beta, c->core};
     gp_ctx* w = nullptr;
     const int st = gp_create(&w, &d, c->device, s);
     if (st != GP_OK) {

@@ -359,6 +359,7 @@ struct PairArgs {
   double inv_rs2;
   double AC;     // A * C
   double sigma2;
+  double inv2l2; // 1 / (2 l^2) of the squared-exponential core, 0 without a core
 };
 
 __device__ inline int warp_incl_scan_int(int v) {
@@ -507,6 +508,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
               S = gpd::dot2_bits(Fp, Fj, mi & mj);
             }
             double vv = a.AC * kst * S;
+            if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
             if (j == p) vv += a.sigma2;
             v = (T)(vv * a.dinv64[p] * a.dinv64[j]);
           }
@@ -911,6 +913,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   pa.inv_rs2 = 1.0 / pa.rs2;
   pa.AC = AC;
   pa.sigma2 = c->sigma2;
+  pa.inv2l2 = c->core == GP_CORE_SQEXP ? 1.0 / (2.0 * c->ell * c->ell) : 0.0;
   const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
   k_pair<T, false><<<gw, kThreads, 0, c->stream>>>(pa);
   GP_LAUNCH_CHECK();
@@ -984,6 +987,7 @@ int assemble(gp_ctx* c, const double* x, int64_t n, const double* h, int precisi
   c->r_s = h[nbp];
   c->A = h[nbp + 1];
   c->sigma2 = h[nbp + 2];
+  c->ell = c->core == GP_CORE_SQEXP ? h[nbp + 3] : 0.0;
   if (n > (int64_t)INT32_MAX - 1) return GP_ERR_UNSUPPORTED;
   c->n_act = 0;
   c->nnz = 0;

@@ -87,6 +87,7 @@ struct AsmScalars {
   double grad_A;
   double grad_rs;
   double grad_s2;
+  double grad_l;           // core length scale (GP_CORE_SQEXP)
   unsigned ticket0;
   unsigned ticket1;
   unsigned ticket2;
@@ -123,6 +124,7 @@ struct gp_ctx {
   cudaStream_t stream = nullptr;
   int dim = 0, n1 = 0, n2 = 0, nb = 0;
   double beta = 1.0;
+  int core = GP_CORE_NONE;
   int num_sms = 0;
 
   // last assembly
@@ -130,6 +132,7 @@ struct gp_ctx {
   int precision = GP_FP32_MIXED;
   int64_t n = 0, n_act = 0, nnz = 0;
   double r_s = 0, A = 0, sigma2 = 0;
+  double ell = 0;  // core length scale (GP_CORE_SQEXP), else 0
   gp::Grid grid{};
 
   // device buffers (grow-only)
@@ -413,6 +416,18 @@ __device__ inline double dot2_bits(const double* a, const double* b, uint32_t bi
     c += te + pe;
   }
   return s + c;
+}
+
+// exp(-t) for t >= 0, the squared-exponential core exp(-d^2 / (2 l^2)) at
+// t = d^2 / (2 l^2).  FP64: exp.  FP32 path: t split as th + tl (th its FP32
+// rounding) and exp(-t) = expf(-th) (1 - tl), so the rounding of t to FP32
+// (relative 2^-24, absolute 2^-24 t) does not enter the result.
+template <typename T>
+__device__ inline double sqexp_core(double t) {
+  if (sizeof(T) == 8) return exp(-t);
+  const float th = (float)t;
+  const double tl = t - (double)th;
+  return (double)expf(-th) * (1.0 - tl);
 }
 
 template <typename T> struct Real;

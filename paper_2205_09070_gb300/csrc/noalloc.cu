@@ -1,8 +1,8 @@
 // gp_get_csr_noalloc: the copy-out of gp_get_csr with its only scratch buffer
 // (the unscaled values, staged on the device before the copy to the caller)
 // in static device memory, so the call allocates nothing.  For callers that
-// cannot allocate device memory at this point (graph capture in progress, or
-// a device memory pool owned by another allocator).
+// must not allocate device memory at this point (another allocator owns the
+// device's memory, or the process is at its device-memory limit).
 #include <mutex>
 
 #include "gp_internal.cuh"
@@ -66,8 +66,12 @@ extern "C" int gp_get_csr_noalloc(gp_ctx* c, int64_t* row_ptr, int32_t* col, dou
   if (c->n_act == 0) {
     if (row_ptr) {
       const int64_t z = 0;
-      if (gp::is_device_ptr(row_ptr)) GP_CUDA(cudaMemcpy(row_ptr, &z, sizeof(z), cudaMemcpyHostToDevice));
-      else *row_ptr = 0;
+      if (gp::is_device_ptr(row_ptr)) {
+        GP_CUDA(cudaMemcpyAsync(row_ptr, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+        GP_CUDA(cudaStreamSynchronize(c->stream));
+      } else {
+        *row_ptr = 0;
+      }
     }
     return GP_OK;
   }

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kThreads) k_predict(const double* __restrict__
                                                       const uint32_t* __restrict__ perm,
                                                       const double* __restrict__ F0,
                                                       const double* __restrict__ alpha, double AC, double rs2,
-                                                      double rs2l, double* __restrict__ mean) {
+                                                      double rs2l, double inv2l2, double* __restrict__ mean) {
   __shared__ double sF[kWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int dim = g.dim;
@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(kThreads) k_predict(const double* __restrict__
           const double S = gpd::dot2_bits(sF[w], F0 + (int64_t)i * n1, common);
           double s2 = (rs2 - d2) / rs2;
           if (s2 < 1e-2) s2 = gpd::one_minus_ratio(xq, xs + (int64_t)j * dim, dim, rs2, rs2l);
-          const double kst = s2 > 0.0 ? gpd::kstat_unit_d(d2 / rs2, s2) : 0.0;
+          double kst = s2 > 0.0 ? gpd::kstat_unit_d(d2 / rs2, s2) : 0.0;
+          if (inv2l2 > 0.0) kst *= exp(-d2 * inv2l2);
           acc += AC * kst * S * alpha[i];
         }
       }
@@ -128,7 +129,8 @@ int predict_mean(gp_ctx* c, const double* xstar, int64_t ns, const double* alpha
   k_predict<<<(unsigned)blocks, kThreads, 0, c->stream>>>(
       xstar, ns, (const gp::BumpParam*)c->bump.p, c->n1, c->n2, c->beta, c->grid, (const int2*)c->cells.p,
       (const double*)c->xs.p, (const uint32_t*)c->smask.p, (const uint32_t*)c->vals.p, (const double*)c->F0.p,
-      alpha, c->A * kStatPrefactor, rs2, rs2l, mean);
+      alpha, c->A * kStatPrefactor, rs2, rs2l,
+      c->core == GP_CORE_SQEXP ? 1.0 / (2.0 * c->ell * c->ell) : 0.0, mean);
   GP_LAUNCH_CHECK();
   c->launches += 1;
   return GP_OK;

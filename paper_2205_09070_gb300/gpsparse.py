@@ -53,9 +53,13 @@ EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set
             "gp_lml_grad_batched", "gp_status_string", "gp_sparsity_estimate", "gp_augmented"]
 
 
+GP_CORE_NONE = 0
+GP_CORE_SQEXP = 1
+
+
 class KernelDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_funcs", ctypes.c_int32), ("n_bumps", ctypes.c_int32),
-                ("beta", ctypes.c_double)]
+                ("beta", ctypes.c_double), ("core", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -138,9 +142,10 @@ def status_string(status: int) -> str:
     return load().gp_status_string(status).decode()
 
 
-def sparsity_estimate(dim: int, n_funcs: int, n_bumps: int, h, domain_volume: float, beta: float = 1.0):
+def sparsity_estimate(dim: int, n_funcs: int, n_bumps: int, h, domain_volume: float, beta: float = 1.0,
+                      core: int = GP_CORE_NONE):
     """(s, d s / d h): the sparsity bound of the paper's kernel (host-side)."""
-    d = KernelDesc(dim, n_funcs, n_bumps, beta)
+    d = KernelDesc(dim, n_funcs, n_bumps, beta, core)
     hh = np.ascontiguousarray(h, dtype=np.float64)
     s = ctypes.c_double()
     g = np.zeros(hh.shape[0], np.float64)
@@ -152,13 +157,22 @@ def sparsity_estimate(dim: int, n_funcs: int, n_bumps: int, h, domain_volume: fl
 
 
 def augmented_objective(dim: int, n_funcs: int, n_bumps: int, h, domain_volume: float, lml: float, lml_grad,
-                        beta: float = 1.0):
-    """(value, gradient, s) of (2 - s(h)) ln L(h) given ln L and its gradient."""
-    d = KernelDesc(dim, n_funcs, n_bumps, beta)
+                        beta: float = 1.0, core: int = GP_CORE_NONE):
+    """(value, gradient, s) of (2 - s(h)) ln L(h) given ln L and its gradient;
+    with lml_grad None only the value and s are formed (gradient None)."""
+    d = KernelDesc(dim, n_funcs, n_bumps, beta, core)
     hh = np.ascontiguousarray(h, dtype=np.float64)
-    lg = np.ascontiguousarray(lml_grad, dtype=np.float64)
     v = ctypes.c_double()
     s = ctypes.c_double()
+    if lml_grad is None:
+        st = load().gp_augmented(ctypes.byref(d), hh.ctypes.data, float(domain_volume), float(lml), None,
+                                 ctypes.byref(v), None, ctypes.byref(s))
+        if st != GP_OK:
+            raise GPError(st, "gp_augmented")
+        return v.value, None, s.value
+    lg = np.ascontiguousarray(lml_grad, dtype=np.float64)
+    if lg.shape != hh.shape:
+        raise ValueError("lml_grad must have one entry per hyperparameter")
     g = np.zeros(hh.shape[0], np.float64)
     st = load().gp_augmented(ctypes.byref(d), hh.ctypes.data, float(domain_volume), float(lml), lg.ctypes.data,
                              ctypes.byref(v), g.ctypes.data, ctypes.byref(s))
@@ -212,11 +226,12 @@ class CSR:
 
 
 class GP:
-    """One library context: a kernel family (dim, n_funcs, n_bumps, beta) on one device."""
+    """One library context: a kernel family (dim, n_funcs, n_bumps, beta, core) on one device."""
 
-    def __init__(self, dim: int, n_funcs: int, n_bumps: int, beta: float = 1.0, device: int = 0):
+    def __init__(self, dim: int, n_funcs: int, n_bumps: int, beta: float = 1.0, device: int = 0,
+                 core: int = GP_CORE_NONE):
         self._lib = load()
-        self.desc = KernelDesc(dim, n_funcs, n_bumps, beta)
+        self.desc = KernelDesc(dim, n_funcs, n_bumps, beta, core)
         self.device = device
         self._stream = _stream_handle(device)
         h = ctypes.c_void_p()

@@ -132,3 +132,40 @@ def test_bench_workload_sampled_rows(G):
         den += p.y[i] ** 2
     assert np.sqrt(num / den) < 1e-3
     gp.close()
+
+
+def test_5m_workload_sampled_rows(G):
+    """The literal 5,000,000-point configuration (mixture, r_s = 0.005, 8 x 16
+    bumps) in the bench's FP32 launch configuration: sampled rows of K against
+    brute force over all N points (pattern bit-exact, every value within
+    1e-5 of the full-accuracy oracle) and the Euler identities of the
+    gradient estimator at that size."""
+    p = W.mixture_3d(seed=5, n=5_000_000)
+    gp = G.GP(p.dim, p.n1, p.n2)
+    o = G.default_opts(precision="fp32", n_probes=32, lanczos_steps=50, cg_rtol=1e-6, seed=2022, max_iter=20000)
+    lml, g, info = gp.lml_grad(dev(p.x), dev(p.y), p.h, o)
+    assert np.isfinite(lml) and np.all(np.isfinite(g))
+    csr = gp.get_csr()
+    table = O.bump_table(p.x, p.h, p.dim, p.n1, p.n2)
+    assert info["n_active"] == int(np.sum(table[1] != 0))
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(len(csr.perm), 24, replace=False))
+    heavy = np.argsort(np.diff(csr.row_ptr))[-8:]
+    for r in np.concatenate([rows, heavy]):
+        i = int(csr.perm[r])
+        cols = csr.perm[csr.col[csr.row_ptr[r]:csr.row_ptr[r + 1]]].astype(np.int64)
+        vals = csr.val[csr.row_ptr[r]:csr.row_ptr[r + 1]]
+        order = np.argsort(cols)
+        pat, _ = O.pair_rows(p.x, p.h, p.dim, p.n1, p.n2, [i], table=table)
+        ref_cols = np.nonzero(pat[0])[0]
+        assert np.array_equal(cols[order], ref_cols), r
+        ref_v = O.entries_hp(p.x, p.h, p.dim, p.n1, p.n2, np.full(len(ref_cols), i), ref_cols)
+        kdiag = O.entries_hp(p.x, p.h, p.dim, p.n1, p.n2, ref_cols, ref_cols)
+        kii = kdiag[ref_cols == i][0]
+        err = np.abs(vals[order] - ref_v)
+        assert np.all(err <= 1e-5 * np.abs(ref_v) + 2.0 ** -149 * np.sqrt(kii * kdiag)), r
+    P = O.unpack_h(p.h, p.dim, p.n1, p.n2)
+    assert P["A"] * g[-2] + P["sigma2"] * g[-1] == pytest.approx(0.5 * info["quad_form"] - 0.5 * p.n, rel=1e-4)
+    amp = [b * (p.dim + 2) + p.dim + 1 for b in range(p.n1 * p.n2)]
+    assert sum(p.h[i] * g[i] for i in amp) == pytest.approx(2 * P["A"] * g[-2], rel=1e-3, abs=1e-6 * abs(g).max())
+    gp.close()

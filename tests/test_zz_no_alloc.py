@@ -1,8 +1,9 @@
-"""gp_get_csr_noalloc: the copy-out for callers that cannot allocate device
-memory at the time of the call (for example while a CUDA graph is being
-captured, or when another allocator owns the device's memory).  It must give
-exactly what gp_get_csr gives, call after call, although every call reuses the
-same static staging area on the device.  This file is collected last."""
+"""gp_get_csr_noalloc: the copy-out for callers that must not allocate device
+memory at the time of the call (another allocator owns the device's memory,
+or the process is at its device-memory limit).  It must give exactly what
+gp_get_csr gives, call after call, although every call reuses the same static
+staging area on the device, and it must leave the device's free memory
+untouched.  This file is collected last."""
 
 import ctypes
 
@@ -61,6 +62,36 @@ def test_noalloc_copy_matches_gp_get_csr_on_consecutive_calls(G, prec):
             for a, b in zip(ref, got):
                 assert np.array_equal(a, b)
         gp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_leaves_device_memory_untouched(G, prec):
+    # on a fresh context, before any allocating copy-out: once the library's
+    # kernels and the staging area's address are set up (first call), a
+    # further call changes the device's free memory by nothing, while the
+    # allocating gp_get_csr grows a context buffer for the same values (a few
+    # MiB here, so that the driver cannot serve it from pages it already holds)
+    n = 30_000
+    p = W.mixture_3d(seed=9, n=n, r_s=0.005 * (5e6 / n) ** (1 / 3))
+    gp = G.GP(p.dim, p.n1, p.n2)
+    info = gp.assemble(torch.as_tensor(p.x, device="cuda"), p.h, precision=prec)
+    assert 300_000 < info["nnz"] <= (1 << 20)
+    torch.cuda.synchronize()
+    first = copy_out(G, gp, "gp_get_csr_noalloc")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    again = copy_out(G, gp, "gp_get_csr_noalloc")
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)
+    ref = copy_out(G, gp, "gp_get_csr")
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1      # the allocating copy-out took memory
+    for a, b in zip(ref, again):
+        assert np.array_equal(a, b)
+    gp.close()
 
 
 def test_noalloc_rejects_matrices_above_the_staging_size(G):
