@@ -467,6 +467,72 @@ def predict_mean(x, y, h, xs, dim, n1, n2, beta=1.0):
     return cross_K(xs, x, h, dim, n1, n2, beta) @ alpha
 
 
+def prior_var(xs, h, dim, n1, n2, beta=1.0):
+    """k(x*, x*) = A k~(0) k_c(0) sum_m f_m(x*)^2 = A C sum_m f_m(x*)^2
+    (Eq. eq:bump_kernel at d = 0; a test point carries no noise)."""
+    p = unpack_h(h, dim, n1, n2)
+    Fq, _ = bump_table(np.asarray(xs, dtype=np.float64).reshape(-1, dim), h, dim, n1, n2, beta)
+    return p["A"] * KSTAT_PREFACTOR * np.sum(Fq * Fq, axis=1)
+
+
+def prior_var_hp(xs, h, dim, n1, n2, beta=1.0, digits=HP_DIGITS):
+    """prior_var with f_m(x*) from the decimal route (bump_sums_hp), rounded
+    once: accurate where the float64 bumps lose digits near their edges."""
+    xs = np.asarray(xs, dtype=np.float64).reshape(-1, dim)
+    out = np.zeros(xs.shape[0])
+    with localcontext() as ctx:
+        ctx.prec = digits
+        p, cand = _hp_candidate_bumps(xs, h, dim, n1, n2)
+        AC = Decimal(p["A"]) * _hp_constants()
+        for a in range(xs.shape[0]):
+            if cand[a]:
+                f = bump_sums_hp(xs[a], p, dim, n1, n2, beta, cand[a])
+                out[a] = float(AC * sum(v * v for v in f))
+    return out
+
+
+def dense_K_hp(x, h, dim, n1, n2, beta=1.0):
+    """dense_K with every stored entry from the decimal route (entries_hp)."""
+    x = np.asarray(x, dtype=np.float64)
+    rp, col, _ = assemble_csr(x, h, dim, n1, n2, beta)
+    rows = np.repeat(np.arange(x.shape[0]), np.diff(rp))
+    K = np.zeros((x.shape[0], x.shape[0]))
+    K[rows, col] = entries_hp(x, h, dim, n1, n2, rows, col, beta)
+    return K
+
+
+def predict_var(x, h, xs, dim, n1, n2, beta=1.0, kappa=None, prior=None, K=None):
+    """Posterior variance of the latent function at test points (Sec. 2.1,
+    Eq. eq:pred_distr): k(x*, x*) - kappa^T (K + V)^-1 kappa, V = sigma_n^2 I
+    inside K; dense K and a dense solve.  `kappa`, `prior` and `K` may pass the
+    cross-covariance, k(x*, x*) and K (for example the full-accuracy ones)."""
+    K = dense_K(x, h, dim, n1, n2, beta) if K is None else K
+    kap = cross_K(xs, x, h, dim, n1, n2, beta) if kappa is None else kappa
+    pri = prior_var(xs, h, dim, n1, n2, beta) if prior is None else prior
+    return pri - np.sum(kap * np.linalg.solve(K, kap.T).T, axis=1)
+
+
+def predict_var_sensitivity(x, h, xs, dim, n1, n2, beta=1.0, kappa=None):
+    """Per test point, what bounds the variance's change when the solve of
+    Khat u = D^-1/2 kappa stops at relative residual eps: to first order
+    kappa^T K^-1 kappa moves by r^T Khat^-1 khat, at most
+    eps |khat| |Khat^-1 khat| (khat = D^-1/2 kappa on the active rows), and by
+    |khat|^T |Khat^-1 khat| times the relative rounding of the entries.
+    Returns (|khat| |Khat^-1 khat|, |khat|^T |Khat^-1 khat|)."""
+    K = dense_K(x, h, dim, n1, n2, beta)
+    _, mask = bump_table(x, h, dim, n1, n2, beta)
+    act = np.nonzero(mask != 0)[0]
+    kap = cross_K(xs, x, h, dim, n1, n2, beta) if kappa is None else kappa
+    if act.size == 0:
+        return np.zeros(kap.shape[0]), np.zeros(kap.shape[0])
+    Ka = K[np.ix_(act, act)]
+    Dm = 1.0 / np.sqrt(np.diag(Ka))
+    Khat = Ka * Dm[:, None] * Dm[None, :]
+    kh = kap[:, act] * Dm[None, :]
+    u = np.linalg.solve(Khat, kh.T).T
+    return np.linalg.norm(kh, axis=1) * np.linalg.norm(u, axis=1), np.sum(np.abs(kh) * np.abs(u), axis=1)
+
+
 # ----------------------------------------------------------------------------
 # Eq. (eqn:log_likelihood): exact LML and its exact gradient
 # ----------------------------------------------------------------------------

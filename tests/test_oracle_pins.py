@@ -637,3 +637,34 @@ def test_core_kernel_full_accuracy_entries_and_cross_covariance():
     k64, khp = O.cross_K(xs, x, hc, dim, n1, n2), O.cross_K_hp(xs, x, hc, dim, n1, n2)
     assert np.array_equal(k64 == 0, khp == 0)
     assert np.allclose(khp, k64, rtol=1e-9, atol=1e-15 * np.abs(k64).max())
+
+
+# --------------------------------------------------------------------- posterior variance
+
+def test_predict_var_identities():
+    # at a training input x_i, kappa = K_:i - s2 e_i and k(x_i, x_i) = K_ii - s2,
+    # so the posterior variance is s2 - s2^2 (K^-1)_ii (an identity the dense
+    # solve does not use); elsewhere 0 <= var <= prior, var = prior where no
+    # training point is within r_s, and 0 outside every bump; with and without
+    # the core kernel
+    for core in (None, 0.2):
+        x, y, h, dim, n1, n2 = small_problem(seed=91, n=120)
+        if core is not None:
+            h = np.append(h, core)
+        p = O.unpack_h(h, dim, n1, n2)
+        K = O.dense_K(x, h, dim, n1, n2)
+        v_train = O.predict_var(x, h, x, dim, n1, n2)
+        expect = p["sigma2"] - p["sigma2"] ** 2 * np.diag(np.linalg.inv(K))
+        assert np.allclose(v_train, expect, rtol=1e-9, atol=1e-13 * p["sigma2"])
+        rng = np.random.default_rng(92)
+        xs = rng.uniform(-0.2, 1.2, (200, dim))
+        v = O.predict_var(x, h, xs, dim, n1, n2)
+        prior = O.prior_var(xs, h, dim, n1, n2)
+        assert np.all(v >= -1e-12 * (1 + prior)) and np.all(v <= prior + 1e-12 * (1 + prior))
+        d2min = np.min(np.sum((xs[:, None, :] - x[None, :, :]) ** 2, axis=2), axis=1)
+        far = d2min >= p["r_s"] ** 2
+        assert np.array_equal(v[far], prior[far])
+        _, mask = O.bump_table(xs, h, dim, n1, n2)
+        assert np.all(v[mask == 0] == 0.0)
+        # the full-accuracy prior agrees with the float64 one to the bumps' rounding
+        assert np.allclose(O.prior_var_hp(xs, h, dim, n1, n2), prior, rtol=1e-10, atol=0)
