@@ -49,7 +49,7 @@ extern "C" {
 
 /* status codes */
 #define GP_OK                 0
-#define GP_ERR_INVALID_ARG    1  /* bad size, null pointer, non-finite or out-of-range h */
+#define GP_ERR_INVALID_ARG    1  /* bad size, null pointer, non-finite or out-of-range h, non-finite y */
 #define GP_ERR_CUDA           2  /* a CUDA runtime call failed */
 #define GP_ERR_OOM            3  /* device allocation failed */
 #define GP_ERR_NOT_CONVERGED  4  /* CG hit max_iter before every column met cg_rtol; outputs are filled */
@@ -136,6 +136,22 @@ typedef struct {
  * spread over probes only.  FP32_MIXED only (else GP_ERR_UNSUPPORTED); the
  * gradient's trace term is Hutchinson's on the same probes either way. */
 #define GP_FLAG_LOGDET_TAYLOR 16
+
+/* gp_opts.flags: failure injection for tests of the error paths, all made on
+ * the host (no device fault, trap or hang):
+ *   GP_FLAG_FAULT_OOM     every device allocation the call needs fails as an
+ *                         out-of-memory would (GP_ERR_OOM); buffers the context
+ *                         already holds are kept
+ *   GP_FLAG_FAULT_NOT_SPD gp_lml / gp_lml_grad negate the assembled matrix
+ *                         before the solve, so CG meets p^T K p < 0
+ *                         (GP_ERR_NOT_SPD)
+ *   GP_FLAG_FAULT_NAN     gp_lml / gp_lml_grad write a NaN into one stored
+ *                         entry before the solve, so the CG scalars turn
+ *                         non-finite (GP_ERR_NOT_SPD)
+ * The next call without the flags re-assembles and runs normally. */
+#define GP_FLAG_FAULT_OOM 128
+#define GP_FLAG_FAULT_NOT_SPD 256
+#define GP_FLAG_FAULT_NAN 512
 
 /* gp_info.spmm_variant */
 #define GP_SPMM_CPASYNC  0
@@ -278,6 +294,23 @@ int gp_solve(gp_ctx* ctx, const double* y, double* alpha, const gp_opts* opts, g
  * info (may be NULL) reports the solve as gp_solve does. */
 int gp_predict(gp_ctx* ctx, const double* y, const double* xstar, int64_t n_star, double* mean,
                const gp_opts* opts, gp_info* info);
+
+/* Posterior variance at test points (Sec. 2.1, Eq. eq:pred_distr: the
+ * posterior covariance at x* is k(x*, x*) - kappa^T (K + V)^-1 kappa with
+ * kappa_i = k(x*, x_i); V = sigma_n^2 I is part of K; this is the variance of
+ * the latent function, with no noise term).  With the last assembled K, the
+ * test points are taken in blocks of 64; each block's kappa columns, Jacobi-
+ * scaled, are solved together as one right-hand-side block of the same CG
+ * (block-Jacobi preconditioned in FP32 when opts ask for it, single-column FP64
+ * CG otherwise), and var_q = k(x*_q, x*_q) - kappa_q^T K^-1 kappa_q with a
+ * compensated sum.  k(x*, x*) = A C sum_m f_m(x*)^2, so points outside every
+ * bump get variance 0.
+ *   xstar: n_star x dim doubles, row-major;  var: n_star doubles
+ * Arrays may be host or device.  GP_ERR_NOT_ASSEMBLED before a gp_assemble;
+ * GP_ERR_NOT_CONVERGED (variances still written) if a block's CG hit
+ * max_iter.  info (may be NULL) reports the largest iteration count. */
+int gp_predict_var(gp_ctx* ctx, const double* xstar, int64_t n_star, double* var, const gp_opts* opts,
+                   gp_info* info);
 
 /* Assemble K and evaluate ln L (Eq. eqn:log_likelihood) with
  * ln|K| = sum ln D + SLQ(D^-1/2 K D^-1/2) + N_inactive ln sigma_n^2, D = diag K.

@@ -34,6 +34,7 @@ bool is_device_ptr(const void* p) {
 int ensure(gp_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return GP_OK;
+  if (c->flags & GP_FLAG_FAULT_OOM) return GP_ERR_OOM;  // injected (tests of the error path)
   if (b.p) {
     GP_CUDA(cudaStreamSynchronize(c->stream));
     GP_CUDA(cudaFree(b.p));
@@ -205,6 +206,7 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
   GP_CHECK(stage_in(c, c->y_in, y, (size_t)n, &yd));
   GP_CHECK(gp::assemble(c, xd, n, h, o->precision));
   tm.mark(1);
+  if (o->flags & (GP_FLAG_FAULT_NOT_SPD | GP_FLAG_FAULT_NAN)) GP_CHECK(gp::inject_matrix_fault(c, o->flags));
   GP_CHECK(gp::precond_setup(c, o->precond_block));
   GP_CHECK(gp::inactive_terms(c, yd));
   const int nv = o->n_probes;
@@ -254,6 +256,7 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
   tm.mark(3);
   gp::AsmScalars hs;
   GP_CHECK(read_scalars(c, &hs));
+  if (!isfinite(hs.inact_y2)) return GP_ERR_INVALID_ARG;  // a non-finite target outside every bump
   if (c->n_act > 0 && hs.status != GP_OK) return hs.status;
   if (c->pc_block > 0 && hs.pc_status != GP_OK) return hs.pc_status;
   const double s2 = c->sigma2;
@@ -428,7 +431,7 @@ int gp_destroy(gp_ctx* c) {
                         &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z,
                         &c->xstar_in, &c->pred_tmp, &c->slq_steps, &c->taylor,
                         &c->w_cnt,  &c->w_tseg, &c->w_trun,     &c->w_trec,    &c->w_segd,    &c->w_runs,
-                        &c->w_rec};
+                        &c->w_rec,  &c->pv_B,   &c->pv_prior};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -601,6 +604,35 @@ int gp_predict(gp_ctx* c, const double* y, const double* xstar, int64_t n_star, 
   GP_CHECK(gp::predict_mean(c, xsd, n_star, (const double*)c->out_tmp.p, md));
   if (!dev && n_star > 0)
     GP_CUDA(cudaMemcpyAsync(mean, md, (size_t)n_star * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  tm.mark(1);
+  GP_CUDA(cudaStreamSynchronize(c->stream));
+  if (info) solve_info(c, iters, max_rel, tm.ms(0, 1), info);
+  return st;
+}
+
+int gp_predict_var(gp_ctx* c, const double* xstar, int64_t n_star, double* var, const gp_opts* o,
+                   gp_info* info) {
+  if (!c || !o || n_star < 0 || (n_star > 0 && (!xstar || !var))) return GP_ERR_INVALID_ARG;
+  if (!c->assembled) return GP_ERR_NOT_ASSEMBLED;
+  GP_CHECK(check_opts(o, false));
+  GP_CUDA(cudaSetDevice(c->device));
+  reset_counters(c, o->flags);
+  Timer tm(c);
+  tm.mark(0);
+  const double* xsd = nullptr;
+  GP_CHECK(stage_in(c, c->xstar_in, xstar, (size_t)n_star * c->dim, &xsd));
+  double* vd = var;
+  const bool dev = n_star > 0 && gp::is_device_ptr(var);
+  if (!dev && n_star > 0) {
+    GP_CHECK(gp::ensure(c, c->pred_tmp, (size_t)n_star * sizeof(double)));
+    vd = (double*)c->pred_tmp.p;
+  }
+  int iters = 0;
+  double max_rel = 0.0;
+  const int st = gp::predict_var(c, xsd, n_star, vd, o, &iters, &max_rel);
+  if (st != GP_OK && st != GP_ERR_NOT_CONVERGED) return st;
+  if (!dev && n_star > 0)
+    GP_CUDA(cudaMemcpyAsync(var, vd, (size_t)n_star * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   tm.mark(1);
   GP_CUDA(cudaStreamSynchronize(c->stream));
   if (info) solve_info(c, iters, max_rel, tm.ms(0, 1), info);

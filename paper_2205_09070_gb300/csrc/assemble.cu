@@ -710,6 +710,12 @@ __global__ void __launch_bounds__(kThreads) k_unscale(int64_t n, const int64_t* 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_negate(T* __restrict__ v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = -v[i];
+}
+
 unsigned grid_for(int64_t items, int per_block, int max_blocks) {
   int64_t g = (items + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -996,8 +1002,61 @@ int assemble(gp_ctx* c, const double* x, int64_t n, const double* h, int precisi
   if (n > 0) {
     int st = precision == GP_FP64 ? assemble_t<double>(c, x, n, h) : assemble_t<float>(c, x, n, h);
     if (st != GP_OK) return st;
+  } else {
+    // no points: the bumps still define k(x*, x*) for predictions
+    std::vector<gp::BumpParam> hb(c->nb);
+    const int np = c->dim + 2;
+    for (int b = 0; b < c->nb; ++b) {
+      const double* q = h + (size_t)b * np;
+      gp::BumpParam& bp = hb[b];
+      for (int k = 0; k < gp::kMaxDim; ++k) {
+        bp.c[k] = k < c->dim ? q[k] : 0.0;
+        bp.c32[k] = 0.f;
+      }
+      bp.r = q[c->dim];
+      gpd::two_prod(bp.r, bp.r, bp.r2, bp.r2l);
+      bp.a = q[c->dim + 1];
+      bp.m = b / c->n2;
+      bp.inv_r2_32 = (float)(1.0 / bp.r2);
+      bp.margin = 1e30f;
+    }
+    GP_CHECK(gp::ensure(c, c->bump, sizeof(gp::BumpParam) * c->nb));
+    GP_CHECK(gp::ensure_pinned(c, sizeof(gp::BumpParam) * c->nb));
+    memcpy(c->pinned, hb.data(), sizeof(gp::BumpParam) * c->nb);
+    GP_CUDA(cudaMemcpyAsync(c->bump.p, c->pinned, sizeof(gp::BumpParam) * c->nb, cudaMemcpyHostToDevice,
+                            c->stream));
+    GP_CUDA(cudaStreamSynchronize(c->stream));
   }
   c->assembled = true;
+  return GP_OK;
+}
+
+int inject_matrix_fault(gp_ctx* c, int flags) {
+  if (c->n_act == 0) return GP_OK;
+  const bool fp64 = c->precision == GP_FP64;
+  const unsigned g = grid_for(c->nnz, kThreads, c->num_sms * 8);
+  if (flags & GP_FLAG_FAULT_NOT_SPD) {
+    if (fp64) {
+      k_negate<double><<<g, kThreads, 0, c->stream>>>((double*)c->val.p, c->nnz);
+    } else {
+      k_negate<float><<<g, kThreads, 0, c->stream>>>((float*)c->val.p, c->nnz);
+      k_negate<float><<<grid_for(c->nbent * kBR, kThreads, c->num_sms * 8), kThreads, 0, c->stream>>>(
+          (float*)c->bval.p, c->nbent * kBR);
+    }
+    GP_LAUNCH_CHECK();
+    c->launches += fp64 ? 1 : 2;
+  }
+  if (flags & GP_FLAG_FAULT_NAN) {
+    if (fp64) {
+      const double nan = NAN;
+      GP_CUDA(cudaMemcpyAsync(c->val.p, &nan, sizeof(nan), cudaMemcpyHostToDevice, c->stream));
+    } else {
+      const float nan = NAN;
+      GP_CUDA(cudaMemcpyAsync(c->val.p, &nan, sizeof(nan), cudaMemcpyHostToDevice, c->stream));
+      GP_CUDA(cudaMemcpyAsync(c->bval.p, &nan, sizeof(nan), cudaMemcpyHostToDevice, c->stream));
+    }
+    GP_CUDA(cudaStreamSynchronize(c->stream));  // the host values above are on the stack
+  }
   return GP_OK;
 }
 

@@ -138,6 +138,7 @@ struct gp_ctx {
   // device buffers (grow-only)
   gp::DevBuf x_in, y_in, out_tmp;
   gp::DevBuf xstar_in, pred_tmp;  // gp_predict: staged test points, posterior means
+  gp::DevBuf pv_B, pv_prior;      // gp_predict_var: right-hand-side block, prior variances
   gp::DevBuf taylor;              // scalars of the truncated-Taylor log-determinant
   gp::DevBuf bump;
   gp::DevBuf mask0, F0, pos;
@@ -218,6 +219,9 @@ int scan_i32_to_i64(gp_ctx* c, const int32_t* in, int64_t* out, int64_t n);
 
 // assemble.cu
 int assemble(gp_ctx* c, const double* x_dev, int64_t n, const double* h, int precision);
+// GP_FLAG_FAULT_NOT_SPD: negate the stored matrix (scalar and block CSR);
+// GP_FLAG_FAULT_NAN: a NaN in the first stored entry (both forms)
+int inject_matrix_fault(gp_ctx* c, int flags);
 
 // precond.cu: inverses of the diagonal blocks of the assembled Khat
 // (pc_block rows per block, FP32 path only); pc_block == 0 switches it off.
@@ -226,13 +230,17 @@ int csr_unscaled(gp_ctx* c, double* val_out_dev);
 
 // solve.cu (cg_run: FP32 batched CG on the 8x1 block CSR)
 // warm: keep X from the previous run on the same block and start from the
-// residual B - Khat X (one extra product) instead of X = 0
+// residual B - Khat X (one extra product) instead of X = 0.  rhs: solve
+// Khat X = rhs for a caller-given N_act x kp FP32 block (row-major) instead of
+// [yhat, probes] (then nv = 0, lanczos_steps = 0, no warm start).
 int cg_run(gp_ctx* c, int k, int kp, const double* y_dev, int n_probes, uint64_t seed,
            int lanczos_steps, int max_iter, double rtol, int check_every,
-           int* iters_out, double* max_rel_resid, bool use_pc, bool warm = false);
+           int* iters_out, double* max_rel_resid, bool use_pc, bool warm = false,
+           const float* rhs = nullptr);
+// rhs: k columns of N_act doubles each (column-major) instead of [yhat, probes]
 int cg_run_fp64(gp_ctx* c, int k, const double* y_dev, int n_probes, uint64_t seed,
                 int lanczos_steps, int max_iter, double rtol, int check_every,
-                int* iters_out, double* max_rel_resid);
+                int* iters_out, double* max_rel_resid, const double* rhs = nullptr);
 int inactive_terms(gp_ctx* c, const double* y_dev);
 int quad_form(gp_ctx* c, const double* y_dev, int kp);
 // SLQ terms from the recorded Lanczos coefficients; with overlap the eigen-
@@ -252,6 +260,10 @@ int taylor_logdet(gp_ctx* c, int n_probes, int kp, int m);
 // predict.cu: posterior mean at ns test points (device arrays) from alpha =
 // K^-1 y in original point order (device, c->n doubles), over the last assembly.
 int predict_mean(gp_ctx* c, const double* xstar, int64_t ns, const double* alpha, double* mean);
+// posterior variance k(x*, x*) - kappa^T K^-1 kappa at ns test points (device
+// arrays), by blocks of test points solved as right-hand-side blocks
+int predict_var(gp_ctx* c, const double* xstar, int64_t ns, double* var, const gp_opts* o, int* iters_out,
+                double* max_rel);
 
 // spmm.cu: Q = Khat P on the 8x1 block CSR (c->brp, bcol, bval; P, Q, part_a
 // of the context), one launch per CG iteration.

@@ -154,10 +154,12 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
       double t = 0.0;
       for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
       st->iter = 0;
-      st->status = GP_OK;
-      st->bad_col = -1;
+      // non-finite targets: no run (the caller gets GP_ERR_INVALID_ARG)
+      st->status = isfinite(t) ? GP_OK : GP_ERR_INVALID_ARG;
+      st->bad_col = isfinite(t) ? -1 : 0;
       st->max_iter = max_iter;
       st->tol2 = tol2;
+      if (!isfinite(t)) t = 0.0;
       bool any = false;
       for (int c = 0; c < gp::kMaxCols; ++c) {
         const double r0 = c == 0 ? t : (c < k ? (double)n : 0.0);
@@ -171,9 +173,9 @@ __global__ void __launch_bounds__(kThreads) k_init_f32(int64_t n, int k, int kp,
         st->steps[c] = 0;
         any = any || (c < k && !st->donep[0][c]);
       }
-      st->fin[0] = !any;
-      st->fin[1] = !any;
-      st->finished = !any;
+      st->fin[0] = !any || st->status != GP_OK;
+      st->fin[1] = st->fin[0];
+      st->finished = st->fin[0];
     }
   }
 }
@@ -268,6 +270,83 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
   }
   const int kp = 4 * kq;
   if (threadIdx.x < kp) part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = red[threadIdx.x / 4][threadIdx.x % 4];
+}
+
+// Start of a CG run on a caller-given right-hand-side block B (N_act x kp,
+// Jacobi-scaled): X = 0, R = P = B, per-block partials of |b_c|^2 (thread per
+// float4 column slot, rows strided as in k_upd_r_f32).
+__global__ void __launch_bounds__(kUpdRThreads) k_rhs_init_f32(int64_t n, int kq, const float4* __restrict__ B,
+                                                               float4* __restrict__ X, float4* __restrict__ R,
+                                                               float4* __restrict__ P, double* __restrict__ part) {
+  __shared__ double red[kUpdRThreads][4];
+  const int ny = kUpdRThreads / kq;
+  const int tx = threadIdx.x % kq, ty = threadIdx.x / kq;
+  gpd::Dot2 b0, b1, b2, b3;
+  if (ty < ny) {
+    const int64_t stride = (int64_t)gridDim.x * ny;
+    for (int64_t p = (int64_t)blockIdx.x * ny + ty; p < n; p += stride) {
+      const float4 b = B[p * kq + tx];
+      X[p * kq + tx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      R[p * kq + tx] = b;
+      P[p * kq + tx] = b;
+      b0.add(b.x, b.x);
+      b1.add(b.y, b.y);
+      b2.add(b.z, b.z);
+      b3.add(b.w, b.w);
+    }
+  }
+  red[threadIdx.x][0] = b0.value();
+  red[threadIdx.x][1] = b1.value();
+  red[threadIdx.x][2] = b2.value();
+  red[threadIdx.x][3] = b3.value();
+  __syncthreads();
+  for (int h = 1; h < ny; h <<= 1) {
+    if (ty < ny && (ty & (2 * h - 1)) == 0 && ty + h < ny) {
+      const int o = threadIdx.x + h * kq;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[threadIdx.x][q] += red[o][q];
+    }
+    __syncthreads();
+  }
+  const int kp = 4 * kq;
+  if (threadIdx.x < kp) part[(int64_t)blockIdx.x * kp + threadIdx.x] = red[threadIdx.x / 4][threadIdx.x % 4];
+}
+
+// The run state for k_rhs_init_f32's block: |r_0|^2 = |b_c|^2 per column
+// (columns with b_c = 0 are done at once), iteration 0.
+__global__ void __launch_bounds__(kRedThreads) k_rhs_state(const double* __restrict__ part, int np, int k, int kp,
+                                                           gp::CgState* st, double tol2, int max_iter) {
+  __shared__ double scratch[kRedThreads];
+  __shared__ double sums[gp::kMaxCols];
+  __shared__ int any_running;
+  block_sum_partials(part, np, kp, kp, sums, scratch);
+  if (threadIdx.x == 0) any_running = 0;
+  __syncthreads();
+  if (threadIdx.x < gp::kMaxCols) {
+    const int c = threadIdx.x;
+    const double r0 = c < k ? sums[c] : 0.0;
+    st->rr0[c] = r0;
+    st->rrp[0][c] = r0;
+    st->rrp[1][c] = r0;
+    st->crr[0][c] = r0;
+    st->crr[1][c] = r0;
+    st->steps[c] = 0;
+    const bool done = !(r0 > 0.0);
+    st->donep[0][c] = done;
+    st->donep[1][c] = done;
+    if (c < k && !done) atomicOr(&any_running, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->iter = 0;
+    st->status = GP_OK;
+    st->bad_col = -1;
+    st->max_iter = max_iter;
+    st->tol2 = tol2;
+    st->fin[0] = !any_running;
+    st->fin[1] = !any_running;
+    st->finished = !any_running;
+  }
 }
 
 // B with the block-Jacobi preconditioner M (diagonal blocks of B rows of
@@ -767,7 +846,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, f
 // ---------------------------------------------------------------- FP64 single RHS
 __global__ void __launch_bounds__(kThreads) k_init_f64(int64_t n, int col0, int nv, const double* __restrict__ y,
                                                        const uint32_t* __restrict__ perm,
-                                                       const double* __restrict__ dinv64, uint64_t seed,
+                                                       const double* __restrict__ dinv64,
+                                                       const double* __restrict__ rhs, uint64_t seed,
                                                        double* __restrict__ X, double* __restrict__ R,
                                                        double* __restrict__ P, uint32_t* __restrict__ zbits,
                                                        double* __restrict__ part, gp::CgState* st, double tol2,
@@ -776,7 +856,9 @@ __global__ void __launch_bounds__(kThreads) k_init_f64(int64_t n, int col0, int 
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = perm[p];
     double v;
-    if (col0 == 0) {
+    if (rhs) {
+      v = rhs[(int64_t)col0 * n + p];
+    } else if (col0 == 0) {
       v = y[i] * dinv64[p];
       uint32_t zb[2] = {0u, 0u};
       for (int l = 0; l < nv; ++l) zb[l >> 5] |= gpd::probe_bit(seed, l, (long long)i) << (l & 31);
@@ -803,8 +885,10 @@ __global__ void __launch_bounds__(kThreads) k_init_f64(int64_t n, int col0, int 
       double t = 0.0;
       for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(part + b);
       st->iter = 0;
-      st->status = GP_OK;
-      st->bad_col = -1;
+      // non-finite targets (or right-hand side): no run, GP_ERR_INVALID_ARG
+      st->status = isfinite(t) ? GP_OK : GP_ERR_INVALID_ARG;
+      st->bad_col = isfinite(t) ? -1 : col0;
+      if (!isfinite(t)) t = 0.0;
       st->max_iter = max_iter;
       st->tol2 = tol2;
       st->rr0[0] = t;
@@ -1113,7 +1197,7 @@ int read_state(gp_ctx* c, gp::CgState* host) {
 namespace gp {
 
 int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
-           int check_every, int* iters_out, double* max_rel, bool use_pc, bool warm) {
+           int check_every, int* iters_out, double* max_rel, bool use_pc, bool warm, const float* rhs) {
   const int64_t n = c->n_act;
   *iters_out = 0;
   *max_rel = 0.0;
@@ -1145,7 +1229,18 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     GP_LAUNCH_CHECK();
     c->launches += 1;
   }
-  {
+  if (rhs) {
+    // a caller-given right-hand-side block: no probes, no Lanczos record
+    if (warm || m_hist != 0) return GP_ERR_INVALID_ARG;
+    const int kqr = kp / 4;
+    const unsigned gr = grid_for(n, kUpdRThreads / kqr, c->num_sms);
+    k_rhs_init_f32<<<gr, kUpdRThreads, 0, c->stream>>>(n, kqr, (const float4*)rhs, (float4*)c->X.p,
+                                                       (float4*)c->R.p, (float4*)c->P.p, (double*)c->part_a.p);
+    k_rhs_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_a.p, (int)gr, k, kp, st, rtol * rtol,
+                                                  max_iter);
+    GP_LAUNCH_CHECK();
+    c->launches += 2;
+  } else {
     unsigned gb = grid_for(n, kThreads, maxb);
     k_init_f32<<<gb, kThreads, 0, c->stream>>>(n, k, kp, y, (const uint32_t*)c->vals.p, (const double*)c->dinv64.p,
                                                seed, nv, (float*)c->X.p, (float*)c->R.p, (float*)c->P.p,
@@ -1302,7 +1397,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
 }
 
 int cg_run_fp64(gp_ctx* c, int k, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
-                int check_every, int* iters_out, double* max_rel) {
+                int check_every, int* iters_out, double* max_rel, const double* rhs) {
   const int64_t n = c->n_act;
   *iters_out = 0;
   *max_rel = 0.0;
@@ -1328,7 +1423,7 @@ int cg_run_fp64(gp_ctx* c, int k, const double* y, int nv, uint64_t seed, int m_
   for (int col = 0; col < k; ++col) {
     double* X = (double*)c->X.p + (int64_t)col * n;
     k_init_f64<<<gb, kThreads, 0, c->stream>>>(n, col, nv, y, (const uint32_t*)c->vals.p,
-                                               (const double*)c->dinv64.p, seed, X, (double*)c->R.p,
+                                               (const double*)c->dinv64.p, rhs, seed, X, (double*)c->R.p,
                                                (double*)c->P.p, (uint32_t*)c->zbits.p, (double*)c->part_a.p, st,
                                                rtol * rtol, max_iter);
     GP_LAUNCH_CHECK();

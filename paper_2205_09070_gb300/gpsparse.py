@@ -39,6 +39,9 @@ GP_FLAG_SPMM_TMA_WIDE = 8
 GP_FLAG_LOGDET_TAYLOR = 16
 GP_FLAG_SPMM_CPASYNC_WIDE = 32
 GP_FLAG_SPMM_WINDOW = 64
+GP_FLAG_FAULT_OOM = 128
+GP_FLAG_FAULT_NOT_SPD = 256
+GP_FLAG_FAULT_NAN = 512
 
 GP_SPMM_CPASYNC = 0
 GP_SPMM_TMA = 1
@@ -50,7 +53,7 @@ SPMM_FLAGS = {"cpasync": GP_FLAG_SPMM_CPASYNC, "tma": GP_FLAG_SPMM_TMA, "tma_wid
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
             "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_predict", "gp_lml", "gp_lml_grad",
-            "gp_lml_grad_batched", "gp_status_string", "gp_sparsity_estimate", "gp_augmented"]
+            "gp_lml_grad_batched", "gp_status_string", "gp_sparsity_estimate", "gp_augmented", "gp_predict_var"]
 
 
 GP_CORE_NONE = 0
@@ -120,6 +123,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gp_get_csr_noalloc.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     lib.gp_solve.argtypes = [vp, dp, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     lib.gp_predict.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
+    lib.gp_predict_var.argtypes = [vp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(Info)]
     lib.gp_lml.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(Info)]
     lib.gp_lml_grad.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double), dp,
@@ -131,7 +135,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gp_status_string.argtypes = [ctypes.c_int]
     lib.gp_status_string.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_destroy", "gp_set_stream", "gp_assemble", "gp_get_csr", "gp_get_csr_noalloc",
-                 "gp_solve", "gp_predict", "gp_lml", "gp_sparsity_estimate", "gp_augmented",
+                 "gp_solve", "gp_predict", "gp_predict_var", "gp_lml", "gp_sparsity_estimate", "gp_augmented",
                  "gp_lml_grad", "gp_lml_grad_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
@@ -326,6 +330,27 @@ class GP:
         self._check(self._lib.gp_predict(self._h, yp, xp, ns, mp, ctypes.byref(o), ctypes.byref(info)),
                     "gp_predict", allow)
         return mean, info.as_dict()
+
+    def predict_var(self, xstar, var=None, opts: Opts | None = None, allow_not_converged=False):
+        """Posterior variance k(x*, x*) - kappa^T K^-1 kappa of the latent
+        function at the test points xstar (n_star x dim) with the last
+        assembled K; var is allocated like the mean in predict if not given."""
+        self._sync_stream()
+        o = opts or default_opts()
+        xp, xk = _ptr(xstar)
+        ns = int(xstar.shape[0])
+        if var is None:
+            if isinstance(xstar, np.ndarray):
+                var = np.zeros(ns, np.float64)
+            else:
+                import torch
+                var = torch.zeros(ns, dtype=torch.float64, device=xstar.device)
+        vp_, vk = _ptr(var)
+        info = Info()
+        allow = (GP_OK, GP_ERR_NOT_CONVERGED) if allow_not_converged else (GP_OK,)
+        self._check(self._lib.gp_predict_var(self._h, xp, ns, vp_, ctypes.byref(o), ctypes.byref(info)),
+                    "gp_predict_var", allow)
+        return var, info.as_dict()
 
     def lml(self, x, y, h, opts: Opts | None = None, allow_not_converged=False):
         self._sync_stream()

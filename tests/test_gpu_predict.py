@@ -133,3 +133,47 @@ def test_predict_when_no_training_point_is_active(G):
     assert info["n_active"] == 0
     assert torch.count_nonzero(mean).item() == 0
     gp.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_predict_var_matches_oracle(G, case, prec):
+    """Posterior variance k(x*, x*) - kappa^T K^-1 kappa (Sec. 2.1,
+    Eq. eq:pred_distr) at 902 test points (15 blocks of 64 right-hand sides,
+    the last ragged) against the oracle's dense solve with full-accuracy K,
+    kappa and prior: within the first-order effect of stopping the block's CG
+    at rtol, rtol |khat| |Khat^-1 khat| (times 4: the recursive residual the
+    CG stops on is not the true one), plus the stored entries' rounding
+    (relative 1e-12 FP64, 1e-5 FP32 of |khat|^T |Khat^-1 khat|) and 1e-12 of
+    the prior variance (an FP64 sum of squared bump values, whose rounding
+    near a bump's edge reaches ~1e-14 relative)."""
+    p = CASES[case]()
+    xs = query_points(p)
+    gp = G.GP(p.dim, p.n1, p.n2, p.beta)
+    gp.assemble(torch.as_tensor(p.x, device="cuda"), p.h, precision=prec)
+    rtol = 1e-10 if prec == "fp64" else 1e-6
+    var, info = gp.predict_var(torch.as_tensor(xs, device="cuda"), opts=G.default_opts(precision=prec, cg_rtol=rtol))
+    v = var.cpu().numpy()
+    kappa = _cross_K_hp(case, p, xs)
+    prior = O.prior_var_hp(xs, p.h, p.dim, p.n1, p.n2, p.beta)
+    Khp = O.dense_K_hp(p.x, p.h, p.dim, p.n1, p.n2, p.beta)
+    ref = O.predict_var(p.x, p.h, xs, p.dim, p.n1, p.n2, p.beta, kappa=kappa, prior=prior, K=Khp)
+    sens, absum = O.predict_var_sensitivity(p.x, p.h, xs, p.dim, p.n1, p.n2, p.beta, kappa=kappa)
+    tol = 4.0 * rtol * sens + (1e-12 if prec == "fp64" else 1e-5) * absum + 1e-12 * prior
+    worst = float(np.max(np.abs(v - ref) / np.where(tol > 0, tol, 1.0)))
+    print(case, prec, "iters", info["iters"], "worst |var - ref| / tol", worst)
+    assert np.all(np.abs(v - ref) <= tol)
+    assert np.all(v[prior == 0.0] == 0.0)       # outside every bump
+    gp.close()
+
+
+def test_predict_var_without_active_training_points_is_the_prior(G):
+    # no training point (N = 0): kappa = 0 and the variance is k(x*, x*)
+    p = W.small_2d(seed=1, n=300)
+    xs = query_points(p, n_new=100)
+    gp = G.GP(p.dim, p.n1, p.n2, p.beta)
+    gp.assemble(torch.zeros((0, p.dim), dtype=torch.float64, device="cuda"), p.h, precision="fp32")
+    var, _ = gp.predict_var(xs)
+    assert np.allclose(var, O.prior_var_hp(xs, p.h, p.dim, p.n1, p.n2, p.beta), rtol=1e-12, atol=0)
+    assert np.any(var > 0)
+    gp.close()
