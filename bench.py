@@ -56,6 +56,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1200)
     ap.add_argument("--n5m", type=int, default=1, help="add the 5M-point leg to the 1M line (0: skip)")
+    ap.add_argument("--batch", type=int, default=1, help="add the 256-instance leg to the 1M line (0: skip)")
     ap.add_argument("--precond-block", type=int, default=None,
                     help="block-Jacobi block size of the preconditioned CG (default: the library's)")
     ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide", "cpasync_wide", "window"],
@@ -281,6 +282,37 @@ def leg_5m(GP, default_opts, spmm_flag, pc_kw, dev, local, stream, a):
     return out
 
 
+def leg_batch(GP, default_opts, dev, local, stream):
+    """The many-instance configuration: 256 independent 2-D GPs, N_i uniform in
+    [1,000, 50,000], each with its own 2 x 4 bumps and r_s, y plus 16 probes,
+    32 Lanczos steps, rtol 1e-6, LML + gradient per instance through
+    gp_lml_grad_batched: instance evaluations/s over one timed batch after one
+    warm-up batch."""
+    import torch
+    from paper_2205_09070_gb300 import workloads as W
+    probs = W.batch_2d(seed=4)
+    offsets = np.concatenate([[0], np.cumsum([q.n for q in probs])])
+    x = torch.as_tensor(np.concatenate([q.x for q in probs]), device=dev)
+    y = torch.as_tensor(np.concatenate([q.y for q in probs]), device=dev)
+    h = np.stack([q.h for q in probs])
+    gp = GP(2, 2, 4, device=local)
+    o = default_opts(precision="fp32", n_probes=16, lanczos_steps=32, cg_rtol=1e-6, seed=2022, max_iter=20000)
+    gp.lml_grad_batched(offsets, x, y, h, o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lml, grad, info = gp.lml_grad_batched(offsets, x, y, h, o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    gp.close()
+    return {"workload": "batch_2d", "n_inst": len(probs), "n_total": int(offsets[-1]),
+            "n_active": info["n_active"], "nnz": info["nnz"], "value": len(probs) / (ms * 1e-3),
+            "unit": "instance evals/s", "ms_per_batch": ms, "max_iters": info["iters"],
+            "path": "worker streams (batch_workers default), each instance through the single-GP path",
+            "lml_finite": bool(np.all(np.isfinite(lml)))}
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     a = args_parse()
@@ -424,6 +456,7 @@ def main():
     scale5m = None
     if a.n5m and p.n == 1_000_000:
         scale5m = leg_5m(GP, default_opts, spmm_flag, pc_kw, dev, local, stream, a)
+    batch256 = leg_batch(GP, default_opts, dev, local, stream) if a.batch and p.n == 1_000_000 else None
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -448,7 +481,7 @@ def main():
                 "assembly": {"nnz_per_s": nnz / (t_asm * 1e-3), "ms": t_asm, "fill_kernel_ms": t_fill},
                 "adjoint_kernel_ms": t_adj,
                 "roofline": roofline, "rooflines": rooflines, "clocks": clocks, "gpu_launches": launches,
-                "e2e": e2e, "fp64_path": fp64, "scale_5m": scale5m, "cpu_baseline": cpu}
+                "e2e": e2e, "fp64_path": fp64, "scale_5m": scale5m, "batch_256": batch256, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     gp.close()
     if dist:

@@ -186,3 +186,34 @@ def test_block_jacobi_128_with_the_most_probes(G):
     assert i128["quad_form"] == pytest.approx(i32["quad_form"], rel=1e-5)
     assert i128["logdet"] == pytest.approx(i32["logdet"], rel=1e-5)
     gp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_instances_match_the_oracle(G, prec):
+    """Independent GPs of the many-instance configuration (2-D, 2 x 4 bumps
+    each with its own hyperparameters, r_s U(0.02, 0.08), y plus 16 probes),
+    sizes from 1 to 1,500 points, through gp_lml_grad_batched: every instance's
+    LML pieces against the oracle's same-probe estimator, and its gradient
+    within the first-order solver bound."""
+    from oracle import gp_oracle as O
+    from helpers import grad_ok
+    probs = W.batch_2d(seed=41, n_inst=5, n_range=(200, 1500))
+    probs[2] = W.batch_2d(seed=42, n_inst=1, n_range=(1, 1))[0]          # N = 1
+    offsets = np.concatenate([[0], np.cumsum([q.n for q in probs])])
+    x = np.concatenate([q.x for q in probs])
+    y = np.concatenate([q.y for q in probs])
+    h = np.stack([q.h for q in probs])
+    nv, m, seed = 16, 32, 7
+    rtol = 1e-10 if prec == "fp64" else 1e-6
+    o = G.default_opts(precision=prec, n_probes=nv, lanczos_steps=m, cg_rtol=rtol, seed=seed)
+    gp = G.GP(2, 2, 4)
+    lml_b, grad_b, info = gp.lml_grad_batched(offsets, torch.as_tensor(x, device="cuda"),
+                                              torch.as_tensor(y, device="cuda"), h, o)
+    for k, q in enumerate(probs):
+        ref, gref, rinfo = O.lml_grad_same_probes(q.x, q.y, q.h, 2, 2, 4, nv, m, seed, with_bounds=True)
+        # the estimator's pieces enter ln L; with N = 1 the log-determinant is exact
+        assert lml_b[k] == pytest.approx(ref, rel=1e-9 if prec == "fp64" else 1e-5, abs=1e-9), (k, q.n)
+        ok, worst = grad_ok(grad_b[k], gref, rinfo, rtol, 2.0)
+        print(prec, "instance", k, "N", q.n, "grad worst / bound", worst)
+        assert ok, (k, q.n, worst)
+    gp.close()
