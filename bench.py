@@ -141,23 +141,26 @@ def spmm_kernel_name(variant: int, kp: int) -> str:
 
 
 WINDOW_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "window.cu")
-SPMM_REGIONS = {  # source file and region of each SpMM form (first marker inclusive, second exclusive)
-    "k_bspmm_f32": (SPMM_SOURCE, "// A: Q = Khat P on the 8x1 block CSR.",
-                    "// ---------------------------------------------------------------- TMA form"),
-    "k_bspmm_tma": (SPMM_SOURCE, "// ---------------------------------------------------------------- TMA form",
-                    "// ---------------------------------------------------------------- wide cp.async form"),
-    "k_bspmm_f32w": (SPMM_SOURCE, "// ---------------------------------------------------------------- wide cp.async form",
-                     "// ---------------------------------------------------------------- host side"),
-    "k_wspmm": (WINDOW_SOURCE, "// ------------------------------------------------------------------ SpMM",
-                "typedef void (*WinFn)"),
+_S_A = "// A: Q = Khat P on the 8x1 block CSR."
+_S_TMA = "// ---------------------------------------------------------------- TMA form"
+_S_WIDE = "// ---------------------------------------------------------------- wide cp.async form"
+_S_HOST = "// ---------------------------------------------------------------- host side"
+# source file and regions (first marker inclusive, second exclusive) of each SpMM form: its kernel
+# and the helpers it calls
+SPMM_REGIONS = {
+    "k_bspmm_f32": (SPMM_SOURCE, [(_S_A, _S_TMA)]),
+    "k_bspmm_tma": (SPMM_SOURCE, [(_S_A, _S_TMA), (_S_TMA, _S_WIDE)]),
+    "k_bspmm_f32w": (SPMM_SOURCE, [(_S_A, _S_TMA), (_S_WIDE, _S_HOST)]),
+    "k_wspmm": (WINDOW_SOURCE, [("// ------------------------------------------------------------------ SpMM",
+                                 "typedef void (*WinFn)")]),
 }
 
 
 def spmm_source_sha(kernel: str) -> str:
-    """sha256 of the source region of the SpMM form `kernel` (its kernel and helpers)."""
-    path, a, b = SPMM_REGIONS[kernel.split("<")[0]]
+    """sha256 of the source regions of the SpMM form `kernel` (its kernel and helpers)."""
+    path, regions = SPMM_REGIONS[kernel.split("<")[0]]
     src = open(path).read()
-    return hashlib.sha256(src[src.index(a):src.index(b)].encode()).hexdigest()
+    return hashlib.sha256("".join(src[src.index(a):src.index(b)] for a, b in regions).encode()).hexdigest()
 
 
 def traffic_record(kernel: str, kp: int):

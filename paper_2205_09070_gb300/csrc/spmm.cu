@@ -34,15 +34,17 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // A: Q = Khat P on the 8x1 block CSR.  Each CTA owns a contiguous run of
 // block rows holding an equal share of the stored blocks; its warps take the
-// rows round-robin (neighbouring block rows gather overlapping P rows, which
-// then hit in L1), and each warp streams its rows' blocks in chunks of 32
-// through a double-buffered shared-memory stage: while the
+// rows round-robin (neighbouring block rows gather overlapping P rows close
+// together in time, while they are in L2), and each warp streams its rows'
+// blocks in chunks through a double-buffered shared-memory stage: while the
 // warp computes chunk c, cp.async copies the P rows (kp floats) and the 8
 // values of chunk c+1 into the other buffer, and the column indices of chunk
 // c+2 are already being loaded.  Compute: the warp's lanes form NG = 32/G
 // groups of G lanes (one float4 of the kp = 4G columns per lane); a group
 // takes every NG-th block of the chunk and applies its P row to the 8 rows
-// of the block row (8 float4 accumulators per lane).
+// of the block row (8 float4 accumulators per lane).  A chunk holds
+// NG floor(32 / NG) blocks, a whole number of warp steps, so that no step
+// multiplies an empty slot in the middle of a block row.
 // Smallest block row b in [0, nblk] whose first stored block is >= target
 // (brp ascending, brp[nblk] = total).  Every block row then belongs to
 // exactly one CTA's share.
@@ -61,9 +63,11 @@ constexpr int kSpmmWarps = kSpmmThreads / 32;
 constexpr int kBR = 8;
 constexpr int kChunk = 32;
 
+// The stage copies bypass the L1 (.cg): allocating the gathered P rows there
+// as well cost more L1 throughput than its hits saved.
 __device__ inline void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -74,9 +78,10 @@ struct ChunkPos {
   int64_t bb, base;
 };
 
+template <int CH = kChunk>
 __device__ inline ChunkPos next_chunk(ChunkPos c, const int64_t* __restrict__ brp, int64_t b1) {
   const int64_t e = __ldg(brp + c.bb + 1);
-  if (c.base + kChunk < e) return {c.bb, c.base + kChunk};
+  if (c.base + CH < e) return {c.bb, c.base + CH};
   const int64_t nb = c.bb + kSpmmWarps;
   if (nb >= b1) return {b1, 0};
   return {nb, __ldg(brp + nb)};
@@ -94,12 +99,19 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   constexpr int NG = 32 / G;
   constexpr int KP = 4 * G;
   constexpr int kStage = kChunk * (KP + kBR);  // floats per stage buffer
+  // a chunk holds a whole number of warp steps; lane l copies piece l % G of
+  // entry l / G of each group of EPI entries
+  constexpr int CH = NG * (kChunk / NG);
+  constexpr int kSteps = CH / NG;
+  constexpr int EPI = 32 / G;
+  constexpr int NIS = (CH + EPI - 1) / EPI;
   extern __shared__ float4 smem_f4[];
   float* stage = (float*)smem_f4 + (size_t)(threadIdx.x >> 5) * 2 * kStage;
   __shared__ double sh[kSpmmWarps][KP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane - grp * G;
   const bool act = grp < NG;
+  const bool lcopy = grp < EPI;  // EPI == NG: the copy layout is the compute layout
   gpd::Dot2 pq0, pq1, pq2, pq3;
   // Work split by stored blocks, not by block rows (cluster cores hold many
   // times more blocks per row than the background).
@@ -114,14 +126,15 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     auto issue = [&](ChunkPos c, int jl, int buf) {
       if (c.bb < b1) {
         const int64_t e = __ldg(brp + c.bb + 1);
-        const int cnt = (int)min((int64_t)kChunk, e - c.base);
+        const int cnt = (int)min((int64_t)CH, e - c.base);
         float* dst = stage + buf * kStage;
+        float* dl = dst + grp * KP + 4 * gl;
+        const float4* pl = P + gl;
 #pragma unroll
-        for (int i = 0; i < G; ++i) {
-          const int q = lane + 32 * i;  // piece q: entry q / G, slot q % G
-          const int ent = q / G;
+        for (int i = 0; i < NIS; ++i) {
+          const int ent = i * EPI + grp;
           const int j = __shfl_sync(kFull, jl, ent < 32 ? ent : 31);
-          if (ent < cnt) cp_async16(dst + ent * KP + 4 * (q - ent * G), P + (int64_t)j * G + (q - ent * G));
+          if (lcopy && ent < cnt) cp_async16(dl + i * EPI * KP, pl + (int64_t)j * G);
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -134,10 +147,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     auto col_of = [&](ChunkPos c) -> int {
       if (c.bb >= b1) return 0;
       const int64_t idx = c.base + lane;
-      return idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
+      return lane < CH && idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
     };
     ChunkPos cur{b0, __ldg(brp + b0)};
-    ChunkPos nx1 = next_chunk(cur, brp, b1);
+    ChunkPos nx1 = next_chunk<CH>(cur, brp, b1);
     issue(cur, col_of(cur), 0);
     int j1 = col_of(nx1);
     // accumulators as float2 pairs (columns x,y and z,w of the lane's float4)
@@ -147,16 +160,15 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
     for (int r = 0; r < 2 * kBR; ++r) acc[r] = make_float2(0.f, 0.f);
     int buf = 0;
     while (cur.bb < b1) {
-      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp, b1) : nx1;
+      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk<CH>(nx1, brp, b1) : nx1;
       issue(nx1, j1, buf ^ 1);            // copies of chunk c+1 in flight
       const int j2 = col_of(nx2);          // indices of chunk c+2 in flight
       cp_async_wait<1>();                  // chunk c has landed
       __syncwarp();
       const int64_t e = __ldg(brp + cur.bb + 1);
-      const int cnt = (int)min((int64_t)kChunk, e - cur.base);
+      const int cnt = (int)min((int64_t)CH, e - cur.base);
       const float* sp = stage + buf * kStage;
       const float* sv = sp + kChunk * KP;
-      constexpr int kSteps = (kChunk + NG - 1) / NG;
 #pragma unroll 2
       for (int t = 0; t < kSteps; ++t) {
         const int src = t * NG + grp;
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
         }
       }
       __syncwarp();  // buffer `buf` may be refilled from the next iteration on
-      if (cur.base + kChunk >= e) {
+      if (cur.base + CH >= e) {
         // last chunk of block row cur.bb: group 0 adds the other groups' sums
 #pragma unroll
         for (int r = 0; r < 2 * kBR; ++r) {
@@ -519,6 +531,13 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
   constexpr int kStage = kChunk * (KP + kBR);  // floats per stage buffer
   constexpr int RP = cpw_rows_per_pass(NG, KQ);
   constexpr int M = 32 / KQ;
+  // a chunk holds a whole number of warp steps (30 blocks at NG = 10)
+  constexpr int CH = NG * (kChunk / NG);
+  constexpr int kSteps = CH / NG;
+  // copy layout: lane l copies piece l % KQ of entry l / KQ of each group of
+  // EPI entries, so its shared-memory offset is fixed for the whole run
+  constexpr int EPI = 32 / KQ;
+  constexpr int NIS = (CH + EPI - 1) / EPI;
   extern __shared__ float4 smem_f4[];
   float* stage = (float*)smem_f4 + (size_t)(threadIdx.x >> 5) * 2 * kStage;
   __shared__ double shp[kSpmmWarps][32][4];
@@ -526,6 +545,8 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
   const int grp = lane / G, gl = lane - grp * G;
   const bool act = grp < NG;
   const int slot = lane < M * KQ ? lane % KQ : -1;
+  const int le = lane / KQ, lp = lane - le * KQ;
+  const bool lcopy = le < EPI;
   gpd::Dot2 pq0, pq1, pq2, pq3;
   const int64_t nent = brp[nblk];
   const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * blockIdx.x / gridDim.x);
@@ -537,14 +558,15 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
     auto issue = [&](ChunkPos c, int jl, int buf) {
       if (c.bb < b1) {
         const int64_t e = __ldg(brp + c.bb + 1);
-        const int cnt = (int)min((int64_t)kChunk, e - c.base);
+        const int cnt = (int)min((int64_t)CH, e - c.base);
         float* dst = stage + buf * kStage;
+        float* dl = dst + le * KP + 4 * lp;
+        const float4* pl = P + lp;
 #pragma unroll
-        for (int i = 0; i < KQ; ++i) {
-          const int q = lane + 32 * i;  // piece q: entry q / KQ, slot q % KQ
-          const int ent = q / KQ;
+        for (int i = 0; i < NIS; ++i) {
+          const int ent = i * EPI + le;
           const int j = __shfl_sync(kFull, jl, ent < 32 ? ent : 31);
-          if (ent < cnt) cp_async16(dst + ent * KP + 4 * (q - ent * KQ), P + (int64_t)j * KQ + (q - ent * KQ));
+          if (lcopy && ent < cnt) cp_async16(dl + i * EPI * KP, pl + (int64_t)j * KQ);
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -557,10 +579,10 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
     auto col_of = [&](ChunkPos c) -> int {
       if (c.bb >= b1) return 0;
       const int64_t idx = c.base + lane;
-      return idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
+      return lane < CH && idx < __ldg(brp + c.bb + 1) ? __ldg(bcol + idx) : 0;
     };
     ChunkPos cur{b0, __ldg(brp + b0)};
-    ChunkPos nx1 = next_chunk(cur, brp, b1);
+    ChunkPos nx1 = next_chunk<CH>(cur, brp, b1);
     issue(cur, col_of(cur), 0);
     int j1 = col_of(nx1);
     float2 acc[kBR][2 * LW];
@@ -570,17 +592,16 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
       for (int u = 0; u < 2 * LW; ++u) acc[r][u] = make_float2(0.f, 0.f);
     int buf = 0;
     while (cur.bb < b1) {
-      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk(nx1, brp, b1) : nx1;
+      const ChunkPos nx2 = nx1.bb < b1 ? next_chunk<CH>(nx1, brp, b1) : nx1;
       issue(nx1, j1, buf ^ 1);            // copies of chunk c+1 in flight
       const int j2 = col_of(nx2);          // indices of chunk c+2 in flight
       cp_async_wait<1>();                  // chunk c has landed
       __syncwarp();
       const int64_t e = __ldg(brp + cur.bb + 1);
-      const int cnt = (int)min((int64_t)kChunk, e - cur.base);
+      const int cnt = (int)min((int64_t)CH, e - cur.base);
       const float* sp = stage + buf * kStage;
       const float* sv = sp + kChunk * KP;
-      constexpr int kSteps = (kChunk + NG - 1) / NG;
-#pragma unroll 2
+#pragma unroll
       for (int t = 0; t < kSteps; ++t) {
         const int src = t * NG + grp;
         if (act && src < cnt) {
@@ -603,7 +624,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
         }
       }
       __syncwarp();
-      if (cur.base + kChunk >= e) {
+      if (cur.base + CH >= e) {
         // last chunk of block row cur.bb: groups write their partial rows to
         // the consumed buffer, then lane l sums slot l % KQ of rows l / KQ + M i
         float4* scr = (float4*)(stage + buf * kStage);
@@ -823,6 +844,7 @@ void spmm_launch(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st) {
 }
 
 void spmm_launch_io(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st, const float* in, float* out) {
+  if (p.variant != GP_SPMM_CPASYNC && p.variant != GP_SPMM_CPASYNC_WIDE) return;
   int64_t n = c->n_act, nblk = c->nblk;
   const int64_t* brp = (const int64_t*)c->brp.p;
   const int32_t* bcol = (const int32_t*)c->bcol.p;
