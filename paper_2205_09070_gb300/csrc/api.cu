@@ -423,7 +423,7 @@ int gp_destroy(gp_ctx* c) {
   gp::DevBuf* bufs[] = {&c->x_in,   &c->y_in,   &c->out_tmp,    &c->bump,      &c->mask0,     &c->F0,
                         &c->pos,    &c->keys,   &c->vals,       &c->keys2,     &c->vals2,     &c->hist,
                         &c->hist_scan, &c->scan_part, &c->cells, &c->perm,     &c->skey,      &c->cellc,
-                        &c->xr,     &c->xs,     &c->Fs,  &c->Fs64,  &c->smask,     &c->dinv,      &c->dinv64,
+                        &c->xr,     &c->xs,     &c->xhl, &c->Fs,  &c->Fhl,  &c->smask,     &c->dinv,      &c->dinv64,
                         &c->cnt,    &c->row_ptr, &c->col,       &c->val,       &c->X,         &c->R,
                         &c->P,      &c->Q,      &c->zbits,      &c->part_a,    &c->part_b,    &c->part_c,
                         &c->hist_alpha, &c->hist_beta, &c->g,   &c->grad_part, &c->grad_bump, &c->cg,

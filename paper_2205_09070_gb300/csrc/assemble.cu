@@ -264,7 +264,12 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restr
 // ------------------------------------------------------------------ sorted points
 // For sorted position p: original index, cell coordinates, FP32 coordinates
 // relative to the own cell (units of h), FP64 coordinates, F and mask in
-// Morton order, D^-1/2, cell table boundaries, and sum ln D.
+// Morton order, D^-1/2, cell table boundaries, and sum ln D.  The FP32 path
+// also gets the coordinates and Fhat = sqrt(A C) D^-1/2 F as double-float
+// pairs (hi = the FP32 rounding, lo = the FP32 rounding of the rest), which
+// carry 48 bits.  |Fhat| <= 1 (D >= A C F^2), and a stored entry is
+// k~ sum_m Fhat_pm Fhat_jm with k~ <= 1, so the products of the table are at
+// least the size of the entry and stay in FP32's normal range when it does.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ x, int64_t n_act,
                                                      const uint32_t* __restrict__ skey,
@@ -273,7 +278,8 @@ __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ 
                                                      const uint32_t* __restrict__ mask0, int n1, double AC,
                                                      double sigma2, int4* __restrict__ cellc,
                                                      float4* __restrict__ xr, double* __restrict__ xs,
-                                                     T* __restrict__ Fs, double* __restrict__ Fs64,
+                                                     float2* __restrict__ xhl, T* __restrict__ Fs,
+                                                     float2* __restrict__ Fhl,
                                                      uint32_t* __restrict__ smask,
                                                      T* __restrict__ dinv, double* __restrict__ dinv64,
                                                      int2* __restrict__ cells, double* __restrict__ part,
@@ -291,18 +297,29 @@ __global__ void __launch_bounds__(kThreads) k_sorted(const double* __restrict__ 
       double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h);
       r[k] = (float)(u - (double)c[k]);
       xs[p * g.dim + k] = xi[k];
+      if (xhl) {
+        const float hi = (float)xi[k];
+        xhl[p * g.dim + k] = make_float2(hi, (float)(xi[k] - (double)hi));
+      }
     }
     xr[p] = make_float4(r[0], r[1], r[2], 0.f);
     double sF = 0.0;
     for (int m = 0; m < n1; ++m) {
       double f = F0[(int64_t)i * n1 + m];
       Fs[p * n1 + m] = (T)f;
-      if (Fs64) Fs64[p * n1 + m] = f;
       sF += f * f;
     }
     smask[p] = mask0[i];
     const double D = AC * sF + sigma2;
     const double di = 1.0 / sqrt(D);
+    if (Fhl) {
+      const double sc = sqrt(AC) * di;
+      for (int m = 0; m < n1; ++m) {
+        const double f = F0[(int64_t)i * n1 + m] * sc;
+        const float hi = (float)f;
+        Fhl[p * n1 + m] = make_float2(hi, (float)(f - (double)hi));
+      }
+    }
     dinv64[p] = di;
     dinv[p] = (T)di;
     acc += log(D);
@@ -344,8 +361,9 @@ struct PairArgs {
   const uint32_t* mask;
   const float4* xr;
   const double* xs;
+  const float2* xhl;    // FP32 path: coordinates as double-float pairs
   const void* Fs;
-  const double* Fs64;   // the sorted bump table in FP64 (entry values)
+  const float2* Fhl;    // FP32 path: the sorted bump table as double-float pairs
   const void* dinv;
   const double* dinv64; // D^-1/2 in FP64 (entry values)
   const int64_t* row_ptr;
@@ -360,6 +378,9 @@ struct PairArgs {
   double AC;     // A * C
   double sigma2;
   double inv2l2; // 1 / (2 l^2) of the squared-exponential core, 0 without a core
+  // the same constants for the FP32 entry values (pairs: hi + lo)
+  float rs2h, rs2lo, inv_rs2f, sigma2f, il2h, il2lo;
+  float s2min;   // FP32 path: entries with s^2 below this take the FP64 route
 };
 
 __device__ inline int warp_incl_scan_int(int v) {
@@ -480,37 +501,107 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
             hit = e2 < a.rs2;
           }
           if (FILL && hit) {
-            // the entry's value from the FP64 inputs: rho^2 and s^2 = 1 - rho^2
-            // in FP64 (s^2 without cancellation near the edge), the sum over
-            // the shared functions in FP64 (compensated on the FP64 path),
-            // one rounding to T at the end
-            if (e2 < 0.0) e2 = dist2_fp64(a.xs, a.dim, p, j);
-            double s2 = (a.rs2 - e2) * a.inv_rs2;
-            if (s2 < (sizeof(T) == 4 ? 1e-6 : 1e-2))
-              s2 = gpd::one_minus_ratio(a.xs + p * a.dim, a.xs + (int64_t)j * a.dim, a.dim, a.rs2, a.rs2l);
-            const double rho2 = e2 * a.inv_rs2;
-            double kst = 0.0;
-            if (s2 > 0.0) {
-              if (sizeof(T) == 4) kst = (double)gpd::kstat_unit_f((float)rho2, (float)s2);
-              else kst = gpd::kstat_unit_d(rho2, s2);
-            }
-            const double* Fp = a.Fs64 + p * a.n1;
-            const double* Fj = a.Fs64 + (int64_t)j * a.n1;
-            double S = 0.0;
-            if (sizeof(T) == 4) {
-              uint32_t common = mi & mj;
-              while (common) {
-                const int m = __ffs(common) - 1;
-                common &= common - 1u;
-                S = fma(Fp[m], Fj[m], S);
+            bool via64 = sizeof(T) == 8;
+            if constexpr (sizeof(T) == 4) {
+              // FP32 path: FP32 arithmetic on double-float inputs.  d^2 as a
+              // pair from exact coordinate differences (TwoSum) and exact
+              // squares (TwoProduct), r_s^2 - d^2 on the pair (no
+              // cancellation near the edge), so s^2 and rho^2 reach the
+              // stationary kernel with one FP32 rounding, as from FP64; the
+              // sum over the shared functions compensated on the double-float
+              // Fhat = sqrt(A C) D^-1/2 F (so it is already the stored entry's
+              // size), the core factor last.  Entries with s^2 below s2min (where the pair's
+              // own error would show) take the FP64 route.
+              float eh = 0.f, el = 0.f;
+              for (int k = 0; k < a.dim; ++k) {
+                const float2 u = a.xhl[p * a.dim + k], w = a.xhl[(int64_t)j * a.dim + k];
+                float t, e;
+                gpd::two_sum_f(u.x, -w.x, t, e);
+                e += u.y - w.y;
+                float sq, sqe;
+                gpd::two_prod_f(t, t, sq, sqe);
+                sqe = fmaf(2.f * t, e, fmaf(e, e, sqe));
+                float sum, se;
+                gpd::two_sum_f(eh, sq, sum, se);
+                eh = sum;
+                el += se + sqe;
               }
-            } else {
-              S = gpd::dot2_bits(Fp, Fj, mi & mj);
+              float nh, nl;
+              gpd::two_sum_f(a.rs2h, -eh, nh, nl);
+              nl += a.rs2lo - el;
+              const float num = nh + nl;  // r_s^2 - d^2
+              if (num >= a.s2min * a.rs2h) {
+                const float s2 = num * a.inv_rs2f;
+                const float rho2 = (eh + el) * a.inv_rs2f;  // el carries the differences' low parts
+                const float kst = gpd::kstat_unit_f(rho2, s2);
+                const float2* Fp = a.Fhl + p * a.n1;
+                const float2* Fj = a.Fhl + (int64_t)j * a.n1;
+                float Sh = 0.f, Sl = 0.f;
+                uint32_t common = mi & mj;
+                while (common) {
+                  const int m = __ffs(common) - 1;
+                  common &= common - 1u;
+                  const float2 f = Fp[m], g2 = Fj[m];
+                  float ph, pe;
+                  gpd::two_prod_f(f.x, g2.x, ph, pe);
+                  pe = fmaf(f.x, g2.y, fmaf(f.y, g2.x, pe));
+                  float t, te;
+                  gpd::two_sum_f(Sh, ph, t, te);
+                  Sh = t;
+                  Sl += te + pe;
+                }
+                float vv = kst * (Sh + Sl);
+                if (j == p) {
+                  const float dp = ((const float*)a.dinv)[p];
+                  vv = fmaf(a.sigma2f * dp, dp, vv);
+                } else if (a.il2h > 0.f) {
+                  // t = d^2 / (2 l^2) as th + tl, exp(-t) = expf(-th) (1 - tl)
+                  const float th = eh * a.il2h;
+                  const float tl = fmaf(eh, a.il2h, -th) + fmaf(el, a.il2h, eh * a.il2lo);
+                  vv *= expf(-th) * (1.f - tl);
+                }
+                v = (T)vv;
+              } else {
+                via64 = true;
+              }
             }
-            double vv = a.AC * kst * S;
-            if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
-            if (j == p) vv += a.sigma2;
-            v = (T)(vv * a.dinv64[p] * a.dinv64[j]);
+            if (via64) {
+              // FP64 route: rho^2 and s^2 = 1 - rho^2 in FP64 (s^2 without
+              // cancellation near the edge), the sum over the shared functions
+              // in FP64 (compensated on the FP64 path), one rounding to T
+              if (e2 < 0.0) e2 = dist2_fp64(a.xs, a.dim, p, j);
+              double s2 = (a.rs2 - e2) * a.inv_rs2;
+              if (s2 < (sizeof(T) == 4 ? 1e-6 : 1e-2))
+                s2 = gpd::one_minus_ratio(a.xs + p * a.dim, a.xs + (int64_t)j * a.dim, a.dim, a.rs2, a.rs2l);
+              const double rho2 = e2 * a.inv_rs2;
+              double kst = 0.0;
+              if (s2 > 0.0) {
+                if (sizeof(T) == 4) kst = (double)gpd::kstat_unit_f((float)rho2, (float)s2);
+                else kst = gpd::kstat_unit_d(rho2, s2);
+              }
+              if constexpr (sizeof(T) == 4) {
+                // the scaled table: S is already A C D_p^-1/2 D_j^-1/2 sum F F
+                double S = 0.0;
+                uint32_t common = mi & mj;
+                while (common) {
+                  const int m = __ffs(common) - 1;
+                  common &= common - 1u;
+                  const float2 f = a.Fhl[p * a.n1 + m], g2 = a.Fhl[(int64_t)j * a.n1 + m];
+                  S = fma((double)f.x + (double)f.y, (double)g2.x + (double)g2.y, S);
+                }
+                double vv = kst * S;
+                if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
+                if (j == p) vv += a.sigma2 * a.dinv64[p] * a.dinv64[p];
+                v = (T)vv;
+              } else {
+                const double S =
+                    gpd::dot2_bits((const double*)a.Fs + p * a.n1, (const double*)a.Fs + (int64_t)j * a.n1, mi & mj);
+                double vv = a.AC * kst * S;
+                if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
+                if (j == p) vv += a.sigma2;
+                v = (T)(vv * a.dinv64[p] * a.dinv64[j]);
+              }
+            }
           }
         }
       }
@@ -873,10 +964,14 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   GP_CHECK(gp::ensure(c, c->xr, (size_t)n_act * sizeof(float4)));
   GP_CHECK(gp::ensure(c, c->xs, (size_t)n_act * dim * sizeof(double)));
   GP_CHECK(gp::ensure(c, c->Fs, (size_t)n_act * n1 * sizeof(T)));
-  // FP32 path: an FP64 copy of the sorted bump table for the entry values
-  // (the FP64 path reads Fs itself)
-  if (sizeof(T) == 4) GP_CHECK(gp::ensure(c, c->Fs64, (size_t)n_act * n1 * sizeof(double)));
-  double* Fs64 = sizeof(T) == 4 ? (double*)c->Fs64.p : nullptr;
+  // FP32 path: coordinates and the sorted bump table as double-float pairs
+  // for the entry values (the FP64 path reads xs and Fs themselves)
+  if (sizeof(T) == 4) {
+    GP_CHECK(gp::ensure(c, c->xhl, (size_t)n_act * dim * sizeof(float2)));
+    GP_CHECK(gp::ensure(c, c->Fhl, (size_t)n_act * n1 * sizeof(float2)));
+  }
+  float2* xhl = sizeof(T) == 4 ? (float2*)c->xhl.p : nullptr;
+  float2* Fhl = sizeof(T) == 4 ? (float2*)c->Fhl.p : nullptr;
   GP_CHECK(gp::ensure(c, c->smask, (size_t)n_act * sizeof(uint32_t)));
   GP_CHECK(gp::ensure(c, c->dinv, (size_t)n_act * sizeof(T)));
   GP_CHECK(gp::ensure(c, c->dinv64, (size_t)n_act * sizeof(double)));
@@ -887,7 +982,7 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     k_sorted<T><<<gb, kThreads, 0, c->stream>>>(x, n_act, (const uint32_t*)c->keys.p, (const uint32_t*)c->vals.p, g,
                                                 (const double*)c->F0.p, (const uint32_t*)c->mask0.p, n1, AC,
                                                 c->sigma2, (int4*)c->cellc.p, (float4*)c->xr.p, (double*)c->xs.p,
-                                                (T*)c->Fs.p, Fs64, (uint32_t*)c->smask.p, (T*)c->dinv.p,
+                                                xhl, (T*)c->Fs.p, Fhl, (uint32_t*)c->smask.p, (T*)c->dinv.p,
                                                 (double*)c->dinv64.p, (int2*)c->cells.p, (double*)c->part_b.p, s);
     GP_LAUNCH_CHECK();
     c->launches += 1;
@@ -907,8 +1002,9 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   pa.mask = (const uint32_t*)c->smask.p;
   pa.xr = (const float4*)c->xr.p;
   pa.xs = (const double*)c->xs.p;
+  pa.xhl = xhl;
   pa.Fs = c->Fs.p;
-  pa.Fs64 = sizeof(T) == 4 ? (const double*)Fs64 : (const double*)c->Fs.p;
+  pa.Fhl = Fhl;
   pa.dinv = c->dinv.p;
   pa.dinv64 = (const double*)c->dinv64.p;
   pa.cnt = (int32_t*)c->cnt.p;
@@ -920,6 +1016,22 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   pa.AC = AC;
   pa.sigma2 = c->sigma2;
   pa.inv2l2 = c->core == GP_CORE_SQEXP ? 1.0 / (2.0 * c->ell * c->ell) : 0.0;
+  // FP32 entry values: the constants as FP32 pairs
+  pa.rs2h = (float)pa.rs2;
+  pa.rs2lo = (float)((pa.rs2 - (double)pa.rs2h) + pa.rs2l);
+  pa.inv_rs2f = (float)pa.inv_rs2;
+  pa.sigma2f = (float)c->sigma2;
+  pa.il2h = (float)pa.inv2l2;
+  pa.il2lo = (float)(pa.inv2l2 - (double)pa.il2h);
+  {
+    // the double-float d^2 carries an absolute error of about 2^-45 X r_s
+    // (X the largest coordinate magnitude: the pairs hold 48 bits of each
+    // coordinate); s^2 = 1 - rho^2 keeps FP32 accuracy while it exceeds
+    // 2^-23 X / r_s, so the FP32 route takes s^2 >= max(2^-16, 2^-20 X / r_s)
+    double X = 0.0;
+    for (int k = 0; k < dim; ++k) X = fmax(X, fmax(fabs(g.lo[k]), fabs(g.lo[k] + g.G[k] * g.h)));
+    pa.s2min = (float)fmax(std::ldexp(1.0, -16), std::ldexp(X / c->r_s, -20));
+  }
   const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
   k_pair<T, false><<<gw, kThreads, 0, c->stream>>>(pa);
   GP_LAUNCH_CHECK();

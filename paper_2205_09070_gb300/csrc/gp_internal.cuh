@@ -144,7 +144,7 @@ struct gp_ctx {
   gp::DevBuf mask0, F0, pos;
   gp::DevBuf keys, vals, keys2, vals2, hist, hist_scan, scan_part;
   gp::DevBuf cells;
-  gp::DevBuf perm, skey, cellc, xr, xs, Fs, Fs64, smask, dinv, dinv64;
+  gp::DevBuf perm, skey, cellc, xr, xs, xhl, Fs, Fhl, smask, dinv, dinv64;
   gp::DevBuf cnt, row_ptr, col, val;
   // 8x1 block CSR of the FP32 path (rows 8b..8b+7 per block row)
   gp::DevBuf bcnt, brp, bcol, bmask, bval;
@@ -451,6 +451,17 @@ template <> struct Real<double> {
   __device__ static double kstat(double r2, double s2) { return kstat_unit_d(r2, s2); }
   __device__ static double dk(double r2, double s2) { return atanh_minus_s_d(r2, s2); }
 };
+
+// The same error-free transformations in FP32: a + b = s + e, a * b = p + e.
+__device__ inline void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+__device__ inline void two_prod_f(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
 
 // Compensated FP32 accumulation of products: the product's rounding error
 // (FMA) and each addition's rounding error (Knuth's TwoSum) are carried in a
