@@ -34,6 +34,7 @@ struct AdjArgs {
   const int4* cellc;
   const float4* xr;
   const double* xs;
+  const float2* xhl;     // FP32 path: coordinates as double-float pairs
   const void* Fs;
   const uint32_t* mask;
   const void* dinv;
@@ -47,6 +48,7 @@ struct AdjArgs {
   double C;
   double inv2l2;            // 1 / (2 l^2) of the squared-exponential core, 0 without one
   double inv_l;             // 1 / l
+  float rs2h, rs2lo, inv_rs2f;  // FP32 path: r_s^2 as a pair, 1 / r_s^2
 };
 
 __device__ inline double warp_sum_d(double v) {
@@ -98,13 +100,12 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(AdjArgs a) {
         rho2 = (T)r2;
         s2 = (T)(1.0f - r2);
         if (s2 < (T)0.1) {
-          double e2 = 0.0;
-          for (int k = 0; k < a.dim; ++k) {
-            const double t = a.xs[p * a.dim + k] - a.xs[(int64_t)j * a.dim + k];
-            e2 += t * t;
-          }
-          rho2 = (T)(e2 / a.rs2);
-          s2 = (T)((a.rs2 - e2) / a.rs2);
+          // near the edge: d^2 and r_s^2 - d^2 from the double-float
+          // coordinates (as in the pair fill), in FP32 arithmetic
+          float eh, el;
+          gpd::dist2_pair_f(a.xhl, a.dim, p, j, eh, el);
+          rho2 = (T)((eh + el) * a.inv_rs2f);
+          s2 = (T)(gpd::pair_gap_f(a.rs2h, a.rs2lo, eh, el) * a.inv_rs2f);
         }
       } else {
         double e2 = 0.0;
@@ -331,6 +332,10 @@ int run_adjoint(gp_ctx* c, int nv, int64_t ld) {
   const double sc = (c->grid.h / c->r_s) * (c->grid.h / c->r_s);
   a.scale = (float)sc;
   a.rs2 = c->r_s * c->r_s;
+  a.xhl = (const float2*)c->xhl.p;
+  a.rs2h = (float)a.rs2;
+  a.rs2lo = (float)((a.rs2 - (double)a.rs2h) + fma(c->r_s, c->r_s, -a.rs2));
+  a.inv_rs2f = (float)(1.0 / a.rs2);
   a.C = kPrefactor;
   a.AC = c->A * kPrefactor;
   a.dk_coef = c->A * 6.0 * kPrefactor / c->r_s;

@@ -512,24 +512,9 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
               // Fhat = sqrt(A C) D^-1/2 F (so it is already the stored entry's
               // size), the core factor last.  Entries with s^2 below s2min (where the pair's
               // own error would show) take the FP64 route.
-              float eh = 0.f, el = 0.f;
-              for (int k = 0; k < a.dim; ++k) {
-                const float2 u = a.xhl[p * a.dim + k], w = a.xhl[(int64_t)j * a.dim + k];
-                float t, e;
-                gpd::two_sum_f(u.x, -w.x, t, e);
-                e += u.y - w.y;
-                float sq, sqe;
-                gpd::two_prod_f(t, t, sq, sqe);
-                sqe = fmaf(2.f * t, e, fmaf(e, e, sqe));
-                float sum, se;
-                gpd::two_sum_f(eh, sq, sum, se);
-                eh = sum;
-                el += se + sqe;
-              }
-              float nh, nl;
-              gpd::two_sum_f(a.rs2h, -eh, nh, nl);
-              nl += a.rs2lo - el;
-              const float num = nh + nl;  // r_s^2 - d^2
+              float eh, el;
+              gpd::dist2_pair_f(a.xhl, a.dim, p, j, eh, el);
+              const float num = gpd::pair_gap_f(a.rs2h, a.rs2lo, eh, el);  // r_s^2 - d^2
               if (num >= a.s2min * a.rs2h) {
                 const float s2 = num * a.inv_rs2f;
                 const float rho2 = (eh + el) * a.inv_rs2f;  // el carries the differences' low parts

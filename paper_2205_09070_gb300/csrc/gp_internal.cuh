@@ -463,6 +463,39 @@ __device__ inline void two_prod_f(float a, float b, float& p, float& e) {
   e = fmaf(a, b, -p);
 }
 
+// |x_p - x_j|^2 as a double-float pair eh + el from coordinates given as
+// double-float pairs (hi, lo): each difference exact (TwoSum on the high
+// parts, plus the low parts), each square exact (TwoProduct, plus the cross
+// and square terms of the correction), the sum carried as a pair.  The
+// correction of a difference is as large as the rounding of the coordinates
+// to FP32 (about 2^-24 |x|), so the high word alone is NOT d^2 to FP32
+// accuracy: use eh + el.
+__device__ inline void dist2_pair_f(const float2* __restrict__ xhl, int dim, int64_t p, int64_t j, float& eh,
+                                    float& el) {
+  eh = 0.f;
+  el = 0.f;
+  for (int k = 0; k < dim; ++k) {
+    const float2 u = xhl[p * dim + k], w = xhl[j * dim + k];
+    float t, e;
+    two_sum_f(u.x, -w.x, t, e);
+    e += u.y - w.y;
+    float sq, sqe;
+    two_prod_f(t, t, sq, sqe);
+    sqe = fmaf(2.f * t, e, fmaf(e, e, sqe));
+    float sum, se;
+    two_sum_f(eh, sq, sum, se);
+    eh = sum;
+    el += se + sqe;
+  }
+}
+// r^2 - (eh + el) for r^2 = rh + rl, on the pairs (no cancellation), rounded once.
+__device__ inline float pair_gap_f(float rh, float rl, float eh, float el) {
+  float nh, nl;
+  two_sum_f(rh, -eh, nh, nl);
+  nl += rl - el;
+  return nh + nl;
+}
+
 // Compensated FP32 accumulation of products: the product's rounding error
 // (FMA) and each addition's rounding error (Knuth's TwoSum) are carried in a
 // second float, so a per-thread partial dot product keeps FP64-class accuracy
