@@ -689,6 +689,170 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
   }
 }
 
+// B = 128 with a two-dimensional split inside each warp: warp w keeps float4
+// slot w, and its lanes form 16 row groups (8 rows each) x 2 k groups, lane
+// (g, h) accumulating
+//   z[8 g + i] += M^-1[8 g + i][k] R[k],  k = 32q + 2kk + h, kk < 16,
+// over the block's panels.  Per k a lane reads 8 entries of M^-1 (row k of
+// the panel: M^-1 is exactly symmetric) and one float4 of R for 32 FMAs, so
+// a warp gets 1024 FMAs from 12 shared wavefronts where the one-dimensional
+// split (4 rows per lane, all 128 k) got 512 from 8; 8 rows keep the
+// kernel within the 96 registers that two CTAs of 288 threads per SM allow.
+// The panel row pitch of 132 floats and the interleaved k keep the loads free
+// of bank conflicts.  At the end of a block the two k-group partial sums of
+// each row are combined by a shuffle reduce-scatter (each lane keeps 4 of its
+// 8 rows).
+template <bool INIT>
+__global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
+                                                                 const float4* __restrict__ Q,
+                                                                 float4* __restrict__ R, float4* __restrict__ Z,
+                                                                 const float* __restrict__ Minv,
+                                                                 double* __restrict__ part,
+                                                                 const gp::CgState* st) {
+  if (!INIT && st->fin[st->iter & 1]) return;
+  constexpr int B = 128;
+  constexpr int S = pc_stages(B);
+  constexpr int NPB = B / kPcPanel;  // panels per block
+  constexpr int ldm = B + 4;         // panel row pitch (floats)
+  extern __shared__ float4 pc_smem[];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int rg = lane >> 1, kg = lane & 1;
+  const int nthr = kPcLanes * kq;        // float4 per R (or Q) panel
+  float4* Rs = pc_smem;                  // S x nthr
+  float4* Qs = Rs + S * nthr;            // S x nthr
+  float* Ms = (float*)(Qs + S * nthr);   // S x 32 x ldm: rows of M^-1
+  const int64_t nblk = (n + B - 1) / B;
+  const int64_t mine = blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t npan = mine * NPB;
+  const int64_t nrows_pc = nblk * B;
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!INIT) {
+    const int q = t % kq;
+    a = make_float4((float)st->alpha[4 * q], (float)st->alpha[4 * q + 1], (float)st->alpha[4 * q + 2],
+                    (float)st->alpha[4 * q + 3]);
+  }
+  auto issue = [&](int64_t pi, int s) {
+    if (pi < npan) {
+      const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+      const int q = (int)(pi % NPB);
+      const int64_t r0 = blk * B + kPcPanel * q;  // first row of the panel
+      const bool ok = r0 + t / kq < n;
+      const int64_t src = ok ? r0 * kq + t : 0;
+      cp_async16_zfill(Rs + s * nthr + t, R + src, ok);
+      if (!INIT) cp_async16_zfill(Qs + s * nthr + t, Q + src, ok);
+      for (int e = t; e < kPcPanel * (B / 4); e += nthr) {
+        const int kr = e / (B / 4), c4 = e - kr * (B / 4);
+        const int64_t grow = r0 + kr;  // row of the stacked blocks of M^-1
+        const bool okm = grow < nrows_pc;
+        const float* srcm = Minv + (okm ? grow * B + 4 * c4 : 0);
+        cp_async16_zfill(Ms + (s * kPcPanel + kr) * ldm + 4 * c4, srcm, okm);
+      }
+    }
+    cp_async_commit();
+  };
+  gpd::Dot2 rz[4], rr[4];
+  float2 acc[8][2];  // acc[i] = z[8 rg + i], columns (x, y) and (z, w) of slot w
+  float4 rv[4];
+  // the rows this lane holds after the reduce-scatter
+  const int myrow0 = 8 * rg + 4 * kg;
+#pragma unroll
+  for (int q = 0; q < S - 1; ++q) issue(q, q);
+  for (int64_t pi = 0; pi < npan; ++pi) {
+    const int s = (int)(pi % S);
+    cp_async_wait<S - 2>();  // this thread's copies of panel pi have landed
+    const int q = (int)(pi % NPB);
+    const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+    const int64_t r0 = blk * B + kPcPanel * q;
+    if (q == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+    }
+    if (!INIT) {
+      float4 v = Rs[s * nthr + t];
+      const float4 qv = Qs[s * nthr + t];
+      v.x = fmaf(-a.x, qv.x, v.x);
+      v.y = fmaf(-a.y, qv.y, v.y);
+      v.z = fmaf(-a.z, qv.z, v.z);
+      v.w = fmaf(-a.w, qv.w, v.w);
+      Rs[s * nthr + t] = v;
+      if (r0 + t / kq < n) R[r0 * kq + t] = v;
+    }
+    // one barrier per panel (as in k_upd_r_pcp)
+    __syncthreads();
+    issue(pi + S - 1, (int)((pi + S - 1) % S));
+    const float4* Rt = Rs + s * nthr;
+    if (myrow0 / kPcPanel == q) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rv[u] = Rt[((myrow0 + u) % kPcPanel) * kq + w];
+    }
+    const float* mrow = Ms + s * kPcPanel * ldm + 8 * rg;
+#pragma unroll 8
+    for (int kk = 0; kk < kPcPanel / 2; ++kk) {
+      const int k = 2 * kk + kg;
+      const float4* mk = (const float4*)(mrow + k * ldm);
+      const float4 x = Rt[k * kq + w];
+      const float2 xlo = make_float2(x.x, x.y), xhi = make_float2(x.z, x.w);
+#pragma unroll
+      for (int c4 = 0; c4 < 2; ++c4) {
+        const float4 m = mk[c4];
+        const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float2 m2v = make_float2(mv[i], mv[i]);
+          acc[4 * c4 + i][0] = __ffma2_rn(m2v, xlo, acc[4 * c4 + i][0]);
+          acc[4 * c4 + i][1] = __ffma2_rn(m2v, xhi, acc[4 * c4 + i][1]);
+        }
+      }
+    }
+    if (q == NPB - 1) {
+      // reduce-scatter over the two k groups: a lane keeps rows 4 kg .. + 3 of its 8
+      const bool b0 = kg;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float2 zc[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float2 lo = acc[u][c], hi = acc[u + 4][c];
+          const float2 send = b0 ? lo : hi, keep = b0 ? hi : lo;
+          zc[c] = make_float2(keep.x + __shfl_xor_sync(kFull, send.x, 1),
+                              keep.y + __shfl_xor_sync(kFull, send.y, 1));
+        }
+        const float4 z = make_float4(zc[0].x, zc[0].y, zc[1].x, zc[1].y);
+        const int64_t row = blk * B + myrow0 + u;
+        if (row < n) Z[row * kq + w] = z;
+        rz[0].add(rv[u].x, z.x);
+        rz[1].add(rv[u].y, z.y);
+        rz[2].add(rv[u].z, z.z);
+        rz[3].add(rv[u].w, z.w);
+        rr[0].add(rv[u].x, rv[u].x);
+        rr[1].add(rv[u].y, rv[u].y);
+        rr[2].add(rv[u].z, rv[u].z);
+        rr[3].add(rv[u].w, rv[u].w);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  // rows beyond n were filled with zeros, so they added nothing above
+  double v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[j] = rz[j].value();
+    v[4 + j] = rr[j].value();
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
+  if (lane == 0) {
+    const int kp = 4 * kq;
+    double* prow = part + (int64_t)blockIdx.x * 2 * kp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      prow[4 * w + j] = v[j];
+      prow[kp + 4 * w + j] = v[4 + j];
+    }
+  }
+}
+
 typedef void (*UpdPcFn)(int64_t, int, const float4*, float4*, float4*, const float*, double*, const gp::CgState*);
 
 template <bool INIT>
@@ -698,7 +862,7 @@ UpdPcFn upd_pc_fn(int B) {
     case 16: return k_upd_r_pc<INIT, 16>;
     case 32: return k_upd_r_pc<INIT, 32>;
     case 64: return k_upd_r_pcp<INIT, 64>;
-    case 128: return k_upd_r_pcp<INIT, 128>;
+    case 128: return k_upd_r_pcq<INIT>;
     default: return nullptr;
   }
 }
