@@ -188,17 +188,104 @@ __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n
 constexpr int kUpdThreads = 256;
 constexpr int kRedThreads = 1024;
 
-// alpha of iteration it (one block): p_c^T q_c from the SpMM partials in a
-// fixed order; alpha_c = |r_c|^2 / p_c^T q_c for columns still running.
-__global__ void __launch_bounds__(kRedThreads) k_cg_alpha(const double* __restrict__ part_pq, int npq, int k,
-                                                          int kp, gp::CgState* st, double* hist_alpha,
-                                                          int m_hist) {
+// The per-iteration reductions spread over one CTA per column: a single CTA
+// pulling all CTAs' partials (16-22 K doubles) through one SM's memory pipe
+// took 12-19 us per launch, latency-bound; a column's partials, one per
+// producing CTA, are summed by kColThreads threads and a fixed-order tree.
+constexpr int kColThreads = 256;
+
+// sum over b < nb of part[b * stride + col], in a fixed order; result in thread 0
+__device__ inline double column_sum(const double* __restrict__ part, int nb, int stride, int col, double* red) {
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kColThreads) a += __ldcg(part + (int64_t)b * stride + col);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kColThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// alpha of iteration it, CTA c for column c: alpha_c = rho_c / p_c^T q_c for
+// columns still running (Saad, Alg. 6.18), p^T q from the SpMM partials; a
+// non-positive or non-finite p^T q is a breakdown.
+__global__ void __launch_bounds__(kColThreads) k_cg_alpha_cols(const double* __restrict__ part_pq, int npq,
+                                                               int k, int kp, gp::CgState* st,
+                                                               double* hist_alpha, int m_hist) {
   const int it = st->iter;
   if (st->fin[it & 1]) return;
-  __shared__ double scratch[kRedThreads];
-  __shared__ double pq[gp::kMaxCols];
-  block_sum_partials(part_pq, npq, kp, kp, pq, scratch);
-  gpd::cg_alpha_finish(st, it, pq, k, kp, hist_alpha, m_hist);
+  __shared__ double red[kColThreads];
+  const int c = blockIdx.x;
+  const double d = column_sum(part_pq, npq, kp, c, red);
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    if (c < k && !st->donep[it & 1][c]) {
+      if (!(d > 0.0) || !isfinite(d)) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = c;
+      } else {
+        a = st->rrp[it & 1][c] / d;
+        if (it < m_hist) {
+          hist_alpha[it * gp::kMaxCols + c] = a;
+          st->steps[c] = it + 1;
+        }
+      }
+    }
+    st->alpha[c] = a;
+  }
+}
+
+// beta and the convergence test of iteration it, CTA c for column c: rho_new
+// from the partials (|r|^2, or r^T z and |r|^2 side by side in rows of 2 kp
+// when preconditioned), convergence on |r|^2, the iteration-(it+1) scalars in
+// parity slot (it+1)&1; the last CTA to finish advances the iteration.
+__global__ void __launch_bounds__(kColThreads) k_cg_beta_cols(const double* __restrict__ part, int nrr, int k,
+                                                              int kp, int pc, gp::CgState* st, double* hist_beta,
+                                                              int m_hist) {
+  const int it = st->iter;
+  const int cur = it & 1, nxt = (it + 1) & 1;
+  if (st->fin[cur]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->fin[nxt] = 1;
+    return;
+  }
+  __shared__ double red[kColThreads];
+  __shared__ bool last;
+  const int c = blockIdx.x;
+  const int width = pc ? 2 * kp : kp;
+  const double rrn = column_sum(part, nrr, width, c, red);  // rho_new = r^T M^-1 r
+  __syncthreads();
+  const double crn = pc ? column_sum(part, nrr, width, kp + c, red) : rrn;  // |r|^2
+  if (threadIdx.x == 0) {
+    const bool was_done = c >= k || st->donep[cur][c];
+    double b = 0.0;
+    bool done = was_done;
+    if (!was_done) {
+      b = rrn / st->rrp[cur][c];
+      if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
+      done = crn <= st->tol2 * st->rr0[c];
+      if (!isfinite(rrn) || !isfinite(crn)) {
+        st->status = GP_ERR_NOT_SPD;
+        st->bad_col = c;
+      }
+    }
+    st->beta[c] = b;
+    st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn;
+    st->crr[nxt][c] = was_done ? st->crr[cur][c] : crn;
+    st->donep[nxt][c] = done;
+    __threadfence();
+    last = atomicInc(&st->ticket_b, gridDim.x - 1) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    int running = 0;
+    for (int q = 0; q < k; ++q) running |= !__ldcg(&st->donep[nxt][q]);
+    st->iter = it + 1;
+    const int f = !running || __ldcg(&st->status) != GP_OK || it + 1 >= st->max_iter;
+    st->fin[nxt] = f;
+    st->finished = f;
+  }
 }
 
 // B: R -= alpha Q with per-block partial sums of |r_c|^2.  A thread owns one
@@ -904,57 +991,6 @@ __global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restri
   }
 }
 
-// beta of iteration it (one block): rho_new from the partials (|r|^2, or
-// r^T z and |r|^2 side by side in rows of 2 kp when preconditioned),
-// convergence on |r|^2, and the iteration-(it+1) scalars in parity slot
-// (it+1)&1.
-__global__ void __launch_bounds__(kRedThreads) k_cg_beta(const double* __restrict__ part, int nrr, int k, int kp,
-                                                         int pc, gp::CgState* st, double* hist_beta,
-                                                         int m_hist) {
-  const int it = st->iter;
-  const int cur = it & 1, nxt = (it + 1) & 1;
-  if (st->fin[cur]) {
-    if (threadIdx.x == 0) st->fin[nxt] = 1;
-    return;
-  }
-  __shared__ double scratch[kRedThreads];
-  __shared__ double sums[2 * gp::kMaxCols];
-  __shared__ int any_running;
-  const int width = pc ? 2 * kp : kp;
-  block_sum_partials(part, nrr, width, width, sums, scratch);
-  const double* rrn = sums;               // rho_new = r^T M^-1 r (|r|^2 without a preconditioner)
-  const double* crn = sums + (pc ? kp : 0);  // |r|^2
-  if (threadIdx.x == 0) any_running = 0;
-  __syncthreads();
-  if (threadIdx.x < kp) {
-    const int c = threadIdx.x;
-    const bool was_done = c >= k || st->donep[cur][c];
-    double b = 0.0;
-    bool done = was_done;
-    if (!was_done) {
-      b = rrn[c] / st->rrp[cur][c];
-      if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
-      done = crn[c] <= st->tol2 * st->rr0[c];
-      if (!isfinite(rrn[c]) || !isfinite(crn[c])) {
-        st->status = GP_ERR_NOT_SPD;
-        st->bad_col = c;
-      }
-    }
-    st->beta[c] = b;
-    st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn[c];
-    st->crr[nxt][c] = was_done ? st->crr[cur][c] : crn[c];
-    st->donep[nxt][c] = done;
-    if (c < k && !done) atomicOr(&any_running, 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st->iter = it + 1;
-    const int f = !any_running || st->status != GP_OK || it + 1 >= st->max_iter;
-    st->fin[nxt] = f;
-    st->finished = f;
-  }
-}
-
 // C: X += alpha P_old, P = Z + beta P_old with Z = M^-1 R (Z = R without a
 // preconditioner); runs for iteration it unless the run had already finished.
 __global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, float4* __restrict__ X,
@@ -1278,7 +1314,11 @@ __device__ bool tridiag_ql(double* d, double* e, double* z, int m) {
 // of column 1+l (Saad, Sec. 6.7.3): T_tt = 1/alpha_t + beta_{t-1}/alpha_{t-1},
 // T_t,t+1 = sqrt(beta_t)/alpha_t; Gamma_l = |z|^2 sum_k tau_k^2 ln theta_k.
 // The last block to finish forms the mean and variance over probes.
-__global__ void k_slq(int nv, int64_t n_act, const double* __restrict__ ha, const double* __restrict__ hb,
+// The kernel runs on a side stream under the preconditioned CG, so it is held
+// to 32 registers: a block of 32 threads then takes exactly the 1024
+// registers that three CTAs of the wide SpMM (128 threads x 168) leave free
+// on an SM, and the SpMM keeps its single wave of 3 CTAs on every SM.
+__global__ void __maxnreg__(32) k_slq(int nv, int64_t n_act, const double* __restrict__ ha, const double* __restrict__ hb,
                       const int* __restrict__ steps, double* gam, gp::AsmScalars* s) {
   const int l = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -1465,19 +1505,19 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     spmm_launch(plan, sm, c, st);
     if (ev1) cudaEventRecordWithFlags(ev1, sm, evf);
     if (!plan.fused_alpha)
-      k_cg_alpha<<<1, kRedThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
-                                            (double*)c->hist_alpha.p, m_hist);
+      k_cg_alpha_cols<<<kp, kColThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
+                                                  (double*)c->hist_alpha.p, m_hist);
     if (pc) {
       upd_pc<<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, (const float4*)c->Q.p,
                                                               (float4*)c->R.p, (float4*)c->Z.p,
                                                               (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
-      k_cg_beta<<<1, kRedThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, st,
-                                           (double*)c->hist_beta.p, m_hist);
+      k_cg_beta_cols<<<kp, kColThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, st,
+                                                 (double*)c->hist_beta.p, m_hist);
     } else {
       k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, sm>>>(n, kq, (const float4*)c->Q.p, (float4*)c->R.p,
                                                     (double*)c->part_b.p, st);
-      k_cg_beta<<<1, kRedThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, 0, st,
-                                           (double*)c->hist_beta.p, m_hist);
+      k_cg_beta_cols<<<kp, kColThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, 0, st,
+                                                 (double*)c->hist_beta.p, m_hist);
     }
     k_upd_xp_f32<<<g_upd, kUpdThreads, 0, sm>>>(n, kq, (float4*)c->X.p, (const float4*)(pc ? c->Z.p : c->R.p),
                                                 (float4*)c->P.p, st);
