@@ -158,11 +158,57 @@ __device__ inline uint32_t morton(const int* c, const gp::Grid& g) {
   return key;
 }
 
-// Sort key: the cell's Morton code in the high bits (points of a cell stay
-// contiguous and cells follow the Z-curve), then the Morton code of the
-// point's sub-cell (2^subbits per axis) so that consecutive rows inside a
-// cell are also close in space.
+// Index along the Hilbert curve of the point X (dim <= 3 coordinates of b
+// bits each), by Skilling's transform ("Programming the Hilbert curve", AIP
+// Conf. Proc. 707, 2004): the coordinates are turned into the transposed
+// index in place, then its bits are read out most significant first.  The
+// curve is hierarchical: the top dim * L bits of the index number the level-L
+// cube containing X, and the points of one such cube are contiguous.
+__device__ inline uint32_t hilbert_index(uint32_t* X, int dim, int b) {
+  const uint32_t m = 1u << (b - 1);
+  for (uint32_t q = m; q > 1; q >>= 1) {
+    const uint32_t lowbits = q - 1;
+    for (int i = 0; i < dim; ++i) {
+      if (X[i] & q) {
+        X[0] ^= lowbits;
+      } else {
+        const uint32_t t = (X[0] ^ X[i]) & lowbits;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  for (int i = 1; i < dim; ++i) X[i] ^= X[i - 1];
+  uint32_t t = 0;
+  for (uint32_t q = m; q > 1; q >>= 1)
+    if (X[dim - 1] & q) t ^= q - 1;
+  for (int i = 0; i < dim; ++i) X[i] ^= t;
+  uint32_t key = 0;
+  for (int j = b - 1; j >= 0; --j)
+    for (int i = 0; i < dim; ++i) key = (key << 1) | ((X[i] >> j) & 1u);
+  return key;
+}
+
+// Sort key.  Hilbert mode: the Hilbert index of the point's sub-cell (cell
+// coordinates extended by subbits bits per axis) over the grid padded to
+// 2^hbits cells per axis.  The cells are level-hbits cubes of the curve, so a
+// cell's points stay contiguous, cells follow the curve, and consecutive
+// rows are close in space without the Z-curve's jumps (on the 1M mixture the
+// 8x1 block CSR needs 11.27 M blocks instead of 12.17 M).  Morton mode (when
+// the padded grid needs more than 32 bits): the cell's Morton code in the
+// high bits, then the Morton code of the sub-cell.
 __device__ inline uint32_t sort_key(const double* xi, const int* c, const gp::Grid& g) {
+  if (g.hilbert) {
+    const int ns = 1 << g.subbits;
+    uint32_t X[gp::kMaxDim] = {0, 0, 0};
+    for (int k = 0; k < g.dim; ++k) {
+      double u = __ddiv_rn(__dsub_rn(xi[k], g.lo[k]), g.h) - (double)c[k];
+      int v = (int)floor(u * ns);
+      v = v < 0 ? 0 : (v > ns - 1 ? ns - 1 : v);
+      X[k] = ((uint32_t)c[k] << g.subbits) | (uint32_t)v;
+    }
+    return hilbert_index(X, g.dim, g.hbits + g.subbits);
+  }
   uint32_t sub = 0;
   if (g.subbits > 0) {
     const int ns = 1 << g.subbits;
@@ -849,8 +895,21 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     g.ncells *= g.G[k];
   }
   if (g.keybits > 32) return GP_ERR_UNSUPPORTED;
+  // Hilbert order when the grid padded to a cube of 2^B cells per axis and at
+  // least one sub-cell bit fit in 32 bits; else the Morton order
+  int B = 0;
+  for (int k = 0; k < dim; ++k) B = g.bits[k] > B ? g.bits[k] : B;
+  g.hilbert = 0;
+  g.hbits = 0;
   g.subbits = 0;
-  while (g.subbits < 2 && g.keybits + (g.subbits + 1) * dim <= 32) ++g.subbits;
+  if (B >= 1 && dim * (B + 1) <= 32) {
+    g.hilbert = 1;
+    g.hbits = B;
+    g.keybits = dim * B;
+    while (g.subbits < 3 && dim * (B + g.subbits + 1) <= 32) ++g.subbits;
+  } else {
+    while (g.subbits < 2 && g.keybits + (g.subbits + 1) * dim <= 32) ++g.subbits;
+  }
   c->grid = g;
 
   // --- bump parameters with FP32 pre-filter margins

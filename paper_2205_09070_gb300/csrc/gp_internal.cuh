@@ -45,6 +45,9 @@ struct Grid {
   int dim;
   int keybits;       // bits of the cell Morton code
   int subbits;       // bits per axis of the sub-cell order inside a cell
+  int hilbert;       // 1: points follow a Hilbert curve over the cells padded to 2^hbits per
+                     // axis and their sub-cells; 0: the Morton (Z) order
+  int hbits;         // bits per axis of the cell part of the Hilbert index
   int64_t ncells;
 };
 
