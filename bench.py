@@ -141,26 +141,33 @@ def spmm_kernel_name(variant: int, kp: int) -> str:
 
 
 WINDOW_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "window.cu")
+ASSEMBLE_SOURCE = os.path.join(ROOT, "paper_2205_09070_gb300", "csrc", "assemble.cu")
 _S_A = "// A: Q = Khat P on the 8x1 block CSR."
 _S_TMA = "// ---------------------------------------------------------------- TMA form"
 _S_WIDE = "// ---------------------------------------------------------------- wide cp.async form"
 _S_HOST = "// ---------------------------------------------------------------- host side"
-# source file and regions (first marker inclusive, second exclusive) of each SpMM form: its kernel
-# and the helpers it calls
+# The matrix a form multiplies is laid out by the assembly (row order, blocks), so the
+# whole assembly source is part of every form's key: its DRAM traffic changes with it.
+_ASM = (ASSEMBLE_SOURCE, None, None)
+# (file, first marker inclusive, second marker exclusive; None, None: the whole file) of each
+# SpMM form: its kernel, the helpers it calls and the assembly that lays out its matrix
 SPMM_REGIONS = {
-    "k_bspmm_f32": (SPMM_SOURCE, [(_S_A, _S_TMA)]),
-    "k_bspmm_tma": (SPMM_SOURCE, [(_S_A, _S_TMA), (_S_TMA, _S_WIDE)]),
-    "k_bspmm_f32w": (SPMM_SOURCE, [(_S_A, _S_TMA), (_S_WIDE, _S_HOST)]),
-    "k_wspmm": (WINDOW_SOURCE, [("// ------------------------------------------------------------------ SpMM",
-                                 "typedef void (*WinFn)")]),
+    "k_bspmm_f32": [(SPMM_SOURCE, _S_A, _S_TMA), _ASM],
+    "k_bspmm_tma": [(SPMM_SOURCE, _S_A, _S_TMA), (SPMM_SOURCE, _S_TMA, _S_WIDE), _ASM],
+    "k_bspmm_f32w": [(SPMM_SOURCE, _S_A, _S_TMA), (SPMM_SOURCE, _S_WIDE, _S_HOST), _ASM],
+    "k_wspmm": [(WINDOW_SOURCE, "// ------------------------------------------------------------------ SpMM",
+                 "typedef void (*WinFn)"), _ASM],
 }
 
 
 def spmm_source_sha(kernel: str) -> str:
-    """sha256 of the source regions of the SpMM form `kernel` (its kernel and helpers)."""
-    path, regions = SPMM_REGIONS[kernel.split("<")[0]]
-    src = open(path).read()
-    return hashlib.sha256("".join(src[src.index(a):src.index(b)] for a, b in regions).encode()).hexdigest()
+    """sha256 of the source regions of the SpMM form `kernel` (its kernel, helpers and the
+    assembly that lays out its matrix)."""
+    parts = []
+    for path, a, b in SPMM_REGIONS[kernel.split("<")[0]]:
+        src = open(path).read()
+        parts.append(src if a is None else src[src.index(a):src.index(b)])
+    return hashlib.sha256("".join(parts).encode()).hexdigest()
 
 
 def traffic_record(kernel: str, kp: int):
