@@ -89,6 +89,14 @@ __global__ void __launch_bounds__(kThreads) k_bbox(const double* __restrict__ x,
 // An FP32 pre-filter (coordinates relative to the bounding box) rejects bumps
 // far from the point; every accepted bump is re-tested and evaluated in FP64
 // with the same operation order as the plain definition.
+// GB300's FP64 pipe takes about 16 cycles per warp instruction, and a branch
+// taken by one lane costs the whole warp, so the accepted (point, bump) pairs
+// of a warp are queued in shared memory and evaluated 32 at a time with all
+// lanes busy (about one FP64 pass per warp instead of one per bump that any
+// lane accepts).  Each lane then adds its own results in bump order, so the
+// compensated sums are those of a plain loop over the bumps.
+constexpr int kBtQueue = 96;  // queued pairs per warp (flushed before it can overflow)
+
 __global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restrict__ x, int64_t n, int dim,
                                                          const gp::BumpParam* __restrict__ bumps, int n1,
                                                          int n2, double beta, double lo0, double lo1,
@@ -96,55 +104,115 @@ __global__ void __launch_bounds__(kThreads) k_bump_table(const double* __restric
                                                          uint32_t* __restrict__ mask0,
                                                          int32_t* __restrict__ flag) {
   extern __shared__ gp::BumpParam sb[];
+  __shared__ int q_pt[kWarps][kBtQueue];        // lane of the point
+  __shared__ int q_b[kWarps][kBtQueue];         // bump index m n2 + j
+  __shared__ double q_val[kWarps][kBtQueue];    // a exp(beta - beta / u), if added
+  __shared__ unsigned char q_fl[kWarps][kBtQueue];  // 1: inside the support, 2: value to add
   const int nb = n1 * n2;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) sb[b] = bumps[b];
   __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = gpd::lanemask_lt();
   const double lo[3] = {lo0, lo1, lo2};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the grid-stride loop runs the same number of times in every lane of a warp
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane; base < n; base += stride) {
+    const int64_t i = base + lane;
+    const bool valid = i < n;
     double xi[gp::kMaxDim] = {0, 0, 0};
     float x32[gp::kMaxDim] = {0, 0, 0};
-    for (int k = 0; k < dim; ++k) {
-      xi[k] = x[i * dim + k];
-      x32[k] = (float)(xi[k] - lo[k]);
+    if (valid) {
+      for (int k = 0; k < dim; ++k) {
+        xi[k] = x[i * dim + k];
+        x32[k] = (float)(xi[k] - lo[k]);
+      }
     }
+    // this lane's running state: compensated sum f + fc of function mcur
+    double f = 0.0, fc = 0.0;
+    int mcur = -1;
     uint32_t mask = 0;
-    for (int m = 0; m < n1; ++m) {
-      double f = 0.0, fc = 0.0;  // compensated sum f + fc over the bumps of f_m
-      bool in_m = false;
-      for (int j = 0; j < n2; ++j) {
-        const gp::BumpParam& bp = sb[m * n2 + j];
+    auto close_until = [&](int m_next) {
+      // F0 of mcur (if any), and zeros for the functions before m_next that
+      // had no accepted bump
+      if (mcur >= 0) F0[i * n1 + mcur] = f + fc;
+      for (int m = mcur + 1; m < m_next; ++m) F0[i * n1 + m] = 0.0;
+      f = 0.0;
+      fc = 0.0;
+      mcur = m_next;
+    };
+    int count = 0;
+    auto flush = [&]() {
+      __syncwarp();
+      for (int e = lane; e < count; e += 32) {
+        const int pl = q_pt[w][e], b = q_b[w][e];
+        const gp::BumpParam& bp = sb[b];
+        double xp[gp::kMaxDim] = {0, 0, 0};
+        for (int k = 0; k < dim; ++k) xp[k] = x[(base + pl) * dim + k];
+        // the support test exactly as the plain definition (FP64, this
+        // operation order); the value from u = 1 - q without cancellation
+        double d2 = 0.0;
+        for (int k = 0; k < dim; ++k) {
+          double t = __dsub_rn(xp[k], bp.c[k]);
+          d2 = __dadd_rn(d2, __dmul_rn(t, t));
+        }
+        const double q = __ddiv_rn(d2, bp.r2);
+        unsigned char fl = 0;
+        double v = 0.0;
+        if (q < 1.0) {
+          fl = 1;
+          const double u = gpd::one_minus_ratio(xp, bp.c, dim, bp.r2, bp.r2l);
+          if (u > 0.0) {
+            fl = 3;
+            v = bp.a * exp(beta - beta / u);
+          }
+        }
+        q_fl[w][e] = fl;
+        q_val[w][e] = v;
+      }
+      __syncwarp();
+      for (int e = 0; e < count; ++e) {
+        if (q_pt[w][e] != lane) continue;
+        const int m = q_b[w][e] / n2;
+        if (m != mcur) close_until(m);
+        const unsigned char fl = q_fl[w][e];
+        if (fl & 1) mask |= 1u << m;
+        if (fl & 2) {
+          double t, er;
+          gpd::two_sum(f, q_val[w][e], t, er);
+          f = t;
+          fc += er;
+        }
+      }
+      __syncwarp();
+      count = 0;
+    };
+    for (int b = 0; b < nb; ++b) {
+      bool pass = false;
+      if (valid) {
+        const gp::BumpParam& bp = sb[b];
         float q32 = 0.0f;
         for (int k = 0; k < dim; ++k) {
           float t = x32[k] - bp.c32[k];
           q32 = fmaf(t, t, q32);
         }
         q32 *= bp.inv_r2_32;
-        if (q32 < 1.0f + bp.margin) {
-          // the support test exactly as the plain definition (FP64, this
-          // operation order); the value from u = 1 - q without cancellation
-          double d2 = 0.0;
-          for (int k = 0; k < dim; ++k) {
-            double t = __dsub_rn(xi[k], bp.c[k]);
-            d2 = __dadd_rn(d2, __dmul_rn(t, t));
-          }
-          double q = __ddiv_rn(d2, bp.r2);
-          if (q < 1.0) {
-            const double u = gpd::one_minus_ratio(xi, bp.c, dim, bp.r2, bp.r2l);
-            if (u > 0.0) {
-              double t, e;
-              gpd::two_sum(f, bp.a * exp(beta - beta / u), t, e);
-              f = t;
-              fc += e;
-            }
-            in_m = true;
-          }
-        }
+        pass = q32 < 1.0f + bp.margin;
       }
-      F0[i * n1 + m] = f + fc;
-      if (in_m) mask |= 1u << m;
+      const unsigned bal = __ballot_sync(kFull, pass);
+      if (pass) {
+        const int slot = count + __popc(bal & lt);
+        q_pt[w][slot] = lane;
+        q_b[w][slot] = b;
+      }
+      count += __popc(bal);
+      if (count > kBtQueue - 32) flush();
     }
-    mask0[i] = mask;
-    flag[i] = mask != 0u;
+    if (count > 0) flush();
+    if (valid) {
+      close_until(n1);
+      mask0[i] = mask;
+      flag[i] = mask != 0u;
+    }
   }
 }
 
@@ -954,6 +1022,8 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
   {
     unsigned gb = grid_for(n, kThreads, maxb);
     size_t smem = sizeof(gp::BumpParam) * nb;
+    // up to kMaxBumps parameters beside the per-warp queues: above the default 48 KB
+    GP_CUDA(cudaFuncSetAttribute(k_bump_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_bump_table<<<gb, kThreads, smem, c->stream>>>(x, n, dim, (const gp::BumpParam*)c->bump.p, n1, n2, c->beta,
                                                     g.lo[0], dim > 1 ? g.lo[1] : 0.0, dim > 2 ? g.lo[2] : 0.0,
                                                     (double*)c->F0.p, (uint32_t*)c->mask0.p,

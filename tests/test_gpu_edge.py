@@ -217,3 +217,32 @@ def test_batched_instances_match_the_oracle(G, prec):
         print(prec, "instance", k, "N", q.n, "grad worst / bound", worst)
         assert ok, (k, q.n, worst)
     gp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_most_bumps_pattern_and_every_value(G, prec):
+    """The largest bump count the library takes (16 functions x 32 bumps, the
+    bump table's parameters then fill 40 KB of shared memory beside the
+    per-warp queues of its FP64 work), against the oracle: the pattern bit-exact,
+    every stored value within the format's tolerance."""
+    from helpers import canonical_gpu_csr, canonical_oracle_csr, value_tol_ok
+    rng = np.random.default_rng(12)
+    n, n1, n2 = 600, 16, 32
+    x = rng.uniform(0.0, 1.0, (n, 2))
+    centres = rng.uniform(0.0, 1.0, (n1, n2, 2))
+    radii = rng.uniform(0.05, 0.12, (n1, n2))
+    amps = rng.normal(0.0, 1.0, (n1, n2))
+    h = W.pack_h(centres, radii, amps, 0.08, 1.0, 1e-4)
+    gp = G.GP(2, n1, n2)
+    info = gp.assemble(torch.as_tensor(x, device="cuda"), h, precision=prec)
+    r, c, v = canonical_gpu_csr(gp.get_csr())
+    ro, co, vo, mask = canonical_oracle_csr(x, h, 2, n1, n2, key=("most_bumps",))
+    assert info["n_active"] == int(np.sum(mask != 0))
+    assert np.array_equal(r, ro) and np.array_equal(c, co)
+    diag = np.zeros(n)
+    dm = ro == co
+    diag[ro[dm]] = vo[dm]
+    ok, worst = value_tol_ok(v, vo, diag, ro, co, 1e-12 if prec == "fp64" else 1e-5, prec)
+    print(prec, "nnz", len(ro), "worst relative error", worst)
+    assert ok, worst
+    gp.close()
