@@ -103,7 +103,7 @@ typedef struct {
                              rows of the Morton-ordered active block (see gp_lml) */
   int32_t batch_workers;  /* gp_lml_grad_batched: instances run concurrently on this many
                              worker streams, each driven by its own host thread with its own
-                             workspace (0: automatic, min(n_inst, 4); at most 16) */
+                             workspace (0: automatic, min(n_inst, 8); at most 16) */
 } gp_opts;
 
 /* gp_opts.flags: time every launch of the SpMM, pair-fill and adjoint kernels

@@ -660,7 +660,7 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
     if (offsets[q] < 0 || offsets[q + 1] < offsets[q]) return GP_ERR_INVALID_ARG;
   GP_CUDA(cudaSetDevice(c->device));
   const int64_t P = (int64_t)c->nb * (c->dim + 2) + 3 + (c->core == GP_CORE_SQEXP ? 1 : 0);
-  int nw = o->batch_workers > 0 ? o->batch_workers : 4;
+  int nw = o->batch_workers > 0 ? o->batch_workers : 8;
   if (nw > n_inst) nw = n_inst;
   // worker contexts: own stream, workspace and CG graphs; kept for later calls
   while ((int)c->workers.size() < nw) {
