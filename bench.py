@@ -146,17 +146,22 @@ _S_A = "// A: Q = Khat P on the 8x1 block CSR."
 _S_TMA = "// ---------------------------------------------------------------- TMA form"
 _S_WIDE = "// ---------------------------------------------------------------- wide cp.async form"
 _S_HOST = "// ---------------------------------------------------------------- host side"
-# The matrix a form multiplies is laid out by the assembly (row order, blocks), so the
-# whole assembly source is part of every form's key: its DRAM traffic changes with it.
-_ASM = (ASSEMBLE_SOURCE, None, None)
-# (file, first marker inclusive, second marker exclusive; None, None: the whole file) of each
-# SpMM form: its kernel, the helpers it calls and the assembly that lays out its matrix
+# The matrix a form multiplies is laid out by the assembly (the row order: the grid and the
+# sort key; the 8x1 blocks), so those parts of the assembly are in every form's key: its
+# DRAM traffic changes with them.
+_ASM = [(ASSEMBLE_SOURCE, "// ------------------------------------------------------------------ cells",
+         "// ------------------------------------------------------------------ radix sort"),
+        (ASSEMBLE_SOURCE, "// ------------------------------------------------------------------ 8x1 block CSR",
+         "int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {"),
+        (ASSEMBLE_SOURCE, "  double h_cell = c->r_s * (1.0 + 1e-9);", "  c->grid = g;")]
+# (file, first marker inclusive, second marker exclusive) of each SpMM form: its kernel, the
+# helpers it calls and the assembly that lays out its matrix
 SPMM_REGIONS = {
-    "k_bspmm_f32": [(SPMM_SOURCE, _S_A, _S_TMA), _ASM],
-    "k_bspmm_tma": [(SPMM_SOURCE, _S_A, _S_TMA), (SPMM_SOURCE, _S_TMA, _S_WIDE), _ASM],
-    "k_bspmm_f32w": [(SPMM_SOURCE, _S_A, _S_TMA), (SPMM_SOURCE, _S_WIDE, _S_HOST), _ASM],
+    "k_bspmm_f32": [(SPMM_SOURCE, _S_A, _S_TMA)] + _ASM,
+    "k_bspmm_tma": [(SPMM_SOURCE, _S_A, _S_TMA), (SPMM_SOURCE, _S_TMA, _S_WIDE)] + _ASM,
+    "k_bspmm_f32w": [(SPMM_SOURCE, _S_A, _S_TMA), (SPMM_SOURCE, _S_WIDE, _S_HOST)] + _ASM,
     "k_wspmm": [(WINDOW_SOURCE, "// ------------------------------------------------------------------ SpMM",
-                 "typedef void (*WinFn)"), _ASM],
+                 "typedef void (*WinFn)")] + _ASM,
 }
 
 
@@ -166,7 +171,7 @@ def spmm_source_sha(kernel: str) -> str:
     parts = []
     for path, a, b in SPMM_REGIONS[kernel.split("<")[0]]:
         src = open(path).read()
-        parts.append(src if a is None else src[src.index(a):src.index(b)])
+        parts.append(src[src.index(a):src.index(b)])
     return hashlib.sha256("".join(parts).encode()).hexdigest()
 
 

@@ -15,8 +15,7 @@ def test_spmm_kernel_names_and_source_regions():
     for name in names.values():
         for path, a, b in bench.SPMM_REGIONS[name.split("<")[0]]:
             src = open(path).read()
-            if a is not None:
-                assert src.index(a) < src.index(b)
+            assert src.index(a) < src.index(b)
         assert len(bench.spmm_source_sha(name)) == 64
 
 
