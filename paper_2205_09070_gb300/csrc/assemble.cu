@@ -516,6 +516,69 @@ __device__ inline double dist2_fp64(const double* __restrict__ xs, int dim, int6
   return d2;
 }
 
+// Value of the stored entry (p, j) of the FP32 path, p and j in each other's
+// support: FP32 arithmetic on double-float inputs.  d^2 as a pair from exact
+// coordinate differences (TwoSum) and exact squares (TwoProduct), r_s^2 - d^2
+// on the pair (no cancellation near the edge), so s^2 and rho^2 reach the
+// stationary kernel with one FP32 rounding, as from FP64; the sum over the
+// shared functions compensated on the double-float Fhat = sqrt(A C) D^-1/2 F
+// (so it is already the stored entry's size), the core factor last.  Entries
+// with s^2 below s2min (where the pair's own error would show) take the FP64
+// route: rho^2 and s^2 in FP64 (s^2 without cancellation), the sum in FP64,
+// one rounding.
+__device__ inline float entry_value_f32(const PairArgs& a, int64_t p, int64_t j, uint32_t common) {
+  float eh, el;
+  gpd::dist2_pair_f(a.xhl, a.dim, p, j, eh, el);
+  const float num = gpd::pair_gap_f(a.rs2h, a.rs2lo, eh, el);  // r_s^2 - d^2
+  if (num >= a.s2min * a.rs2h) {
+    const float s2 = num * a.inv_rs2f;
+    const float rho2 = (eh + el) * a.inv_rs2f;  // el carries the differences' low parts
+    const float kst = gpd::kstat_unit_f(rho2, s2);
+    const float2* Fp = a.Fhl + p * a.n1;
+    const float2* Fj = a.Fhl + j * a.n1;
+    float Sh = 0.f, Sl = 0.f;
+    while (common) {
+      const int m = __ffs(common) - 1;
+      common &= common - 1u;
+      const float2 f = Fp[m], g2 = Fj[m];
+      float ph, pe;
+      gpd::two_prod_f(f.x, g2.x, ph, pe);
+      pe = fmaf(f.x, g2.y, fmaf(f.y, g2.x, pe));
+      float t, te;
+      gpd::two_sum_f(Sh, ph, t, te);
+      Sh = t;
+      Sl += te + pe;
+    }
+    float vv = kst * (Sh + Sl);
+    if (j == p) {
+      const float dp = ((const float*)a.dinv)[p];
+      vv = fmaf(a.sigma2f * dp, dp, vv);
+    } else if (a.il2h > 0.f) {
+      // t = d^2 / (2 l^2) as th + tl, exp(-t) = expf(-th) (1 - tl)
+      const float th = eh * a.il2h;
+      const float tl = fmaf(eh, a.il2h, -th) + fmaf(el, a.il2h, eh * a.il2lo);
+      vv *= expf(-th) * (1.f - tl);
+    }
+    return vv;
+  }
+  const double e2 = dist2_fp64(a.xs, a.dim, p, j);
+  double s2 = (a.rs2 - e2) * a.inv_rs2;
+  if (s2 < 1e-6) s2 = gpd::one_minus_ratio(a.xs + p * a.dim, a.xs + j * a.dim, a.dim, a.rs2, a.rs2l);
+  const double rho2 = e2 * a.inv_rs2;
+  const double kst = s2 > 0.0 ? (double)gpd::kstat_unit_f((float)rho2, (float)s2) : 0.0;
+  double S = 0.0;
+  while (common) {
+    const int m = __ffs(common) - 1;
+    common &= common - 1u;
+    const float2 f = a.Fhl[p * a.n1 + m], g2 = a.Fhl[j * a.n1 + m];
+    S = fma((double)f.x + (double)f.y, (double)g2.x + (double)g2.y, S);
+  }
+  double vv = kst * S;
+  if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<float>(e2 * a.inv2l2);
+  if (j == p) vv += a.sigma2 * a.dinv64[p] * a.dinv64[p];
+  return (float)vv;
+}
+
 // One warp per active row p.  The 3^dim neighbour cells of p's cell are
 // ordered by their first sorted index, so visiting their point ranges in that
 // order yields ascending column indices; the ranges are flattened and 32
@@ -615,91 +678,24 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
             hit = e2 < a.rs2;
           }
           if (FILL && hit) {
-            bool via64 = sizeof(T) == 8;
             if constexpr (sizeof(T) == 4) {
-              // FP32 path: FP32 arithmetic on double-float inputs.  d^2 as a
-              // pair from exact coordinate differences (TwoSum) and exact
-              // squares (TwoProduct), r_s^2 - d^2 on the pair (no
-              // cancellation near the edge), so s^2 and rho^2 reach the
-              // stationary kernel with one FP32 rounding, as from FP64; the
-              // sum over the shared functions compensated on the double-float
-              // Fhat = sqrt(A C) D^-1/2 F (so it is already the stored entry's
-              // size), the core factor last.  Entries with s^2 below s2min (where the pair's
-              // own error would show) take the FP64 route.
-              float eh, el;
-              gpd::dist2_pair_f(a.xhl, a.dim, p, j, eh, el);
-              const float num = gpd::pair_gap_f(a.rs2h, a.rs2lo, eh, el);  // r_s^2 - d^2
-              if (num >= a.s2min * a.rs2h) {
-                const float s2 = num * a.inv_rs2f;
-                const float rho2 = (eh + el) * a.inv_rs2f;  // el carries the differences' low parts
-                const float kst = gpd::kstat_unit_f(rho2, s2);
-                const float2* Fp = a.Fhl + p * a.n1;
-                const float2* Fj = a.Fhl + (int64_t)j * a.n1;
-                float Sh = 0.f, Sl = 0.f;
-                uint32_t common = mi & mj;
-                while (common) {
-                  const int m = __ffs(common) - 1;
-                  common &= common - 1u;
-                  const float2 f = Fp[m], g2 = Fj[m];
-                  float ph, pe;
-                  gpd::two_prod_f(f.x, g2.x, ph, pe);
-                  pe = fmaf(f.x, g2.y, fmaf(f.y, g2.x, pe));
-                  float t, te;
-                  gpd::two_sum_f(Sh, ph, t, te);
-                  Sh = t;
-                  Sl += te + pe;
-                }
-                float vv = kst * (Sh + Sl);
-                if (j == p) {
-                  const float dp = ((const float*)a.dinv)[p];
-                  vv = fmaf(a.sigma2f * dp, dp, vv);
-                } else if (a.il2h > 0.f) {
-                  // t = d^2 / (2 l^2) as th + tl, exp(-t) = expf(-th) (1 - tl)
-                  const float th = eh * a.il2h;
-                  const float tl = fmaf(eh, a.il2h, -th) + fmaf(el, a.il2h, eh * a.il2lo);
-                  vv *= expf(-th) * (1.f - tl);
-                }
-                v = (T)vv;
-              } else {
-                via64 = true;
-              }
-            }
-            if (via64) {
-              // FP64 route: rho^2 and s^2 = 1 - rho^2 in FP64 (s^2 without
+              v = entry_value_f32(a, p, j, mi & mj);
+            } else {
+              // FP64 path: rho^2 and s^2 = 1 - rho^2 in FP64 (s^2 without
               // cancellation near the edge), the sum over the shared functions
-              // in FP64 (compensated on the FP64 path), one rounding to T
+              // compensated, one rounding
               if (e2 < 0.0) e2 = dist2_fp64(a.xs, a.dim, p, j);
               double s2 = (a.rs2 - e2) * a.inv_rs2;
-              if (s2 < (sizeof(T) == 4 ? 1e-6 : 1e-2))
+              if (s2 < 1e-2)
                 s2 = gpd::one_minus_ratio(a.xs + p * a.dim, a.xs + (int64_t)j * a.dim, a.dim, a.rs2, a.rs2l);
               const double rho2 = e2 * a.inv_rs2;
-              double kst = 0.0;
-              if (s2 > 0.0) {
-                if (sizeof(T) == 4) kst = (double)gpd::kstat_unit_f((float)rho2, (float)s2);
-                else kst = gpd::kstat_unit_d(rho2, s2);
-              }
-              if constexpr (sizeof(T) == 4) {
-                // the scaled table: S is already A C D_p^-1/2 D_j^-1/2 sum F F
-                double S = 0.0;
-                uint32_t common = mi & mj;
-                while (common) {
-                  const int m = __ffs(common) - 1;
-                  common &= common - 1u;
-                  const float2 f = a.Fhl[p * a.n1 + m], g2 = a.Fhl[(int64_t)j * a.n1 + m];
-                  S = fma((double)f.x + (double)f.y, (double)g2.x + (double)g2.y, S);
-                }
-                double vv = kst * S;
-                if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
-                if (j == p) vv += a.sigma2 * a.dinv64[p] * a.dinv64[p];
-                v = (T)vv;
-              } else {
-                const double S =
-                    gpd::dot2_bits((const double*)a.Fs + p * a.n1, (const double*)a.Fs + (int64_t)j * a.n1, mi & mj);
-                double vv = a.AC * kst * S;
-                if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
-                if (j == p) vv += a.sigma2;
-                v = (T)(vv * a.dinv64[p] * a.dinv64[j]);
-              }
+              const double kst = s2 > 0.0 ? gpd::kstat_unit_d(rho2, s2) : 0.0;
+              const double S =
+                  gpd::dot2_bits((const double*)a.Fs + p * a.n1, (const double*)a.Fs + (int64_t)j * a.n1, mi & mj);
+              double vv = a.AC * kst * S;
+              if (a.inv2l2 > 0.0 && j != p) vv *= gpd::sqexp_core<T>(e2 * a.inv2l2);
+              if (j == p) vv += a.sigma2;
+              v = (T)(vv * a.dinv64[p] * a.dinv64[j]);
             }
           }
         }
@@ -725,8 +721,11 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
 // The support predicate is evaluated exactly as in k_pair (same FP32
 // expression, same FP64 guard band), so the two patterns are identical, and
 // candidate columns are visited in ascending order, so the hits of each row
-// arrive in the order of its scalar-CSR row: the fill copies the values
-// already computed there.
+// arrive in the order of its scalar-CSR row.  COUNT writes the blocks per
+// block row and also the entries per row (the scalar CSR's counts, so no
+// separate count pass); FILL copies the values k_pair computed.  (Computing
+// the values here instead, once for both matrices, took 10.1 ms at 1M
+// against 2.7 + 1.2 ms: the value code lifts the kernel to 162 registers.)
 constexpr int kBR = 8;
 constexpr int kBWarps = 4;
 constexpr int kMaxCand = kBR * 27;  // distinct neighbour cells of one block row
@@ -751,7 +750,7 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
     const int64_t r0 = bb * kBR;
     const int nr = (int)min((int64_t)kBR, a.n - r0);
     int4 myc = make_int4(-1, -1, -1, 0);
-    int64_t myrow = 0;  // next unread scalar-CSR entry of row r0 + lane
+    int64_t myrow = 0;  // FILL: next unread scalar-CSR entry of row r0 + lane; COUNT: its entries
     if (lane < nr) {
       myc = a.cellc[r0 + lane];
       s_rx[w][lane] = a.xr[r0 + lane];
@@ -863,7 +862,13 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
         }
       }
       const unsigned bal = __ballot_sync(kFull, bits != 0u);
-      if (FILL) {
+      if (!FILL) {
+#pragma unroll
+        for (int rr = 0; rr < kBR; ++rr) {
+          const unsigned br = __ballot_sync(kFull, (bits >> rr) & 1u);
+          if (lane == rr) myrow += __popc(br);
+        }
+      } else {
         float v[kBR];
 #pragma unroll
         for (int rr = 0; rr < kBR; ++rr) {
@@ -883,7 +888,10 @@ __global__ void __launch_bounds__(kBWarps * 32) k_bpair(PairArgs a, int64_t nblk
       }
       count += __popc(bal);
     }
-    if (!FILL && lane == 0) bcnt[bb] = count;
+    if (!FILL) {
+      if (lane == 0) bcnt[bb] = count;
+      if (lane < nr) a.cnt[r0 + lane] = (int32_t)myrow;
+    }
     __syncwarp();
   }
 }
@@ -1146,37 +1154,42 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
     for (int k = 0; k < dim; ++k) X = fmax(X, fmax(fabs(g.lo[k]), fabs(g.lo[k] + g.G[k] * g.h)));
     pa.s2min = (float)fmax(std::ldexp(1.0, -16), std::ldexp(X / c->r_s, -20));
   }
-  const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
-  k_pair<T, false><<<gw, kThreads, 0, c->stream>>>(pa);
-  GP_LAUNCH_CHECK();
-  c->launches += 1;
-  GP_CHECK(gp::ensure(c, c->row_ptr, (size_t)(n_act + 1) * sizeof(int64_t)));
-  GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->cnt.p, (int64_t*)c->row_ptr.p, n_act));
-  GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->row_ptr.p + n_act, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                          c->stream));
-  GP_CUDA(cudaStreamSynchronize(c->stream));
-  const int64_t nnz = *(int64_t*)c->pinned;
-  c->nnz = nnz;
-  GP_CHECK(gp::ensure(c, c->col, (size_t)nnz * sizeof(int32_t)));
-  GP_CHECK(gp::ensure(c, c->val, (size_t)nnz * sizeof(T)));
-  pa.row_ptr = (const int64_t*)c->row_ptr.p;
-  pa.col = (int32_t*)c->col.p;
-  pa.val = c->val.p;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
-  if (timed) {
-    GP_CHECK(gp::kernel_events(c));
-    GP_CUDA(cudaEventRecord(c->kev[128], c->stream));
-  }
-  k_pair<T, true><<<gw, kThreads, 0, c->stream>>>(pa);
-  GP_LAUNCH_CHECK();
-  c->launches += 1;
-  if (timed) {
-    GP_CUDA(cudaEventRecord(c->kev[129], c->stream));
-    GP_CUDA(cudaEventSynchronize(c->kev[129]));
-    c->t_fill += gp::event_ms(c->kev[128], c->kev[129]);
-  }
-  if (sizeof(T) == 4) {
-    // 8x1 block CSR for the FP32 SpMM: count, scan, fill
+  GP_CHECK(gp::ensure(c, c->row_ptr, (size_t)(n_act + 1) * sizeof(int64_t)));
+  GP_CHECK(gp::ensure_pinned(c, 2 * sizeof(int64_t)));
+  if constexpr (sizeof(T) == 8) {
+    // FP64 path: the scalar CSR alone, count then fill
+    const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
+    k_pair<T, false><<<gw, kThreads, 0, c->stream>>>(pa);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+    GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->cnt.p, (int64_t*)c->row_ptr.p, n_act));
+    GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->row_ptr.p + n_act, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            c->stream));
+    GP_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t nnz = *(int64_t*)c->pinned;
+    c->nnz = nnz;
+    GP_CHECK(gp::ensure(c, c->col, (size_t)nnz * sizeof(int32_t)));
+    GP_CHECK(gp::ensure(c, c->val, (size_t)nnz * sizeof(T)));
+    pa.row_ptr = (const int64_t*)c->row_ptr.p;
+    pa.col = (int32_t*)c->col.p;
+    pa.val = c->val.p;
+    if (timed) {
+      GP_CHECK(gp::kernel_events(c));
+      GP_CUDA(cudaEventRecord(c->kev[128], c->stream));
+    }
+    k_pair<T, true><<<gw, kThreads, 0, c->stream>>>(pa);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+    if (timed) {
+      GP_CUDA(cudaEventRecord(c->kev[129], c->stream));
+      GP_CUDA(cudaEventSynchronize(c->kev[129]));
+      c->t_fill += gp::event_ms(c->kev[128], c->kev[129]);
+    }
+  } else {
+    // FP32 path: the scalar CSR (adjoint, copy-out) and the 8x1 block CSR
+    // (SpMM): one count pass for both, both scans, one host read of both
+    // totals, then the scalar fill and the block fill
     const int64_t nblk = (n_act + kBR - 1) / kBR;
     c->nblk = nblk;
     GP_CHECK(gp::ensure(c, c->bcnt, (size_t)nblk * sizeof(int32_t)));
@@ -1186,16 +1199,38 @@ int assemble_t(gp_ctx* c, const double* x, int64_t n, const double* h) {
                                                          nullptr);
     GP_LAUNCH_CHECK();
     c->launches += 1;
+    GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->cnt.p, (int64_t*)c->row_ptr.p, n_act));
     GP_CHECK(gp::scan_i32_to_i64(c, (const int32_t*)c->bcnt.p, (int64_t*)c->brp.p, nblk));
-    GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->brp.p + nblk, sizeof(int64_t), cudaMemcpyDeviceToHost,
+    GP_CUDA(cudaMemcpyAsync(c->pinned, (int64_t*)c->row_ptr.p + n_act, sizeof(int64_t), cudaMemcpyDeviceToHost,
                             c->stream));
+    GP_CUDA(cudaMemcpyAsync((int64_t*)c->pinned + 1, (int64_t*)c->brp.p + nblk, sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, c->stream));
     GP_CUDA(cudaStreamSynchronize(c->stream));
-    const int64_t nbe = *(int64_t*)c->pinned;
+    const int64_t nnz = ((int64_t*)c->pinned)[0], nbe = ((int64_t*)c->pinned)[1];
+    c->nnz = nnz;
     c->nbent = nbe;
+    GP_CHECK(gp::ensure(c, c->col, (size_t)nnz * sizeof(int32_t)));
+    GP_CHECK(gp::ensure(c, c->val, (size_t)nnz * sizeof(T)));
     GP_CHECK(gp::ensure(c, c->bcol, (size_t)nbe * sizeof(int32_t)));
     GP_CHECK(gp::ensure(c, c->bmask, (size_t)nbe));
     GP_CHECK(gp::ensure(c, c->bval, (size_t)nbe * kBR * sizeof(float)));
-    // pa.row_ptr / pa.val point at the filled scalar CSR
+    pa.row_ptr = (const int64_t*)c->row_ptr.p;
+    pa.col = (int32_t*)c->col.p;
+    pa.val = c->val.p;
+    if (timed) {
+      GP_CHECK(gp::kernel_events(c));
+      GP_CUDA(cudaEventRecord(c->kev[128], c->stream));
+    }
+    const unsigned gw = grid_for(n_act, kWarps, c->num_sms * 8);
+    k_pair<T, true><<<gw, kThreads, 0, c->stream>>>(pa);
+    GP_LAUNCH_CHECK();
+    c->launches += 1;
+    if (timed) {
+      GP_CUDA(cudaEventRecord(c->kev[129], c->stream));
+      GP_CUDA(cudaEventSynchronize(c->kev[129]));
+      c->t_fill += gp::event_ms(c->kev[128], c->kev[129]);
+    }
+    // the blocks copy the values just computed
     k_bpair<true><<<gbk, kBWarps * 32, 0, c->stream>>>(pa, nblk, (const int64_t*)c->brp.p, nullptr,
                                                         (int32_t*)c->bcol.p, (uint8_t*)c->bmask.p,
                                                         (float*)c->bval.p);
