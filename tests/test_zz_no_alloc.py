@@ -110,3 +110,38 @@ def test_noalloc_rejects_matrices_above_the_staging_size(G):
     assert lib.gp_get_csr_noalloc(gp._h, rp.ctypes.data, None, None, None, sizes) == G.GP_OK
     assert rp[-1] == info["nnz"]
     gp.close()
+
+
+def test_noalloc_while_another_stream_captures(G):
+    """The call is made while a CUDA graph is being captured on a stream of the
+    caller's (relaxed capture mode), with its outputs allocated beforehand: the
+    copy-out runs on the context's own stream, the capture is left intact, and
+    the outputs equal gp_get_csr's."""
+    p = W.small_2d(seed=1, n=600)
+    gp = G.GP(p.dim, p.n1, p.n2, p.beta)
+    gp.assemble(torch.as_tensor(p.x, device="cuda"), p.h, precision="fp32")
+    copy_out(G, gp, "gp_get_csr_noalloc")  # first call on the device: outside any capture
+    rp0, col0, val0, perm0 = copy_out(G, gp, "gp_get_csr")
+    lib = G.load()
+    sizes = (ctypes.c_int64 * 2)()
+    assert lib.gp_get_csr_noalloc(gp._h, None, None, None, None, sizes) == G.GP_OK
+    rp = np.zeros(int(sizes[0]) + 1, np.int64)
+    col = np.zeros(int(sizes[1]), np.int32)
+    perm = np.zeros(int(sizes[0]), np.int32)
+    val_t = torch.zeros(int(sizes[1]), dtype=torch.float64, device="cuda")
+    a = torch.arange(16, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+            b = a * 2.0
+            st = lib.gp_get_csr_noalloc(gp._h, rp.ctypes.data, col.ctypes.data, val_t.data_ptr(),
+                                        perm.ctypes.data, sizes)
+    assert st == G.GP_OK, G.status_string(st)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b, a * 2.0)
+    assert np.array_equal(rp, rp0) and np.array_equal(col, col0) and np.array_equal(perm, perm0)
+    assert np.array_equal(val_t.cpu().numpy(), val0)
+    gp.close()
