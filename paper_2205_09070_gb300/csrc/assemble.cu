@@ -586,13 +586,34 @@ __device__ inline float entry_value_f32(const PairArgs& a, int64_t p, int64_t j,
 //   mask_p & mask_j != 0  and  |x_p - x_j|^2 < r_s^2   (j == p always passes).
 // COUNT writes the number of hits per row; FILL writes columns and the
 // Jacobi-scaled values  D_p^-1/2 (A C k~ sum_m F_pm F_jm + sigma_n^2 [p==j]) D_j^-1/2.
+// FP32 FILL: a warp step finds about 5 hits among its 32 candidates, so the
+// value code would run with 5 of 32 lanes busy; hits are queued per warp
+// instead (entry, column, row) and their values computed 32 at a time.
+constexpr int kPairQueue = 64;
+
 template <typename T, bool FILL>
 __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
   __shared__ int sh_start[kWarps][32];
   __shared__ int sh_pre[kWarps][32];
   __shared__ int sh_off[kWarps][32];
+  constexpr bool kQueue = FILL && sizeof(T) == 4;
+  __shared__ int64_t q_pos[kQueue ? kWarps : 1][kPairQueue];
+  __shared__ int q_row[kQueue ? kWarps : 1][kPairQueue];
+  __shared__ int q_col[kQueue ? kWarps : 1][kPairQueue];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   T* val = (T*)a.val;
+  int qn = 0;  // queued hits of this warp
+  auto flush = [&]() {
+    if constexpr (kQueue) {
+      __syncwarp();
+      for (int e = lane; e < qn; e += 32) {
+        const int pp = q_row[w][e], jj = q_col[w][e];
+        val[q_pos[w][e]] = (T)entry_value_f32(a, pp, jj, a.mask[pp] & a.mask[jj]);
+      }
+      __syncwarp();
+      qn = 0;
+    }
+  };
   const int G[3] = {a.G0, a.G1, a.G2};
   for (int64_t p = (int64_t)blockIdx.x * kWarps + w; p < a.n; p += (int64_t)gridDim.x * kWarps) {
     const int4 ci4 = a.cellc[p];
@@ -678,9 +699,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
             hit = e2 < a.rs2;
           }
           if (FILL && hit) {
-            if constexpr (sizeof(T) == 4) {
-              v = entry_value_f32(a, p, j, mi & mj);
-            } else {
+            if constexpr (sizeof(T) == 8) {
               // FP64 path: rho^2 and s^2 = 1 - rho^2 in FP64 (s^2 without
               // cancellation near the edge), the sum over the shared functions
               // compensated, one rounding
@@ -704,12 +723,24 @@ __global__ void __launch_bounds__(kThreads) k_pair(PairArgs a) {
       if (FILL && hit) {
         const int64_t q = out + count + __popc(bal & gpd::lanemask_lt());
         a.col[q] = j;
-        val[q] = v;
+        if constexpr (kQueue) {
+          const int slot = qn + __popc(bal & gpd::lanemask_lt());
+          q_pos[w][slot] = q;
+          q_row[w][slot] = (int)p;
+          q_col[w][slot] = j;
+        } else {
+          val[q] = v;
+        }
       }
       count += __popc(bal);
+      if constexpr (kQueue) {
+        qn += __popc(bal);
+        if (qn > kPairQueue - 32) flush();
+      }
     }
     if (!FILL && lane == 0) a.cnt[p] = count;
   }
+  flush();
 }
 
 // ------------------------------------------------------------------ 8x1 block CSR
