@@ -65,6 +65,7 @@ struct CgState {
   int status;              // GP_OK or GP_ERR_NOT_SPD
   int bad_col;
   unsigned ticket_a;       // last-block tickets (reset by the last block)
+  unsigned run_cnt;        // columns still running after this iteration (reset by the last block)
   unsigned ticket_b;
   unsigned ticket_c;
   int max_iter;

@@ -194,38 +194,54 @@ constexpr int kRedThreads = 1024;
 // producing CTA, are summed by kColThreads threads and a fixed-order tree.
 constexpr int kColThreads = 256;
 
-// sum over b < nb of part[b * stride + col], in a fixed order; result in thread 0
-__device__ inline double column_sum(const double* __restrict__ part, int nb, int stride, int col, double* red) {
-  double a = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kColThreads) a += __ldcg(part + (int64_t)b * stride + col);
-  red[threadIdx.x] = a;
+// sums over b < nb of part[b * stride + col0] and (col1 >= 0) of part[b *
+// stride + col1], in a fixed order, in one pass; results in thread 0
+__device__ inline double2 column_sums(const double* __restrict__ part, int nb, int stride, int col0, int col1,
+                                      double* red0, double* red1) {
+  double a = 0.0, b2 = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kColThreads) {
+    a += __ldcg(part + (int64_t)b * stride + col0);
+    if (col1 >= 0) b2 += __ldcg(part + (int64_t)b * stride + col1);
+  }
+  red0[threadIdx.x] = a;
+  red1[threadIdx.x] = b2;
   __syncthreads();
   for (int o = kColThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+      red0[threadIdx.x] += red0[threadIdx.x + o];
+      red1[threadIdx.x] += red1[threadIdx.x + o];
+    }
     __syncthreads();
   }
-  return red[0];
+  return make_double2(red0[0], red1[0]);
 }
 
 // alpha of iteration it, CTA c for column c: alpha_c = rho_c / p_c^T q_c for
 // columns still running (Saad, Alg. 6.18), p^T q from the SpMM partials; a
-// non-positive or non-finite p^T q is a breakdown.
+// non-positive or non-finite p^T q is a breakdown.  The column's state is read
+// before the sum, so that its latency overlaps the sum's.
 __global__ void __launch_bounds__(kColThreads) k_cg_alpha_cols(const double* __restrict__ part_pq, int npq,
                                                                int k, int kp, gp::CgState* st,
                                                                double* hist_alpha, int m_hist) {
   const int it = st->iter;
   if (st->fin[it & 1]) return;
-  __shared__ double red[kColThreads];
+  __shared__ double red0[kColThreads], red1[kColThreads];
   const int c = blockIdx.x;
-  const double d = column_sum(part_pq, npq, kp, c, red);
+  bool running = false;
+  double rho = 0.0;
+  if (threadIdx.x == 0) {
+    running = c < k && !st->donep[it & 1][c];
+    rho = st->rrp[it & 1][c];
+  }
+  const double d = column_sums(part_pq, npq, kp, c, -1, red0, red1).x;
   if (threadIdx.x == 0) {
     double a = 0.0;
-    if (c < k && !st->donep[it & 1][c]) {
+    if (running) {
       if (!(d > 0.0) || !isfinite(d)) {
         st->status = GP_ERR_NOT_SPD;
         st->bad_col = c;
       } else {
-        a = st->rrp[it & 1][c] / d;
+        a = rho / d;
         if (it < m_hist) {
           hist_alpha[it * gp::kMaxCols + c] = a;
           st->steps[c] = it + 1;
@@ -239,7 +255,8 @@ __global__ void __launch_bounds__(kColThreads) k_cg_alpha_cols(const double* __r
 // beta and the convergence test of iteration it, CTA c for column c: rho_new
 // from the partials (|r|^2, or r^T z and |r|^2 side by side in rows of 2 kp
 // when preconditioned), convergence on |r|^2, the iteration-(it+1) scalars in
-// parity slot (it+1)&1; the last CTA to finish advances the iteration.
+// parity slot (it+1)&1.  Running columns are counted in st->run_cnt; the last
+// CTA to finish reads and clears the count and advances the iteration.
 __global__ void __launch_bounds__(kColThreads) k_cg_beta_cols(const double* __restrict__ part, int nrr, int k,
                                                               int kp, int pc, gp::CgState* st, double* hist_beta,
                                                               int m_hist) {
@@ -249,40 +266,47 @@ __global__ void __launch_bounds__(kColThreads) k_cg_beta_cols(const double* __re
     if (blockIdx.x == 0 && threadIdx.x == 0) st->fin[nxt] = 1;
     return;
   }
-  __shared__ double red[kColThreads];
+  __shared__ double red0[kColThreads], red1[kColThreads];
   __shared__ bool last;
   const int c = blockIdx.x;
   const int width = pc ? 2 * kp : kp;
-  const double rrn = column_sum(part, nrr, width, c, red);  // rho_new = r^T M^-1 r
-  __syncthreads();
-  const double crn = pc ? column_sum(part, nrr, width, kp + c, red) : rrn;  // |r|^2
+  bool was_done = true;
+  double rrp = 0.0, crr = 0.0, lim = 0.0;
   if (threadIdx.x == 0) {
-    const bool was_done = c >= k || st->donep[cur][c];
+    was_done = c >= k || st->donep[cur][c];
+    rrp = st->rrp[cur][c];
+    crr = st->crr[cur][c];
+    lim = st->tol2 * st->rr0[c];
+  }
+  // rho_new = r^T M^-1 r and |r|^2
+  const double2 sums = column_sums(part, nrr, width, c, pc ? kp + c : -1, red0, red1);
+  const double rrn = sums.x, crn = pc ? sums.y : sums.x;
+  if (threadIdx.x == 0) {
     double b = 0.0;
     bool done = was_done;
     if (!was_done) {
-      b = rrn / st->rrp[cur][c];
+      b = rrn / rrp;
       if (it < m_hist) hist_beta[it * gp::kMaxCols + c] = b;
-      done = crn <= st->tol2 * st->rr0[c];
+      done = crn <= lim;
       if (!isfinite(rrn) || !isfinite(crn)) {
         st->status = GP_ERR_NOT_SPD;
         st->bad_col = c;
       }
     }
     st->beta[c] = b;
-    st->rrp[nxt][c] = was_done ? st->rrp[cur][c] : rrn;
-    st->crr[nxt][c] = was_done ? st->crr[cur][c] : crn;
+    st->rrp[nxt][c] = was_done ? rrp : rrn;
+    st->crr[nxt][c] = was_done ? crr : crn;
     st->donep[nxt][c] = done;
+    if (c < k && !done) atomicAdd(&st->run_cnt, 1u);
     __threadfence();
     last = atomicInc(&st->ticket_b, gridDim.x - 1) == gridDim.x - 1;
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    int running = 0;
-    for (int q = 0; q < k; ++q) running |= !__ldcg(&st->donep[nxt][q]);
+    const unsigned running = atomicExch(&st->run_cnt, 0u);
     st->iter = it + 1;
-    const int f = !running || __ldcg(&st->status) != GP_OK || it + 1 >= st->max_iter;
+    const int f = running == 0u || __ldcg(&st->status) != GP_OK || it + 1 >= st->max_iter;
     st->fin[nxt] = f;
     st->finished = f;
   }
