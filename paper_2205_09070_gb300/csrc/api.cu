@@ -237,8 +237,10 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
     // short plain run of lanczos_steps iterations (expected not to converge),
     // reduced to SLQ terms before the preconditioned run reuses the CG state
     double lanczos_rel = 0.0;
+    // (one check interval of lanczos_steps iterations: the run always goes to
+    // its cap, so shorter intervals only add host checks and idle launches)
     const int lst = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->lanczos_steps, o->cg_rtol,
-                               o->check_every, &lanczos_iters, &lanczos_rel, false);
+                               o->lanczos_steps, &lanczos_iters, &lanczos_rel, false);
     if (lst != GP_OK && lst != GP_ERR_NOT_CONVERGED) return lst;
     // the eigen-solves overlap the preconditioned run (side stream)
     GP_CHECK(gp::slq(c, nv, kp, true));
