@@ -246,3 +246,61 @@ def test_most_bumps_pattern_and_every_value(G, prec):
     print(prec, "nnz", len(ro), "worst relative error", worst)
     assert ok, worst
     gp.close()
+
+
+def _pattern_and_values(G, x, h, dim, n1, n2, prec, key):
+    from helpers import canonical_gpu_csr, canonical_oracle_csr, value_tol_ok
+    gp = G.GP(dim, n1, n2)
+    info = gp.assemble(torch.as_tensor(x, device="cuda"), h, precision=prec)
+    r, c, v = canonical_gpu_csr(gp.get_csr())
+    ro, co, vo, mask = canonical_oracle_csr(x, h, dim, n1, n2, key=key)
+    assert info["n_active"] == int(np.sum(mask != 0))
+    assert np.array_equal(r, ro) and np.array_equal(c, co)
+    diag = np.zeros(x.shape[0])
+    dm = ro == co
+    diag[ro[dm]] = vo[dm]
+    ok, worst = value_tol_ok(v, vo, diag, ro, co, 1e-12 if prec == "fp64" else 1e-5, prec)
+    gp.close()
+    return ok, worst, len(ro)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_elongated_domain_uses_the_morton_order(G, prec):
+    """Clusters along a strip 40,000 r_s long: the cell grid padded to a
+    power-of-two square needs 2 x 16 bits plus a sub-cell bit, more than the
+    32-bit sort key holds, so the points follow the Morton order instead of
+    the Hilbert curve; the pattern and every value still match the oracle."""
+    rng = np.random.default_rng(21)
+    r_s, n1, n2 = 0.05, 2, 6
+    # 12 clusters of 150 points, 3 r_s across, spread along the strip (the
+    # first and last at its ends, so the active points span 40,000 cells);
+    # one bump per cluster and function
+    cx = np.sort(rng.uniform(0.0, 40000 * r_s, n1 * n2))
+    cx[0], cx[-1] = 2 * r_s, 39998 * r_s
+    x = np.concatenate([np.column_stack([c + rng.uniform(-1.5 * r_s, 1.5 * r_s, 150),
+                                         rng.uniform(0.0, r_s, 150)]) for c in cx])
+    centres = np.column_stack([cx, np.full(n1 * n2, 0.5 * r_s)])
+    centres = centres[rng.permutation(n1 * n2)].reshape(n1, n2, 2)
+    radii = rng.uniform(2.5 * r_s, 4.0 * r_s, (n1, n2))
+    amps = rng.normal(0.0, 1.0, (n1, n2))
+    h = W.pack_h(centres, radii, amps, r_s, 1.0, 1e-4)
+    ok, worst, nnz = _pattern_and_values(G, x, h, 2, n1, n2, prec, ("strip",))
+    print(prec, "nnz", nnz, "worst relative error", worst)
+    assert ok, worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coordinates_far_from_the_origin(G, prec):
+    """The small 2-D workload moved by 1000 along each axis (20,000 r_s): the
+    double-float coordinates of the FP32 fill then carry an absolute error of
+    about 2^-45 x 1000, so more entries near the support edge take the FP64
+    route; pattern and values still match the oracle on the moved points."""
+    p = W.small_2d(seed=5, n=1500)
+    x = p.x + 1000.0
+    h = p.h.copy()
+    np_ = p.dim + 2
+    for b in range(p.n1 * p.n2):
+        h[b * np_: b * np_ + p.dim] += 1000.0  # bump centres move with the points
+    ok, worst, nnz = _pattern_and_values(G, x, h, p.dim, p.n1, p.n2, prec, ("moved", 5))
+    print(prec, "nnz", nnz, "worst relative error", worst)
+    assert ok, worst
