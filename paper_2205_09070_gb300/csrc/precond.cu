@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
                                                   float* __restrict__ Mout, gp::AsmScalars* s) {
   extern __shared__ float pc_sf[];
   float (*A)[B + 1] = (float (*)[B + 1])pc_sf;
-  float* yd = pc_sf + B * (B + 1);  // Y[c][c] = 1 / L_cc
+  float* yd = pc_sf + B * (B + 1);  // L_cc during the factorisation, then Y[c][c] = 1 / L_cc
   const int t = threadIdx.x;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
     const int64_t r0 = b * B;
@@ -139,10 +139,13 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
       }
     }
     __syncthreads();
+    // Two barriers per column: every thread takes the pivot from A[j][j],
+    // which only step j reads, and the pivot goes to yd[j] (A[j][j] is set
+    // after the loop), so no thread can see it overwritten mid-step.
     for (int j = 0; j < nb; ++j) {
-      if (t == j) A[j][j] = sqrtf(fmaxf(A[j][j], 1e-6f));
-      __syncthreads();
-      if (t > j && t < nb) A[t][j] /= A[j][j];
+      const float piv = sqrtf(fmaxf(A[j][j], 1e-6f));
+      if (t == j) yd[j] = piv;
+      if (t > j && t < nb) A[t][j] /= piv;
       __syncthreads();
       if (t > j && t < nb) {
         const float lt = A[t][j];
@@ -150,6 +153,8 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
       }
       __syncthreads();
     }
+    if (t < nb) A[t][t] = yd[t];
+    __syncthreads();
     // Y = L^-1, column t, into row t of the upper triangle; four partial
     // sums shorten the add chains
     if (t < nb) {
@@ -170,9 +175,13 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
     }
     __syncthreads();
     // M^-1 = Y^T Y: M[t][jj] = sum_{k >= max(t, jj)} Y[k][t] Y[k][jj], with
-    // Y[k][c] = A[c][k] for k > c and yd[c] for k = c; zero outside nb x nb
+    // Y[k][c] = A[c][k] for k > c and yd[c] for k = c; zero outside nb x nb.
+    // Thread t forms the entries jj >= t of its row and writes both M[t][jj]
+    // and M[jj][t]: the two are the same products in the same order (the
+    // factors of each multiply and FMA only swap places), so M^-1 is exactly
+    // symmetric, as the apply relies on.
     float* Mb = Mout + b * (int64_t)B * B;
-    for (int jj = 0; jj < B; ++jj) {
+    for (int jj = t; jj < B; ++jj) {
       float m = 0.f;
       if (t < nb && jj < nb) {
         const int lo = t > jj ? t : jj;
@@ -188,6 +197,7 @@ __global__ void __launch_bounds__(B) k_pc_setup32(int64_t n, int64_t nblk, const
         m += m1;
       }
       Mb[t * B + jj] = m;
+      Mb[jj * B + t] = m;
     }
     __syncthreads();
   }
