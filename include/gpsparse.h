@@ -101,9 +101,10 @@ typedef struct {
   int32_t precond_block;  /* FP32_MIXED only: 0 = Jacobi scaling alone; 8, 16, 32, 64 or 128 = also
                              block-Jacobi preconditioned CG, blocks of that many consecutive
                              rows of the Morton-ordered active block (see gp_lml) */
-  int32_t batch_workers;  /* gp_lml_grad_batched: instances run concurrently on this many
-                             worker streams, each driven by its own host thread with its own
-                             workspace (0: automatic, min(n_inst, 8); at most 16) */
+  int32_t batch_workers;  /* gp_lml_grad_batched: host threads that run the instances' assembly
+                             and gradient (grouped CG launches), or whole instances on as many
+                             worker streams, each with its own workspace (0: automatic,
+                             min(n_inst, 8); at most 16) */
 } gp_opts;
 
 /* gp_opts.flags: time every launch of the SpMM, pair-fill and adjoint kernels
@@ -152,6 +153,10 @@ typedef struct {
 #define GP_FLAG_FAULT_OOM 128
 #define GP_FLAG_FAULT_NOT_SPD 256
 #define GP_FLAG_FAULT_NAN 512
+
+/* gp_opts.flags: gp_lml_grad_batched runs every instance on its own on the
+ * worker streams, even where its grouped CG launches apply (see there). */
+#define GP_FLAG_BATCH_STREAMS 1024
 
 /* gp_info.spmm_variant */
 #define GP_SPMM_CPASYNC  0
@@ -333,12 +338,27 @@ int gp_lml_grad(gp_ctx* ctx, const double* x, const double* y, int64_t n, const 
 /* Many independent GPs that share the kernel family.  Instance k owns points
  * offsets[k] .. offsets[k+1]-1 of x / y (offsets: host, n_inst+1 entries) and
  * hyperparameters h[k*P .. (k+1)*P).  lml: n_inst doubles, grad: n_inst*P
- * doubles (host or device); grad may be NULL.  info (may be NULL) gets totals.
- * Instances are taken largest first by opts->batch_workers workers, each with
- * its own stream and workspace (kept in ctx for later calls); the workers
- * start after the work already queued on the context stream, and the call
- * returns when all instances are done.  Each instance's result is the one
- * gp_lml_grad gives for it alone (same kernels, same reduction order). */
+ * doubles (host or device); grad may be NULL.  info (may be NULL) gets totals
+ * (iters: the largest instance's count).  Workspaces are kept in ctx for later
+ * calls; the work starts after what is already queued on the context stream,
+ * and the call returns when all instances are done.
+ *
+ * Grouped CG launches (the default for FP32_MIXED with the SLQ estimator):
+ * instances are taken largest first in waves of up to 256, one workspace and
+ * stream each.  opts->batch_workers host threads assemble them; then the CG
+ * iterations of all of them run as single launches on the context stream,
+ * each launch doing one iteration for every instance still running (an
+ * instance leaves when its run finishes); then the threads form each
+ * instance's ln L and gradient.  The product is the wide cp.async form (else
+ * the cp.async form) for every instance, and each instance's result is the one
+ * gp_lml_grad gives for it alone with GP_FLAG_SPMM_CPASYNC_WIDE set (the same
+ * kernels and grid, the same reduction order).
+ *
+ * Worker streams (GP_FLAG_BATCH_STREAMS, FP64, GP_FLAG_LOGDET_TAYLOR, the
+ * fault flags, or another GP_FLAG_SPMM_* form): opts->batch_workers workers
+ * each take whole instances, largest first, on their own stream, and each
+ * instance's result is the one gp_lml_grad gives for it alone with the same
+ * options. */
 int gp_lml_grad_batched(gp_ctx* ctx, int32_t n_inst, const int64_t* offsets,
                         const double* x, const double* y, const double* h,
                         const gp_opts* opts, double* lml, double* grad, gp_info* info);

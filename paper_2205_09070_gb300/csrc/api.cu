@@ -81,6 +81,10 @@ double event_ms(cudaEvent_t a, cudaEvent_t b) {
 
 namespace {
 
+// gp_lml_grad_batched, grouped CG launches: instances per wave (one worker
+// context each)
+constexpr int kBatchWave = 256;
+
 void reset_counters(gp_ctx* c, int flags) {
   c->flags = flags;
   c->launches = 0;
@@ -191,47 +195,64 @@ int read_scalars(gp_ctx* c, gp::AsmScalars* hs) {
   return GP_OK;
 }
 
-// Assemble, solve [y, probes], SLQ, optional adjoint.
-int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const double* h, const gp_opts* o,
-             double* lml, double* grad, gp_info* info) {
-  if (!c || !lml || n < 0 || (n > 0 && (!x || !y))) return GP_ERR_INVALID_ARG;
+// One evaluation between its phases: the batched path runs the CG runs of
+// many instances together between the front and the back of each.
+struct EvalRun {
+  const double *xd = nullptr, *yd = nullptr;
+  int64_t n = 0;
+  int nv = 0, k = 0, kp = 0;
+  bool taylor = false;
+  int iters = 0, lanczos_iters = 0;
+  double max_rel = 0.0;
+  int cg_status = GP_OK;
+};
+
+// Stage the inputs in, assemble, and set up the preconditioner and the terms
+// of the inactive points.
+int eval_front(gp_ctx* c, const double* x, const double* y, int64_t n, const double* h, const gp_opts* o,
+               EvalRun* r) {
+  if (!c || n < 0 || (n > 0 && (!x || !y))) return GP_ERR_INVALID_ARG;
   GP_CHECK(check_h(c, h));
   GP_CHECK(check_opts(o, true));
   GP_CUDA(cudaSetDevice(c->device));
   reset_counters(c, o->flags);
   Timer tm(c);
   tm.mark(0);
-  const double *xd = nullptr, *yd = nullptr;
-  GP_CHECK(stage_in(c, c->x_in, x, (size_t)n * c->dim, &xd));
-  GP_CHECK(stage_in(c, c->y_in, y, (size_t)n, &yd));
-  GP_CHECK(gp::assemble(c, xd, n, h, o->precision));
+  r->n = n;
+  GP_CHECK(stage_in(c, c->x_in, x, (size_t)n * c->dim, &r->xd));
+  GP_CHECK(stage_in(c, c->y_in, y, (size_t)n, &r->yd));
+  GP_CHECK(gp::assemble(c, r->xd, n, h, o->precision));
   tm.mark(1);
   if (o->flags & (GP_FLAG_FAULT_NOT_SPD | GP_FLAG_FAULT_NAN)) GP_CHECK(gp::inject_matrix_fault(c, o->flags));
   GP_CHECK(gp::precond_setup(c, o->precond_block));
-  GP_CHECK(gp::inactive_terms(c, yd));
-  const int nv = o->n_probes;
-  const int k = 1 + nv;
-  const int kp = (k + 3) / 4 * 4;
-  int iters = 0, lanczos_iters = 0;
-  double max_rel = 0.0;
-  int cg_status;
+  GP_CHECK(gp::inactive_terms(c, r->yd));
+  r->nv = o->n_probes;
+  r->k = 1 + r->nv;
+  r->kp = (r->k + 3) / 4 * 4;
   // the log-determinant estimator: SLQ, or the truncated Taylor series the
   // paper cites (FP32 path; lanczos_steps terms on the same probes)
-  const bool taylor = (o->flags & GP_FLAG_LOGDET_TAYLOR) != 0;
-  if (taylor && o->precision != GP_FP32_MIXED) return GP_ERR_UNSUPPORTED;
+  r->taylor = (o->flags & GP_FLAG_LOGDET_TAYLOR) != 0;
+  if (r->taylor && o->precision != GP_FP32_MIXED) return GP_ERR_UNSUPPORTED;
+  return GP_OK;
+}
+
+// The solves of one evaluation on its own context.
+int eval_solve(gp_ctx* c, const gp_opts* o, EvalRun* r) {
+  const int nv = r->nv, k = r->k, kp = r->kp;
+  const double* yd = r->yd;
   if (o->precision == GP_FP64) {
-    cg_status = gp::cg_run_fp64(c, k, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
-                                &iters, &max_rel);
-  } else if (taylor) {
+    r->cg_status = gp::cg_run_fp64(c, k, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol,
+                                   o->check_every, &r->iters, &r->max_rel);
+  } else if (r->taylor) {
     // the solves alone (preconditioned when asked), then the series on V = C^k Z
-    cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters,
-                           &max_rel, c->pc_block > 0);
-    if (cg_status == GP_OK || cg_status == GP_ERR_NOT_CONVERGED)
+    r->cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &r->iters,
+                              &r->max_rel, c->pc_block > 0);
+    if (r->cg_status == GP_OK || r->cg_status == GP_ERR_NOT_CONVERGED)
       GP_CHECK(gp::taylor_logdet(c, nv, kp, o->lanczos_steps));
   } else if (c->pc_block == 0) {
     // one plain CG run: its first lanczos_steps coefficients feed SLQ
-    cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol, o->check_every,
-                           &iters, &max_rel, false);
+    r->cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->max_iter, o->cg_rtol,
+                              o->check_every, &r->iters, &r->max_rel, false);
   } else {
     // SLQ needs the Lanczos coefficients of Khat itself from the probes: a
     // short plain run of lanczos_steps iterations (expected not to converge),
@@ -240,16 +261,29 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
     // (one check interval of lanczos_steps iterations: the run always goes to
     // its cap, so shorter intervals only add host checks and idle launches)
     const int lst = gp::cg_run(c, k, kp, yd, nv, o->seed, o->lanczos_steps, o->lanczos_steps, o->cg_rtol,
-                               o->lanczos_steps, &lanczos_iters, &lanczos_rel, false);
+                               o->lanczos_steps, &r->lanczos_iters, &lanczos_rel, false);
     if (lst != GP_OK && lst != GP_ERR_NOT_CONVERGED) return lst;
     // the eigen-solves overlap the preconditioned run (side stream)
     GP_CHECK(gp::slq(c, nv, kp, true));
     // the preconditioned solves start from the Lanczos run's iterate
-    cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &iters,
-                           &max_rel, true, true);
+    r->cg_status = gp::cg_run(c, k, kp, yd, nv, o->seed, 0, o->max_iter, o->cg_rtol, o->check_every, &r->iters,
+                              &r->max_rel, true, true);
     const int jst = gp::slq_join(c);
     if (jst != GP_OK) return jst;
   }
+  return GP_OK;
+}
+
+// Everything after the solves: the quadratic form, SLQ when no
+// preconditioned run overlapped it, the adjoint gradient, and ln L.
+int eval_back(gp_ctx* c, const gp_opts* o, const EvalRun& r, double* lml, double* grad, gp_info* info) {
+  const int64_t n = r.n;
+  const int nv = r.nv, k = r.k, kp = r.kp;
+  const double* yd = r.yd;
+  const bool taylor = r.taylor;
+  const int cg_status = r.cg_status, iters = r.iters, lanczos_iters = r.lanczos_iters;
+  const double max_rel = r.max_rel;
+  Timer tm(c);
   if (cg_status != GP_OK && cg_status != GP_ERR_NOT_CONVERGED) return cg_status;
   GP_CHECK(gp::quad_form(c, yd, kp));
   if (!taylor && (o->precision == GP_FP64 || c->pc_block == 0)) GP_CHECK(gp::slq(c, nv, kp));
@@ -314,6 +348,16 @@ int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const doubl
     fill_counters(c, info);
   }
   return cg_status;
+}
+
+// Assemble, solve [y, probes], SLQ, optional adjoint.
+int evaluate(gp_ctx* c, const double* x, const double* y, int64_t n, const double* h, const gp_opts* o,
+             double* lml, double* grad, gp_info* info) {
+  if (!c || !lml) return GP_ERR_INVALID_ARG;
+  EvalRun r;
+  GP_CHECK(eval_front(c, x, y, n, h, o, &r));
+  GP_CHECK(eval_solve(c, o, &r));
+  return eval_back(c, o, r, lml, grad, info);
 }
 
 }  // namespace
@@ -433,7 +477,7 @@ int gp_destroy(gp_ctx* c) {
                         &c->bval,   &c->slq_g,  &c->pc_Minv,    &c->pc_part,   &c->Z,
                         &c->xstar_in, &c->pred_tmp, &c->slq_steps, &c->taylor,
                         &c->w_cnt,  &c->w_tseg, &c->w_trun,     &c->w_trec,    &c->w_segd,    &c->w_runs,
-                        &c->w_rec,  &c->pv_B,   &c->pv_prior};
+                        &c->w_rec,  &c->pv_B,   &c->pv_prior, &c->grp_inst, &c->grp_map};
   for (gp::DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -664,8 +708,19 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
   const int64_t P = (int64_t)c->nb * (c->dim + 2) + 3 + (c->core == GP_CORE_SQEXP ? 1 : 0);
   int nw = o->batch_workers > 0 ? o->batch_workers : 8;
   if (nw > n_inst) nw = n_inst;
+  // the CG runs of the instances as grouped launches, unless the options ask
+  // for what those do not cover (FP64, the Taylor series, injected faults, a
+  // product form other than the wide cp.async one) or for the worker streams
+  const int spmm_flags = o->flags & (GP_FLAG_SPMM_CPASYNC | GP_FLAG_SPMM_TMA | GP_FLAG_SPMM_TMA_WIDE |
+                                     GP_FLAG_SPMM_CPASYNC_WIDE | GP_FLAG_SPMM_WINDOW);
+  const bool grouped = !(o->flags & GP_FLAG_BATCH_STREAMS) && o->precision == GP_FP32_MIXED &&
+                       !(o->flags & (GP_FLAG_LOGDET_TAYLOR | GP_FLAG_FAULT_OOM | GP_FLAG_FAULT_NOT_SPD |
+                                     GP_FLAG_FAULT_NAN)) &&
+                       (spmm_flags == 0 || spmm_flags == GP_FLAG_SPMM_CPASYNC_WIDE);
+  // grouped: one worker context per instance of a wave; else one per worker
+  const int nctx = grouped ? (n_inst < kBatchWave ? n_inst : kBatchWave) : nw;
   // worker contexts: own stream, workspace and CG graphs; kept for later calls
-  while ((int)c->workers.size() < nw) {
+  while ((int)c->workers.size() < nctx) {
     cudaStream_t s = nullptr;
     GP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     const gp_kernel_desc d{c->dim, c->n1, c->n2, c->beta, c->core};
@@ -683,7 +738,8 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
   cudaEvent_t ready = nullptr;
   GP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
   GP_CUDA(cudaEventRecord(ready, c->stream));
-  for (int wi = 0; wi < nw; ++wi) GP_CUDA(cudaStreamWaitEvent(c->workers[wi]->stream, ready, 0));
+  for (int wi = 0; wi < nctx; ++wi) GP_CUDA(cudaStreamWaitEvent(c->workers[wi]->stream, ready, 0));
+  cudaEventDestroy(ready);
   // largest instances first, so the tail is short
   std::vector<int32_t> order(n_inst);
   for (int32_t q = 0; q < n_inst; ++q) order[q] = q;
@@ -693,26 +749,115 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
   std::vector<double> lml_h(n_inst, 0.0), grad_h(grad ? (size_t)n_inst * P : 0);
   std::vector<gp_info> infos(n_inst);
   std::vector<int> status(n_inst, GP_OK);
-  std::atomic<int32_t> next{0};
   std::atomic<bool> abort{false};
-  auto work = [&](int wi) {
-    cudaSetDevice(c->device);
-    gp_ctx* w = c->workers[wi];
-    for (;;) {
-      const int32_t t = next.fetch_add(1);
-      if (t >= n_inst || abort.load()) break;
-      const int32_t q = order[t];
-      const int64_t a = offsets[q], b = offsets[q + 1];
-      status[q] = evaluate(w, x ? x + a * c->dim : nullptr, y ? y + a : nullptr, b - a, h + q * P, o, &lml_h[q],
-                           grad ? grad_h.data() + (size_t)q * P : nullptr, &infos[q]);
-      if (status[q] != GP_OK && status[q] != GP_ERR_NOT_CONVERGED) abort.store(true);
-    }
+  auto failed = [](int s) { return s != GP_OK && s != GP_ERR_NOT_CONVERGED; };
+  // fn(t, wi) for t < count, pulled by nw host threads (wi: the thread)
+  auto pool = [&](int32_t count, const auto& fn) {
+    std::atomic<int32_t> next{0};
+    auto work = [&](int wi) {
+      cudaSetDevice(c->device);
+      for (;;) {
+        const int32_t t = next.fetch_add(1);
+        if (t >= count || abort.load()) break;
+        fn(t, wi);
+      }
+    };
+    std::vector<std::thread> threads;
+    for (int wi = 1; wi < nw; ++wi) threads.emplace_back(work, wi);
+    work(0);
+    for (std::thread& t : threads) t.join();
   };
-  std::vector<std::thread> pool;
-  for (int wi = 1; wi < nw; ++wi) pool.emplace_back(work, wi);
-  work(0);
-  for (std::thread& t : pool) t.join();
-  cudaEventDestroy(ready);
+  auto xs = [&](int32_t q) { return x ? x + offsets[q] * c->dim : nullptr; };
+  auto ysrc = [&](int32_t q) { return y ? y + offsets[q] : nullptr; };
+  auto gout = [&](int32_t q) { return grad ? grad_h.data() + (size_t)q * P : nullptr; };
+  const int64_t launches0 = c->launches;
+  if (!grouped) {
+    // each instance on its own through evaluate, on the pulling thread's context
+    pool(n_inst, [&](int32_t t, int wi) {
+      const int32_t q = order[t];
+      status[q] = evaluate(c->workers[wi], xs(q), ysrc(q), offsets[q + 1] - offsets[q], h + q * P, o, &lml_h[q],
+                           gout(q), &infos[q]);
+      if (failed(status[q])) abort.store(true);
+    });
+  } else {
+    for (int32_t w0 = 0; w0 < n_inst && !abort.load(); w0 += nctx) {
+      const int32_t nwv = n_inst - w0 < nctx ? n_inst - w0 : nctx;
+      // instance j of the wave: order[w0 + j] on worker context j
+      std::vector<EvalRun> runs(nwv);
+      pool(nwv, [&](int32_t j, int) {
+        const int32_t q = order[w0 + j];
+        status[q] = eval_front(c->workers[j], xs(q), ysrc(q), offsets[q + 1] - offsets[q], h + q * P, o, &runs[j]);
+        if (failed(status[q])) abort.store(true);
+      });
+      if (abort.load()) break;
+      // the CG runs of the wave as grouped launches on the context stream
+      const int nv = runs[0].nv, k = runs[0].k, kp = runs[0].kp;
+      std::vector<int32_t> pcj, plainj;
+      for (int32_t j = 0; j < nwv; ++j) {
+        const gp_ctx* w = c->workers[j];
+        if (w->n_act > 0) (w->pc_block > 0 ? pcj : plainj).push_back(j);
+      }
+      auto run_group = [&](const std::vector<int32_t>& js, int m_hist, int max_iter, int check_every, bool use_pc,
+                           bool warm, bool lanczos) -> int {
+        const size_t m = js.size();
+        if (m == 0) return GP_OK;
+        std::vector<gp_ctx*> cs(m);
+        std::vector<const double*> ys(m);
+        std::vector<int> it(m), st(m);
+        std::vector<double> rel(m);
+        for (size_t i = 0; i < m; ++i) {
+          cs[i] = c->workers[js[i]];
+          ys[i] = runs[js[i]].yd;
+        }
+        GP_CHECK(gp::cg_run_group(c, cs.data(), (int)m, k, kp, ys.data(), nv, o->seed, m_hist, max_iter,
+                                  o->cg_rtol, check_every, use_pc, warm, it.data(), rel.data(), st.data()));
+        for (size_t i = 0; i < m; ++i) {
+          EvalRun& r = runs[js[i]];
+          const int32_t q = order[w0 + js[i]];
+          if (lanczos) {
+            r.lanczos_iters = it[i];
+            if (failed(st[i])) status[q] = st[i];
+          } else {
+            r.iters = it[i];
+            r.max_rel = rel[i];
+            r.cg_status = st[i];
+          }
+        }
+        return GP_OK;
+      };
+      const int L = o->lanczos_steps;
+      int gst = GP_OK;
+      // one plain run per instance: its first lanczos_steps coefficients feed SLQ
+      if (gst == GP_OK) gst = run_group(plainj, L, o->max_iter, o->check_every, false, false, false);
+      if (gst == GP_OK && !pcj.empty()) {
+        // the Lanczos run of lanczos_steps plain iterations, SLQ on each
+        // instance's side stream, then the preconditioned solves from the
+        // Lanczos iterate (as eval_solve does for one instance)
+        gst = run_group(pcj, L, L, L, false, false, true);
+        std::vector<int32_t> ok;
+        for (int32_t j : pcj) {
+          const int32_t q = order[w0 + j];
+          if (gst == GP_OK && !failed(status[q])) status[q] = gp::slq(c->workers[j], nv, kp, true);
+          if (!failed(status[q])) ok.push_back(j);
+        }
+        if (gst == GP_OK) gst = run_group(ok, 0, o->max_iter, o->check_every, true, true, false);
+        for (int32_t j : ok) {
+          const int32_t q = order[w0 + j];
+          const int jst = gp::slq_join(c->workers[j]);
+          if (jst != GP_OK) status[q] = jst;
+        }
+      }
+      if (gst != GP_OK) return gst;
+      for (int32_t j = 0; j < nwv; ++j)
+        if (failed(status[order[w0 + j]])) abort.store(true);
+      if (abort.load()) break;
+      pool(nwv, [&](int32_t j, int) {
+        const int32_t q = order[w0 + j];
+        status[q] = eval_back(c->workers[j], o, runs[j], &lml_h[q], gout(q), &infos[q]);
+        if (failed(status[q])) abort.store(true);
+      });
+    }
+  }
   int result = GP_OK;
   for (int32_t q = 0; q < n_inst; ++q) {
     if (status[q] != GP_OK && status[q] != GP_ERR_NOT_CONVERGED) return status[q];
@@ -748,6 +893,7 @@ int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const
       // the instances' common SpMM form, -1 if they differ
       info->spmm_variant = q == 0 || inf.spmm_variant == info->spmm_variant ? inf.spmm_variant : -1;
     }
+    info->launches += c->launches - launches0;  // the grouped launches
   }
   return result;
 }

@@ -121,6 +121,34 @@ struct SpmmPlan {
   alignas(64) unsigned char tmap[128] = {};
 };
 
+// Grouped CG launches: the CG runs of many independent GPs advanced by the
+// same launches.  A CTA of a grouped launch works for one instance exactly as
+// the CTA of the same index in that instance's own launch would, so each
+// instance computes what a run on its own computes.
+enum GroupKind { kGSpmm = 0, kGPc = 1, kGUpd = 2, kGUpdR = 3 };
+struct GInst {
+  int64_t n, nblk;  // active rows, 8-row block rows
+  const int64_t* brp;
+  const int32_t* bcol;
+  const float4* bval;
+  float4 *X, *R, *P, *Q, *Z;
+  const float4* D;  // what the X, P update adds: Z when preconditioned, else R
+  const float* Minv;
+  double *part_a, *part_b, *hist_alpha, *hist_beta;
+  CgState* st;
+  int grid[4];  // the instance's own grid size per GroupKind
+};
+// inst == nullptr: an ordinary launch for one GP with its own arguments.
+// Otherwise CTA b works for instance map[b] >> kGroupShift as its CTA
+// map[b] & kGroupMask (for the per-column kernels, the column).
+struct Group {
+  const GInst* inst;
+  const uint32_t* map;
+};
+constexpr int kGroupShift = 20;
+constexpr uint32_t kGroupMask = (1u << kGroupShift) - 1u;
+constexpr int kMaxGroup = 1 << (32 - kGroupShift);  // instances per grouped launch
+
 }  // namespace gp
 
 struct gp_ctx {
@@ -143,6 +171,7 @@ struct gp_ctx {
   gp::DevBuf x_in, y_in, out_tmp;
   gp::DevBuf xstar_in, pred_tmp;  // gp_predict: staged test points, posterior means
   gp::DevBuf pv_B, pv_prior;      // gp_predict_var: right-hand-side block, prior variances
+  gp::DevBuf grp_inst, grp_map;   // grouped CG launches: instance table, per-CTA maps
   gp::DevBuf taylor;              // scalars of the truncated-Taylor log-determinant
   gp::DevBuf bump;
   gp::DevBuf mask0, F0, pos;
@@ -241,6 +270,15 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y_dev, int n_probes, uint64_t
            int lanczos_steps, int max_iter, double rtol, int check_every,
            int* iters_out, double* max_rel_resid, bool use_pc, bool warm = false,
            const float* rhs = nullptr);
+// The CG runs of nc GPs (contexts cs, each assembled, with its own stream) as
+// one: every context is prepared as cg_run prepares it, then the iterations
+// of all of them run as grouped launches on the owner's stream (an instance
+// leaves the group when its run finishes), then each is read as cg_run reads
+// it.  The product is the cp.async form, wide where kp allows, for every
+// instance.  ys[i]: context i's targets; iters, max_rel, status: per context.
+int cg_run_group(gp_ctx* owner, gp_ctx* const* cs, int nc, int k, int kp, const double* const* ys, int n_probes,
+                 uint64_t seed, int lanczos_steps, int max_iter, double rtol, int check_every, bool use_pc,
+                 bool warm, int* iters, double* max_rel, int* status);
 // rhs: k columns of N_act doubles each (column-major) instead of [yhat, probes]
 int cg_run_fp64(gp_ctx* c, int k, const double* y_dev, int n_probes, uint64_t seed,
                 int lanczos_steps, int max_iter, double rtol, int check_every,
@@ -289,11 +327,23 @@ void window_launch(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st,
 // the same product with another input / output block (cp.async forms only:
 // the TMA forms carry a tensor map of P)
 void spmm_launch_io(const SpmmPlan& plan, cudaStream_t s, gp_ctx* c, CgState* st, const float* in, float* out);
+// a grouped launch of a cp.async form (total CTAs over all instances)
+void spmm_launch_group(const SpmmPlan& plan, cudaStream_t s, unsigned total, Group g);
 
 }  // namespace gp
 
 // ---------------------------------------------------------------- device utils
 namespace gpd {
+
+// A grouped launch (gp::Group): this CTA's instance, and its index bx in that
+// instance's own grid of gx CTAs for launches of the given kind.
+__device__ __forceinline__ const gp::GInst* group_cta(const gp::Group& g, int kind, int& bx, int& gx) {
+  const uint32_t m = __ldg(g.map + blockIdx.x);
+  const gp::GInst* I = g.inst + (m >> gp::kGroupShift);
+  bx = (int)(m & gp::kGroupMask);
+  gx = I->grid[kind];
+  return I;
+}
 
 // Cell of a point in the uniform search grid: floor((x - lo) / h) per axis,
 // clamped to the grid (a point outside it lands in a boundary cell; the exact

@@ -20,6 +20,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "gp_internal.cuh"
 
 namespace {
@@ -222,11 +225,20 @@ __device__ inline double2 column_sums(const double* __restrict__ part, int nb, i
 // before the sum, so that its latency overlaps the sum's.
 __global__ void __launch_bounds__(kColThreads) k_cg_alpha_cols(const double* __restrict__ part_pq, int npq,
                                                                int k, int kp, gp::CgState* st,
-                                                               double* hist_alpha, int m_hist) {
+                                                               double* hist_alpha, int m_hist, gp::Group g) {
+  int c = blockIdx.x;
+  if (g.inst) {
+    const uint32_t m = __ldg(g.map + blockIdx.x);
+    const gp::GInst* I = g.inst + (m >> gp::kGroupShift);
+    c = (int)(m & gp::kGroupMask);
+    part_pq = I->part_a;
+    npq = I->grid[gp::kGSpmm];
+    st = I->st;
+    hist_alpha = I->hist_alpha;
+  }
   const int it = st->iter;
   if (st->fin[it & 1]) return;
   __shared__ double red0[kColThreads], red1[kColThreads];
-  const int c = blockIdx.x;
   bool running = false;
   double rho = 0.0;
   if (threadIdx.x == 0) {
@@ -259,16 +271,25 @@ __global__ void __launch_bounds__(kColThreads) k_cg_alpha_cols(const double* __r
 // CTA to finish reads and clears the count and advances the iteration.
 __global__ void __launch_bounds__(kColThreads) k_cg_beta_cols(const double* __restrict__ part, int nrr, int k,
                                                               int kp, int pc, gp::CgState* st, double* hist_beta,
-                                                              int m_hist) {
+                                                              int m_hist, gp::Group g) {
+  int c = blockIdx.x;
+  if (g.inst) {
+    const uint32_t m = __ldg(g.map + blockIdx.x);
+    const gp::GInst* I = g.inst + (m >> gp::kGroupShift);
+    c = (int)(m & gp::kGroupMask);
+    part = I->part_b;
+    nrr = I->grid[pc ? gp::kGPc : gp::kGUpdR];
+    st = I->st;
+    hist_beta = I->hist_beta;
+  }
   const int it = st->iter;
   const int cur = it & 1, nxt = (it + 1) & 1;
   if (st->fin[cur]) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->fin[nxt] = 1;
+    if (c == 0 && threadIdx.x == 0) st->fin[nxt] = 1;
     return;
   }
   __shared__ double red0[kColThreads], red1[kColThreads];
   __shared__ bool last;
-  const int c = blockIdx.x;
   const int width = pc ? 2 * kp : kp;
   bool was_done = true;
   double rrp = 0.0, crr = 0.0, lim = 0.0;
@@ -299,7 +320,7 @@ __global__ void __launch_bounds__(kColThreads) k_cg_beta_cols(const double* __re
     st->donep[nxt][c] = done;
     if (c < k && !done) atomicAdd(&st->run_cnt, 1u);
     __threadfence();
-    last = atomicInc(&st->ticket_b, gridDim.x - 1) == gridDim.x - 1;
+    last = atomicInc(&st->ticket_b, kp - 1) == (unsigned)kp - 1;
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
@@ -320,7 +341,16 @@ constexpr int kUpdRThreads = 1024;
 
 __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, const float4* __restrict__ Q,
                                                             float4* __restrict__ R, double* __restrict__ part_rr,
-                                                            const gp::CgState* st) {
+                                                            const gp::CgState* st, gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGUpdR, bx, gx);
+    n = I->n;
+    Q = I->Q;
+    R = I->R;
+    part_rr = I->part_b;
+    st = I->st;
+  }
   if (st->fin[st->iter & 1]) return;
   __shared__ double red[kUpdRThreads][4];
   const int ny = kUpdRThreads / kq;
@@ -329,8 +359,8 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
   if (ty < ny) {
     const float4 a = make_float4((float)st->alpha[4 * tx], (float)st->alpha[4 * tx + 1],
                                  (float)st->alpha[4 * tx + 2], (float)st->alpha[4 * tx + 3]);
-    const int64_t stride = (int64_t)gridDim.x * ny;
-    int64_t p = (int64_t)blockIdx.x * ny + ty;
+    const int64_t stride = (int64_t)gx * ny;
+    int64_t p = (int64_t)bx * ny + ty;
     for (; p + 3 * stride < n; p += 4 * stride) {
       float4 r[4], q[4];
 #pragma unroll
@@ -380,7 +410,7 @@ __global__ void __launch_bounds__(kUpdRThreads) k_upd_r_f32(int64_t n, int kq, c
     __syncthreads();
   }
   const int kp = 4 * kq;
-  if (threadIdx.x < kp) part_rr[(int64_t)blockIdx.x * kp + threadIdx.x] = red[threadIdx.x / 4][threadIdx.x % 4];
+  if (threadIdx.x < kp) part_rr[(int64_t)bx * kp + threadIdx.x] = red[threadIdx.x / 4][threadIdx.x % 4];
 }
 
 // Start of a CG run on a caller-given right-hand-side block B (N_act x kp,
@@ -508,7 +538,18 @@ template <bool INIT, int B>
 __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
                                                              const float4* __restrict__ Q, float4* __restrict__ R,
                                                              float4* __restrict__ Z, const float* __restrict__ Minv,
-                                                             double* __restrict__ part, const gp::CgState* st) {
+                                                             double* __restrict__ part, const gp::CgState* st, gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGPc, bx, gx);
+    n = I->n;
+    Q = I->Q;
+    R = I->R;
+    Z = I->Z;
+    Minv = I->Minv;
+    part = I->part_b;
+    st = I->st;
+  }
   if (!INIT && st->fin[st->iter & 1]) return;
   constexpr int kPcStages = pc_stages(B);
   constexpr int RPL = pc_rows_per_lane(B);
@@ -553,12 +594,12 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
   };
   gpd::Dot2 rz[4], rr[4];
   const int kb = ((RPL * lane) / B) * B;  // first tile row of this lane's block
-  int64_t tile = blockIdx.x;
+  int64_t tile = bx;
 #pragma unroll
-  for (int q = 0; q < kPcStages - 1; ++q) issue(tile + q * (int64_t)gridDim.x, q);
-  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+  for (int q = 0; q < kPcStages - 1; ++q) issue(tile + q * (int64_t)gx, q);
+  for (int i = 0; tile < ntiles; ++i, tile += gx) {
     const int s = i % kPcStages;
-    issue(tile + (kPcStages - 1) * (int64_t)gridDim.x, (i + kPcStages - 1) % kPcStages);
+    issue(tile + (kPcStages - 1) * (int64_t)gx, (i + kPcStages - 1) % kPcStages);
     cp_async_wait<kPcStages - 1>();  // this thread's copies of tile i have landed
     const int64_t r0 = tile * TILE;
     if (!INIT) {
@@ -638,7 +679,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pc(int64_t n, int kq,
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
   if (lane == 0) {
     const int kp = 4 * kq;
-    double* prow = part + (int64_t)blockIdx.x * 2 * kp;
+    double* prow = part + (int64_t)bx * 2 * kp;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       prow[4 * w + j] = v[j];
@@ -661,7 +702,18 @@ template <bool INIT, int B>
 __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
                                                               const float4* __restrict__ Q, float4* __restrict__ R,
                                                               float4* __restrict__ Z, const float* __restrict__ Minv,
-                                                              double* __restrict__ part, const gp::CgState* st) {
+                                                              double* __restrict__ part, const gp::CgState* st, gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGPc, bx, gx);
+    n = I->n;
+    Q = I->Q;
+    R = I->R;
+    Z = I->Z;
+    Minv = I->Minv;
+    part = I->part_b;
+    st = I->st;
+  }
   if (!INIT && st->fin[st->iter & 1]) return;
   constexpr int S = pc_stages(B);
   constexpr int RPL = B / kPcLanes;  // rows per lane
@@ -674,7 +726,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
   float4* Qs = Rs + S * nthr;      // S x nthr
   float* Ms = (float*)(Qs + S * nthr);  // S x 32 lane groups x ldm
   const int64_t nblk = (n + B - 1) / B;
-  const int64_t mine = blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t mine = bx < nblk ? (nblk - 1 - bx) / gx + 1 : 0;
   const int64_t npan = mine * NPB;
   const int64_t nrows_pc = nblk * B;
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -685,7 +737,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
   }
   auto issue = [&](int64_t pi, int s) {
     if (pi < npan) {
-      const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+      const int64_t blk = bx + (pi / NPB) * gx;
       const int q = (int)(pi % NPB);
       const int64_t r0 = blk * B + kPcPanel * q;  // first row of the panel
       const bool ok = r0 + t / kq < n;
@@ -711,7 +763,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
     const int s = (int)(pi % S);
     cp_async_wait<S - 2>();  // this thread's copies of panel pi have landed
     const int q = (int)(pi % NPB);
-    const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+    const int64_t blk = bx + (pi / NPB) * gx;
     const int64_t r0 = blk * B + kPcPanel * q;
     if (q == 0) {
 #pragma unroll
@@ -791,7 +843,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcp(int64_t n, int kq,
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
   if (lane == 0) {
     const int kp = 4 * kq;
-    double* prow = part + (int64_t)blockIdx.x * 2 * kp;
+    double* prow = part + (int64_t)bx * 2 * kp;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       prow[4 * w + j] = v[j];
@@ -819,7 +871,18 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
                                                                  float4* __restrict__ R, float4* __restrict__ Z,
                                                                  const float* __restrict__ Minv,
                                                                  double* __restrict__ part,
-                                                                 const gp::CgState* st) {
+                                                                 const gp::CgState* st, gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGPc, bx, gx);
+    n = I->n;
+    Q = I->Q;
+    R = I->R;
+    Z = I->Z;
+    Minv = I->Minv;
+    part = I->part_b;
+    st = I->st;
+  }
   if (!INIT && st->fin[st->iter & 1]) return;
   constexpr int B = 128;
   constexpr int S = pc_stages(B);
@@ -833,7 +896,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
   float4* Qs = Rs + S * nthr;            // S x nthr
   float* Ms = (float*)(Qs + S * nthr);   // S x 32 x ldm: rows of M^-1
   const int64_t nblk = (n + B - 1) / B;
-  const int64_t mine = blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t mine = bx < nblk ? (nblk - 1 - bx) / gx + 1 : 0;
   const int64_t npan = mine * NPB;
   const int64_t nrows_pc = nblk * B;
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -844,7 +907,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
   }
   auto issue = [&](int64_t pi, int s) {
     if (pi < npan) {
-      const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+      const int64_t blk = bx + (pi / NPB) * gx;
       const int q = (int)(pi % NPB);
       const int64_t r0 = blk * B + kPcPanel * q;  // first row of the panel
       const bool ok = r0 + t / kq < n;
@@ -872,7 +935,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
     const int s = (int)(pi % S);
     cp_async_wait<S - 2>();  // this thread's copies of panel pi have landed
     const int q = (int)(pi % NPB);
-    const int64_t blk = blockIdx.x + (pi / NPB) * gridDim.x;
+    const int64_t blk = bx + (pi / NPB) * gx;
     const int64_t r0 = blk * B + kPcPanel * q;
     if (q == 0) {
 #pragma unroll
@@ -955,7 +1018,7 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(kFull, v[j], o);
   if (lane == 0) {
     const int kp = 4 * kq;
-    double* prow = part + (int64_t)blockIdx.x * 2 * kp;
+    double* prow = part + (int64_t)bx * 2 * kp;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       prow[4 * w + j] = v[j];
@@ -964,7 +1027,8 @@ __global__ void __launch_bounds__(kPcMaxThreads) k_upd_r_pcq(int64_t n, int kq,
   }
 }
 
-typedef void (*UpdPcFn)(int64_t, int, const float4*, float4*, float4*, const float*, double*, const gp::CgState*);
+typedef void (*UpdPcFn)(int64_t, int, const float4*, float4*, float4*, const float*, double*, const gp::CgState*,
+                        gp::Group);
 
 template <bool INIT>
 UpdPcFn upd_pc_fn(int B) {
@@ -1019,7 +1083,16 @@ __global__ void __launch_bounds__(kRedThreads) k_pc_state(const double* __restri
 // preconditioner); runs for iteration it unless the run had already finished.
 __global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, float4* __restrict__ X,
                                                             const float4* __restrict__ R, float4* __restrict__ P,
-                                                            const gp::CgState* st) {
+                                                            const gp::CgState* st, gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGUpd, bx, gx);
+    n = I->n;
+    X = I->X;
+    R = I->D;
+    P = I->P;
+    st = I->st;
+  }
   // beta has already advanced the counter for this iteration (or, when the
   // run had finished, marked the parity slot of it - 1 finished as well)
   if (st->fin[(st->iter - 1) & 1]) return;
@@ -1030,8 +1103,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_upd_xp_f32(int64_t n, int kq, f
                                (float)st->alpha[4 * tx + 3]);
   const float4 b = make_float4((float)st->beta[4 * tx], (float)st->beta[4 * tx + 1], (float)st->beta[4 * tx + 2],
                                (float)st->beta[4 * tx + 3]);
-  const int64_t stride = (int64_t)gridDim.x * ny;
-  int64_t p = (int64_t)blockIdx.x * ny + ty;
+  const int64_t stride = (int64_t)gx * ny;
+  int64_t p = (int64_t)bx * ny + ty;
   for (; p + stride < n; p += 2 * stride) {
     float4 po[2], r[2], x[2];
 #pragma unroll
@@ -1424,12 +1497,25 @@ int read_state(gp_ctx* c, gp::CgState* host) {
 
 namespace gp {
 
-int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
-           int check_every, int* iters_out, double* max_rel, bool use_pc, bool warm, const float* rhs) {
+namespace {
+
+// What the iterations of one FP32 CG run launch, fixed by its preparation.
+struct CgLoop {
+  SpmmPlan plan;
+  bool pc = false;
+  int kq = 0;
+  unsigned g_pc = 0, g_upd = 0, g_upd_r = 0;
+  size_t pc_smem = 0;
+  UpdPcFn upd_pc = nullptr;
+};
+
+// Everything of a run before its iterations (c->n_act > 0): buffers, the
+// starting state and residual (warm start, caller block, or [yhat, probes]),
+// the preconditioned start, and the launch shapes of the iterations, with the
+// SpMM form chosen under spmm_flags.
+int cg_prepare(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter,
+               double rtol, bool use_pc, bool warm, const float* rhs, int spmm_flags, CgLoop* L) {
   const int64_t n = c->n_act;
-  *iters_out = 0;
-  *max_rel = 0.0;
-  if (n == 0) return GP_OK;
   if (!spmm_available(GP_SPMM_CPASYNC, kp)) return GP_ERR_UNSUPPORTED;
   GP_CHECK(ensure(c, c->X, (size_t)n * kp * sizeof(float)));
   GP_CHECK(ensure(c, c->R, (size_t)n * kp * sizeof(float)));
@@ -1442,6 +1528,7 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
   GP_CHECK(ensure(c, c->hist_alpha, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
   GP_CHECK(ensure(c, c->hist_beta, (size_t)kMaxLanczos * kMaxCols * sizeof(double)));
   CgState* st = (CgState*)c->cg.p;
+  const Group none{nullptr, nullptr};
   // the warm start keeps rr0 = |B|^2 and relies on the preconditioned start
   // to set rho_0 from the new residual
   if (warm && !(use_pc && c->pc_block > 0)) return GP_ERR_INVALID_ARG;
@@ -1478,43 +1565,81 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     c->launches += 1;
   }
   // block-Jacobi preconditioned CG: Z = M^-1 R, beta from r^T z, stop on |r|
-  const bool pc = use_pc && c->pc_block > 0;
-  UpdPcFn upd_pc_init = nullptr, upd_pc = nullptr;
-  const int kq = kp / 4;
-  unsigned g_pc = 0;
-  size_t pc_smem = 0;
-  if (pc) {
-    pc_smem = pc_smem_bytes(kq, c->pc_block);
+  L->pc = use_pc && c->pc_block > 0;
+  L->kq = kp / 4;
+  const int kq = L->kq;
+  L->g_pc = 0;
+  L->pc_smem = 0;
+  L->upd_pc = nullptr;
+  if (L->pc) {
+    L->pc_smem = pc_smem_bytes(kq, c->pc_block);
     int smem_max = 0;
     GP_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    if (pc_smem > (size_t)smem_max) return GP_ERR_UNSUPPORTED;
-    upd_pc_init = upd_pc_fn<true>(c->pc_block);
-    upd_pc = upd_pc_fn<false>(c->pc_block);
-    if (!upd_pc_init || !upd_pc) return GP_ERR_UNSUPPORTED;
-    GP_CUDA(cudaFuncSetAttribute(upd_pc_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
-    GP_CUDA(cudaFuncSetAttribute(upd_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pc_smem));
+    if (L->pc_smem > (size_t)smem_max) return GP_ERR_UNSUPPORTED;
+    UpdPcFn upd_pc_init = upd_pc_fn<true>(c->pc_block);
+    L->upd_pc = upd_pc_fn<false>(c->pc_block);
+    if (!upd_pc_init || !L->upd_pc) return GP_ERR_UNSUPPORTED;
+    GP_CUDA(cudaFuncSetAttribute(upd_pc_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->pc_smem));
+    GP_CUDA(cudaFuncSetAttribute(L->upd_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->pc_smem));
     // two blocks per SM, two tiles each in flight: enough bytes in flight for
     // HBM without many partial rows for the one-block reduction
-    g_pc = grid_for(n, pc_tile(c->pc_block), c->num_sms * 2);
+    L->g_pc = grid_for(n, pc_tile(c->pc_block), c->num_sms * 2);
     GP_CHECK(ensure(c, c->Z, (size_t)n * kp * sizeof(float)));
-    GP_CHECK(ensure(c, c->part_b, (size_t)g_pc * 2 * kp * sizeof(double)));
-    upd_pc_init<<<g_pc, kPcLanes * kq, pc_smem, c->stream>>>(n, kq, nullptr, (float4*)c->R.p,
-                                                                 (float4*)c->P.p, (const float*)c->pc_Minv.p,
-                                                                 (double*)c->part_b.p, st);
-    k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)g_pc, k, kp, st);
+    GP_CHECK(ensure(c, c->part_b, (size_t)L->g_pc * 2 * kp * sizeof(double)));
+    upd_pc_init<<<L->g_pc, kPcLanes * kq, L->pc_smem, c->stream>>>(n, kq, nullptr, (float4*)c->R.p,
+                                                                     (float4*)c->P.p, (const float*)c->pc_Minv.p,
+                                                                     (double*)c->part_b.p, st, none);
+    k_pc_state<<<1, kRedThreads, 0, c->stream>>>((const double*)c->part_b.p, (int)L->g_pc, k, kp, st);
     GP_LAUNCH_CHECK();
     c->launches += 2;
   }
-  const int64_t nblk = c->nblk;
   // the SpMM form: forced by the flags, else the autotuner's for this shape
-  SpmmPlan plan;
-  GP_CHECK(spmm_select(c, kp, c->flags, st, &plan, k, m_hist));
-  c->spmm_variant = plan.variant;
-  const unsigned g_spmm = plan.grid;
-  const int ny = kUpdThreads / kq;
-  const unsigned g_upd = grid_for(n, ny, c->num_sms * 8);
-  const int ny_r = kUpdRThreads / kq;
-  const unsigned g_upd_r = grid_for(n, ny_r, c->num_sms);
+  GP_CHECK(spmm_select(c, kp, spmm_flags, st, &L->plan, k, m_hist));
+  c->spmm_variant = L->plan.variant;
+  L->g_upd = grid_for(n, kUpdThreads / kq, c->num_sms * 8);
+  L->g_upd_r = grid_for(n, kUpdRThreads / kq, c->num_sms);
+  return GP_OK;
+}
+
+// The outcome of a run from its final state: iterations, the largest relative
+// residual over the k columns, and the run's status.
+int cg_finish(gp_ctx* c, int k, int* iters_out, double* max_rel) {
+  CgState hs;
+  GP_CHECK(read_state(c, &hs));
+  *iters_out = hs.iter;
+  double mr = 0.0;
+  bool all_done = true;
+  const int par = hs.iter & 1;
+  for (int q = 0; q < k; ++q) {
+    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.crr[par][q] / hs.rr0[q]));
+    all_done = all_done && hs.donep[par][q];
+  }
+  *max_rel = mr;
+  c->bad_col = hs.bad_col;
+  c->bad_iter = hs.iter;
+  if (hs.status != GP_OK) return hs.status;
+  if (!all_done) return GP_ERR_NOT_CONVERGED;
+  return GP_OK;
+}
+
+}  // namespace
+
+int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,
+           int check_every, int* iters_out, double* max_rel, bool use_pc, bool warm, const float* rhs) {
+  const int64_t n = c->n_act;
+  *iters_out = 0;
+  *max_rel = 0.0;
+  if (n == 0) return GP_OK;
+  CgLoop L;
+  GP_CHECK(cg_prepare(c, k, kp, y, nv, seed, m_hist, max_iter, rtol, use_pc, warm, rhs, c->flags, &L));
+  CgState* st = (CgState*)c->cg.p;
+  const Group none{nullptr, nullptr};
+  const int64_t nblk = c->nblk;
+  const SpmmPlan& plan = L.plan;
+  const bool pc = L.pc;
+  const int kq = L.kq;
+  const unsigned g_spmm = plan.grid, g_pc = L.g_pc, g_upd = L.g_upd, g_upd_r = L.g_upd_r;
+  const size_t pc_smem = L.pc_smem;
   if (check_every <= 0) check_every = 16;
   if (check_every > 64) check_every = 64;
   const bool timed = (c->flags & GP_FLAG_TIME_KERNELS) != 0;
@@ -1530,21 +1655,21 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     if (ev1) cudaEventRecordWithFlags(ev1, sm, evf);
     if (!plan.fused_alpha)
       k_cg_alpha_cols<<<kp, kColThreads, 0, sm>>>((const double*)c->part_a.p, (int)g_spmm, k, kp, st,
-                                                  (double*)c->hist_alpha.p, m_hist);
+                                                  (double*)c->hist_alpha.p, m_hist, none);
     if (pc) {
-      upd_pc<<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, (const float4*)c->Q.p,
-                                                              (float4*)c->R.p, (float4*)c->Z.p,
-                                                              (const float*)c->pc_Minv.p, (double*)c->part_b.p, st);
+      L.upd_pc<<<g_pc, kPcLanes * kq, pc_smem, sm>>>(n, kq, (const float4*)c->Q.p, (float4*)c->R.p,
+                                                     (float4*)c->Z.p, (const float*)c->pc_Minv.p,
+                                                     (double*)c->part_b.p, st, none);
       k_cg_beta_cols<<<kp, kColThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_pc, k, kp, 1, st,
-                                                 (double*)c->hist_beta.p, m_hist);
+                                                 (double*)c->hist_beta.p, m_hist, none);
     } else {
       k_upd_r_f32<<<g_upd_r, kUpdRThreads, 0, sm>>>(n, kq, (const float4*)c->Q.p, (float4*)c->R.p,
-                                                    (double*)c->part_b.p, st);
+                                                    (double*)c->part_b.p, st, none);
       k_cg_beta_cols<<<kp, kColThreads, 0, sm>>>((const double*)c->part_b.p, (int)g_upd_r, k, kp, 0, st,
-                                                 (double*)c->hist_beta.p, m_hist);
+                                                 (double*)c->hist_beta.p, m_hist, none);
     }
     k_upd_xp_f32<<<g_upd, kUpdThreads, 0, sm>>>(n, kq, (float4*)c->X.p, (const float4*)(pc ? c->Z.p : c->R.p),
-                                                (float4*)c->P.p, st);
+                                                (float4*)c->P.p, st, none);
   };
   // graph of check_every iterations, rebuilt only when an argument changes
   // (with GP_FLAG_TIME_KERNELS the graph also records the SpMM events)
@@ -1607,21 +1732,174 @@ int cg_run(gp_ctx* c, int k, int kp, const double* y, int nv, uint64_t seed, int
     iter_before = hs.iter;
     if (hs.finished) break;
   }
-  GP_CHECK(read_state(c, &hs));
-  *iters_out = hs.iter;
-  double mr = 0.0;
-  bool all_done = true;
-  const int par = hs.iter & 1;
-  for (int q = 0; q < k; ++q) {
-    if (hs.rr0[q] > 0) mr = fmax(mr, sqrt(hs.crr[par][q] / hs.rr0[q]));
-    all_done = all_done && hs.donep[par][q];
+  return cg_finish(c, k, iters_out, max_rel);
+}
+
+namespace {
+
+// finished flag of every instance of a group (1 for those not in it)
+__global__ void k_group_done(const GInst* __restrict__ inst, int nc, int* __restrict__ out) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) out[i] = inst[i].st ? inst[i].st->finished : 1;
+}
+
+// CTA maps of a grouped launch over the live instances: for each kind, the
+// instance's own grid in order (entry (i << kGroupShift) | b for CTA b of
+// instance i).  kColMap: the per-column kernels (kp CTAs per instance).
+constexpr int kColMap = 4;
+void group_maps(const std::vector<GInst>& inst, const std::vector<int>& live, int kp, std::vector<uint32_t>& maps,
+                size_t off[6]) {
+  maps.clear();
+  for (int kind = 0; kind < 5; ++kind) {
+    off[kind] = maps.size();
+    for (int i : live) {
+      const int g = kind == kColMap ? kp : inst[i].grid[kind];
+      for (int b = 0; b < g; ++b) maps.push_back(((uint32_t)i << kGroupShift) | (uint32_t)b);
+    }
   }
-  *max_rel = mr;
-  c->bad_col = hs.bad_col;
-  c->bad_iter = hs.iter;
-  if (hs.status != GP_OK) return hs.status;
-  if (!all_done) return GP_ERR_NOT_CONVERGED;
-  return GP_OK;
+  off[5] = maps.size();
+}
+
+}  // namespace
+
+int cg_run_group(gp_ctx* owner, gp_ctx* const* cs, int nc, int k, int kp, const double* const* ys, int nv,
+                 uint64_t seed, int m_hist, int max_iter, double rtol, int check_every, bool use_pc, bool warm,
+                 int* iters, double* max_rel, int* status) {
+  if (nc < 0 || nc > kMaxGroup) return GP_ERR_INVALID_ARG;
+  if (nc == 0) return GP_OK;
+  if (check_every <= 0) check_every = 16;
+  if (check_every > 64) check_every = 64;
+  cudaStream_t s = owner->stream;
+  std::vector<CgLoop> L(nc);
+  std::vector<GInst> inst(nc);
+  std::vector<int> live;
+  std::vector<cudaEvent_t> ready(nc, nullptr);
+  int first = -1;
+  int result = GP_OK;
+  for (int i = 0; i < nc && result == GP_OK; ++i) {
+    gp_ctx* c = cs[i];
+    iters[i] = 0;
+    max_rel[i] = 0.0;
+    status[i] = GP_OK;
+    GInst& I = inst[i];
+    memset(&I, 0, sizeof(I));
+    if (c->n_act == 0) continue;
+    // the same preparation as a run on its own, with the cp.async product
+    status[i] = cg_prepare(c, k, kp, ys[i], nv, seed, m_hist, max_iter, rtol, use_pc, warm, nullptr,
+                           GP_FLAG_SPMM_CPASYNC_WIDE, &L[i]);
+    if (status[i] != GP_OK) continue;
+    if (first < 0) first = i;
+    // every instance of one grouped launch runs the same kernel
+    const CgLoop& L0 = L[first];
+    if (L[i].plan.fn != L0.plan.fn || L[i].plan.smem != L0.plan.smem || L[i].pc != L0.pc ||
+        L[i].upd_pc != L0.upd_pc || L[i].pc_smem != L0.pc_smem) {
+      result = GP_ERR_UNSUPPORTED;
+      break;
+    }
+    I.n = c->n_act;
+    I.nblk = c->nblk;
+    I.brp = (const int64_t*)c->brp.p;
+    I.bcol = (const int32_t*)c->bcol.p;
+    I.bval = (const float4*)c->bval.p;
+    I.X = (float4*)c->X.p;
+    I.R = (float4*)c->R.p;
+    I.P = (float4*)c->P.p;
+    I.Q = (float4*)c->Q.p;
+    I.Z = L[i].pc ? (float4*)c->Z.p : nullptr;
+    I.D = L[i].pc ? I.Z : I.R;
+    I.Minv = (const float*)c->pc_Minv.p;
+    I.part_a = (double*)c->part_a.p;
+    I.part_b = (double*)c->part_b.p;
+    I.hist_alpha = (double*)c->hist_alpha.p;
+    I.hist_beta = (double*)c->hist_beta.p;
+    I.st = (CgState*)c->cg.p;
+    I.grid[kGSpmm] = (int)L[i].plan.grid;
+    I.grid[kGPc] = (int)L[i].g_pc;
+    I.grid[kGUpd] = (int)L[i].g_upd;
+    I.grid[kGUpdR] = (int)L[i].g_upd_r;
+    live.push_back(i);
+    // the group's stream starts after the instance's preparation
+    GP_CUDA(cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming));
+    GP_CUDA(cudaEventRecord(ready[i], c->stream));
+    GP_CUDA(cudaStreamWaitEvent(s, ready[i], 0));
+  }
+  if (result == GP_OK && !live.empty()) {
+    const CgLoop& L0 = L[first];
+    const int kq = L0.kq;
+    const bool pc = L0.pc;
+    // instance table (uploaded once) and the finished flags after it
+    const size_t tab_bytes = (size_t)nc * sizeof(GInst);
+    GP_CHECK(ensure(owner, owner->grp_inst, tab_bytes + (size_t)nc * sizeof(int)));
+    GInst* dinst = (GInst*)owner->grp_inst.p;
+    int* ddone = (int*)((char*)owner->grp_inst.p + tab_bytes);
+    GP_CUDA(cudaMemcpyAsync(dinst, inst.data(), tab_bytes, cudaMemcpyHostToDevice, s));
+    std::vector<uint32_t> maps;
+    size_t off[6];
+    std::vector<int> done(nc);
+    bool rebuild = true;
+    const int max_checks = max_iter / check_every + 2;
+    for (int chk = 0; chk < max_checks && !live.empty(); ++chk) {
+      if (rebuild) {
+        // the CTA maps of the instances still running (the launches of the
+        // last check interval have completed: their flags were read)
+        group_maps(inst, live, kp, maps, off);
+        // (the first build is the largest: buffers never grow while a copy
+        // from or to them is queued)
+        GP_CHECK(ensure(owner, owner->grp_map, maps.size() * sizeof(uint32_t)));
+        GP_CHECK(ensure_pinned(owner, std::max(maps.size() * sizeof(uint32_t), (size_t)nc * sizeof(int))));
+        memcpy(owner->pinned, maps.data(), maps.size() * sizeof(uint32_t));
+        GP_CUDA(cudaMemcpyAsync(owner->grp_map.p, owner->pinned, maps.size() * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, s));
+        rebuild = false;
+      }
+      const uint32_t* dmap = (const uint32_t*)owner->grp_map.p;
+      const Group gs{dinst, dmap + off[kGSpmm]}, gc{dinst, dmap + off[kColMap]}, gpc{dinst, dmap + off[kGPc]},
+          gu{dinst, dmap + off[kGUpd]}, gr{dinst, dmap + off[kGUpdR]};
+      const unsigned n_spmm = (unsigned)(off[kGSpmm + 1] - off[kGSpmm]);
+      const unsigned n_pc = (unsigned)(off[kGPc + 1] - off[kGPc]);
+      const unsigned n_upd = (unsigned)(off[kGUpd + 1] - off[kGUpd]);
+      const unsigned n_updr = (unsigned)(off[kGUpdR + 1] - off[kGUpdR]);
+      const unsigned n_col = (unsigned)(off[kColMap + 1] - off[kColMap]);
+      for (int t = 0; t < check_every; ++t) {
+        // one iteration of every live instance: the launches of cg_run, each
+        // CTA taking its instance's arguments from the table
+        spmm_launch_group(L0.plan, s, n_spmm, gs);
+        k_cg_alpha_cols<<<n_col, kColThreads, 0, s>>>(nullptr, 0, k, kp, nullptr, nullptr, m_hist, gc);
+        if (pc) {
+          L0.upd_pc<<<n_pc, kPcLanes * kq, L0.pc_smem, s>>>(0, kq, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                            nullptr, gpc);
+          k_cg_beta_cols<<<n_col, kColThreads, 0, s>>>(nullptr, 0, k, kp, 1, nullptr, nullptr, m_hist, gc);
+        } else {
+          k_upd_r_f32<<<n_updr, kUpdRThreads, 0, s>>>(0, kq, nullptr, nullptr, nullptr, nullptr, gr);
+          k_cg_beta_cols<<<n_col, kColThreads, 0, s>>>(nullptr, 0, k, kp, 0, nullptr, nullptr, m_hist, gc);
+        }
+        k_upd_xp_f32<<<n_upd, kUpdThreads, 0, s>>>(0, kq, nullptr, nullptr, nullptr, nullptr, gu);
+      }
+      GP_LAUNCH_CHECK();
+      k_group_done<<<1, 256, 0, s>>>(dinst, nc, ddone);
+      GP_LAUNCH_CHECK();
+      owner->launches += 5 * check_every + 1;
+      GP_CUDA(cudaMemcpyAsync(owner->pinned, ddone, (size_t)nc * sizeof(int), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      memcpy(done.data(), owner->pinned, (size_t)nc * sizeof(int));
+      std::vector<int> still;
+      for (int i : live)
+        if (!done[i]) still.push_back(i);
+      rebuild = still.size() != live.size();
+      live.swap(still);
+    }
+  }
+  // every instance's stream continues after the group's launches
+  cudaEvent_t after = nullptr;
+  GP_CUDA(cudaEventCreateWithFlags(&after, cudaEventDisableTiming));
+  GP_CUDA(cudaEventRecord(after, s));
+  for (int i = 0; i < nc; ++i) {
+    if (ready[i]) cudaEventDestroy(ready[i]);
+    if (cs[i]->n_act == 0 || status[i] != GP_OK) continue;
+    GP_CUDA(cudaStreamWaitEvent(cs[i]->stream, after, 0));
+    if (result == GP_OK) status[i] = cg_finish(cs[i], k, &iters[i], &max_rel[i]);
+  }
+  cudaEventDestroy(after);
+  return result;
 }
 
 int cg_run_fp64(gp_ctx* c, int k, const double* y, int nv, uint64_t seed, int m_hist, int max_iter, double rtol,

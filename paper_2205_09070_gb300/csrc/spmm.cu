@@ -93,7 +93,21 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
                                                             const int32_t* __restrict__ bcol,
                                                             const float4* __restrict__ bval,
                                                             const float4* __restrict__ P, float4* __restrict__ Q,
-                                                            double* __restrict__ part, gp::CgState* st) {
+                                                            double* __restrict__ part, gp::CgState* st,
+    gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGSpmm, bx, gx);
+    n = I->n;
+    nblk = I->nblk;
+    brp = I->brp;
+    bcol = I->bcol;
+    bval = I->bval;
+    P = I->P;
+    Q = I->Q;
+    part = I->part_a;
+    st = I->st;
+  }
   const int it = st->iter;
   if (st->fin[it & 1]) return;
   constexpr int NG = 32 / G;
@@ -116,8 +130,8 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   // Work split by stored blocks, not by block rows (cluster cores hold many
   // times more blocks per row than the background).
   const int64_t nent = brp[nblk];
-  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * blockIdx.x / gridDim.x);
-  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (blockIdx.x + 1) / gridDim.x);
+  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * bx / gx);
+  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (bx + 1) / gx);
   const int64_t b0 = cb0 + w;
   if (b0 < b1) {
     // stage a chunk: consecutive lanes copy consecutive 16-byte pieces of the
@@ -234,7 +248,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32(int64_t n, int64_t n
   if (threadIdx.x < KP) {
     double t = 0.0;
     for (int ww = 0; ww < kSpmmWarps; ++ww) t += sh[ww][threadIdx.x];
-    part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
+    part[(int64_t)bx * KP + threadIdx.x] = t;
   }
 }
 
@@ -521,7 +535,21 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
                                                              const int32_t* __restrict__ bcol,
                                                              const float4* __restrict__ bval,
                                                              const float4* __restrict__ P, float4* __restrict__ Q,
-                                                             double* __restrict__ part, gp::CgState* st) {
+                                                             double* __restrict__ part, gp::CgState* st,
+    gp::Group g) {
+  int bx = blockIdx.x, gx = gridDim.x;
+  if (g.inst) {
+    const gp::GInst* I = gpd::group_cta(g, gp::kGSpmm, bx, gx);
+    n = I->n;
+    nblk = I->nblk;
+    brp = I->brp;
+    bcol = I->bcol;
+    bval = I->bval;
+    P = I->P;
+    Q = I->Q;
+    part = I->part_a;
+    st = I->st;
+  }
   const int it = st->iter;
   if (st->fin[it & 1]) return;
   static_assert(KQ % LW == 0 && LW > 1, "wide lanes");
@@ -549,8 +577,8 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
   const bool lcopy = le < EPI;
   gpd::Dot2 pq0, pq1, pq2, pq3;
   const int64_t nent = brp[nblk];
-  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * blockIdx.x / gridDim.x);
-  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (blockIdx.x + 1) / gridDim.x);
+  const int64_t cb0 = first_row_at_or_after(brp, nblk, nent * bx / gx);
+  const int64_t b1 = first_row_at_or_after(brp, nblk, nent * (bx + 1) / gx);
   const int64_t b0 = cb0 + w;
   if (b0 < b1) {
     // stage a chunk as k_bspmm_f32 does: KQ 16-byte pieces per P row, then the
@@ -685,13 +713,13 @@ __global__ void __launch_bounds__(kSpmmThreads) k_bspmm_f32w(int64_t n, int64_t 
     for (int ww = 0; ww < kSpmmWarps; ++ww)
       for (int l = 0; l < 32; ++l)
         if ((l < M * KQ ? l % KQ : -1) == q) t += shp[ww][l][cc];
-    part[(int64_t)blockIdx.x * KP + threadIdx.x] = t;
+    part[(int64_t)bx * KP + threadIdx.x] = t;
   }
 }
 
 // ---------------------------------------------------------------- host side
 typedef void (*CpAsyncFn)(int64_t, int64_t, const int64_t*, const int32_t*, const float4*, const float4*, float4*,
-                          double*, gp::CgState*);
+                          double*, gp::CgState*, gp::Group);
 typedef void (*TmaFn)(int64_t, int64_t, const int64_t*, const int32_t*, const float4*, const CUtensorMap,
                       const float4*, float4*, double*, gp::CgState*);
 
@@ -835,7 +863,8 @@ void spmm_launch(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st) {
   float4* Q = (float4*)c->Q.p;
   double* part = (double*)c->part_a.p;
   if (p.variant == GP_SPMM_CPASYNC || p.variant == GP_SPMM_CPASYNC_WIDE) {
-    void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st};
+    Group g{nullptr, nullptr};
+    void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st, &g};
     cudaLaunchKernel(p.fn, dim3(p.grid), dim3(kSpmmThreads), args, p.smem, s);
   } else {
     void* args[] = {&n, &nblk, &brp, &bcol, &bval, (void*)p.tmap, &P, &Q, &part, &st};
@@ -852,8 +881,24 @@ void spmm_launch_io(const SpmmPlan& p, cudaStream_t s, gp_ctx* c, CgState* st, c
   const float4* P = (const float4*)in;
   float4* Q = (float4*)out;
   double* part = (double*)c->part_a.p;
-  void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st};
+  Group g{nullptr, nullptr};
+  void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st, &g};
   cudaLaunchKernel(p.fn, dim3(p.grid), dim3(kSpmmThreads), args, p.smem, s);
+}
+
+void spmm_launch_group(const SpmmPlan& p, cudaStream_t s, unsigned total, Group g) {
+  if (p.variant != GP_SPMM_CPASYNC && p.variant != GP_SPMM_CPASYNC_WIDE) return;
+  // every argument but the group is taken from the instance table
+  int64_t n = 0, nblk = 0;
+  const int64_t* brp = nullptr;
+  const int32_t* bcol = nullptr;
+  const float4* bval = nullptr;
+  const float4* P = nullptr;
+  float4* Q = nullptr;
+  double* part = nullptr;
+  CgState* st = nullptr;
+  void* args[] = {&n, &nblk, &brp, &bcol, &bval, &P, &Q, &part, &st, &g};
+  cudaLaunchKernel(p.fn, dim3(total), dim3(kSpmmThreads), args, p.smem, s);
 }
 
 int spmm_select(gp_ctx* c, int kp, int flags, CgState* st, SpmmPlan* plan, int k, int m_hist) {

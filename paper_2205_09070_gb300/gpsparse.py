@@ -42,6 +42,7 @@ GP_FLAG_SPMM_WINDOW = 64
 GP_FLAG_FAULT_OOM = 128
 GP_FLAG_FAULT_NOT_SPD = 256
 GP_FLAG_FAULT_NAN = 512
+GP_FLAG_BATCH_STREAMS = 1024
 
 GP_SPMM_CPASYNC = 0
 GP_SPMM_TMA = 1

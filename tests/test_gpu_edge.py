@@ -154,21 +154,101 @@ def test_iteration_cap_reports_not_converged(G, prec):
     gp.close()
 
 
-def test_batched_matches_single_calls(G):
-    probs = W.batch_2d(seed=4, n_inst=6, n_range=(1, 4000))
-    probs[1] = W.batch_2d(seed=5, n_inst=1, n_range=(1, 1))[0]          # an instance with N = 1
+def _batch(G, seeds=(4, 5), n_inst=6, n_range=(1, 4000)):
+    probs = W.batch_2d(seed=seeds[0], n_inst=n_inst, n_range=n_range)
+    probs[1] = W.batch_2d(seed=seeds[1], n_inst=1, n_range=(1, 1))[0]          # an instance with N = 1
     offsets = np.concatenate([[0], np.cumsum([q.n for q in probs])])
-    x = np.concatenate([q.x for q in probs])
-    y = np.concatenate([q.y for q in probs])
+    x = torch.as_tensor(np.concatenate([q.x for q in probs]), device="cuda")
+    y = torch.as_tensor(np.concatenate([q.y for q in probs]), device="cuda")
     h = np.stack([q.h for q in probs])
+    return probs, offsets, x, y, h
+
+
+def _singles(G, gp, probs, o):
+    out = []
+    for q in probs:
+        out.append(gp.lml_grad(torch.as_tensor(q.x, device="cuda"), torch.as_tensor(q.y, device="cuda"), q.h, o))
+    return out
+
+
+@pytest.mark.parametrize("precond_block", [128, 0])
+def test_grouped_batch_matches_single_calls(G, precond_block):
+    """The grouped CG launches (the batched default for FP32): every
+    instance's ln L and gradient bitwise equal to its own call with the wide
+    cp.async product, with and without the block-Jacobi preconditioner."""
+    probs, offsets, x, y, h = _batch(G)
     gp = G.GP(2, 2, 4)
-    o = opts(G, "fp32")
-    lml_b, grad_b, _ = gp.lml_grad_batched(offsets, torch.as_tensor(x, device="cuda"),
-                                           torch.as_tensor(y, device="cuda"), h, o)
-    for k, q in enumerate(probs):
-        l1, g1, _ = gp.lml_grad(torch.as_tensor(q.x, device="cuda"), torch.as_tensor(q.y, device="cuda"), q.h, o)
+    o = opts(G, "fp32", precond_block=precond_block)
+    lml_b, grad_b, info = gp.lml_grad_batched(offsets, x, y, h, o)
+    one = opts(G, "fp32", precond_block=precond_block, flags=G.GP_FLAG_SPMM_CPASYNC_WIDE)
+    singles = _singles(G, gp, probs, one)
+    for k, (l1, g1, _) in enumerate(singles):
+        assert lml_b[k] == l1, (k, probs[k].n)
+        assert np.array_equal(grad_b[k], g1), (k, probs[k].n)
+    assert info["iters"] == max(i["iters"] for _, _, i in singles)
+    gp.close()
+
+
+def test_worker_stream_batch_matches_single_calls(G):
+    """GP_FLAG_BATCH_STREAMS: whole instances on the worker streams, each
+    bitwise equal to its own call with the same options."""
+    probs, offsets, x, y, h = _batch(G)
+    gp = G.GP(2, 2, 4)
+    o = opts(G, "fp32", flags=G.GP_FLAG_BATCH_STREAMS)
+    lml_b, grad_b, _ = gp.lml_grad_batched(offsets, x, y, h, o)
+    for k, (l1, g1, _) in enumerate(_singles(G, gp, probs, opts(G, "fp32"))):
         assert lml_b[k] == l1
         assert np.array_equal(grad_b[k], g1)
+    gp.close()
+
+
+def test_grouped_batch_retires_instances_at_their_own_counts(G):
+    """Instances whose runs need very different iteration counts (sizes 200 to
+    12,000 points, r_s from 0.02 to 0.08) in one group: each leaves the
+    grouped launches when its own run finishes, so its count and result equal
+    its own call's."""
+    probs, offsets, x, y, h = _batch(G, seeds=(9, 10), n_inst=24, n_range=(200, 12000))
+    gp = G.GP(2, 2, 4)
+    o = opts(G, "fp32", check_every=4)
+    lml_b, grad_b, info = gp.lml_grad_batched(offsets, x, y, h, o)
+    one = opts(G, "fp32", check_every=4, flags=G.GP_FLAG_SPMM_CPASYNC_WIDE)
+    singles = _singles(G, gp, probs, one)
+    counts = [i["iters"] for _, _, i in singles]
+    assert max(counts) > 2 * min(c for c in counts if c > 0)
+    for k, (l1, g1, _) in enumerate(singles):
+        assert lml_b[k] == l1 and np.array_equal(grad_b[k], g1), k
+    # a second call on the same context reuses the workspaces and gives the same
+    lml_c, grad_c, _ = gp.lml_grad_batched(offsets, x, y, h, o)
+    assert np.array_equal(lml_b, lml_c) and np.array_equal(grad_b, grad_c)
+    gp.close()
+
+
+def test_grouped_batch_in_two_waves(G):
+    """260 small instances: two waves of grouped launches (256, then 4) on
+    the same worker workspaces, every instance bitwise equal to its own call."""
+    probs = W.batch_2d(seed=13, n_inst=260, n_range=(1, 300))
+    offsets = np.concatenate([[0], np.cumsum([q.n for q in probs])])
+    x = torch.as_tensor(np.concatenate([q.x for q in probs]), device="cuda")
+    y = torch.as_tensor(np.concatenate([q.y for q in probs]), device="cuda")
+    h = np.stack([q.h for q in probs])
+    gp = G.GP(2, 2, 4)
+    lml_b, grad_b, _ = gp.lml_grad_batched(offsets, x, y, h, opts(G, "fp32"))
+    one = opts(G, "fp32", flags=G.GP_FLAG_SPMM_CPASYNC_WIDE)
+    for k, (l1, g1, _) in enumerate(_singles(G, gp, probs, one)):
+        assert lml_b[k] == l1 and np.array_equal(grad_b[k], g1), (k, probs[k].n)
+    gp.close()
+
+
+def test_grouped_batch_reports_the_iteration_cap(G):
+    probs, offsets, x, y, h = _batch(G)
+    gp = G.GP(2, 2, 4)
+    for flags in (0, G.GP_FLAG_BATCH_STREAMS):
+        with pytest.raises(G.GPError) as e:
+            gp.lml_grad_batched(offsets, x, y, h, opts(G, "fp32", max_iter=3, check_every=1, flags=flags))
+        assert e.value.status == G.GP_ERR_NOT_CONVERGED
+    # the context stays usable
+    lml_b, _, _ = gp.lml_grad_batched(offsets, x, y, h, opts(G, "fp32"))
+    assert np.all(np.isfinite(lml_b))
     gp.close()
 
 
