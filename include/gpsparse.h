@@ -225,6 +225,49 @@ int gp_sparsity_estimate(const gp_kernel_desc* desc, const double* h, double dom
 int gp_augmented(const gp_kernel_desc* desc, const double* h, double domain_volume, double lml,
                  const double* lml_grad, double* value, double* grad, double* s_out);
 
+/* gp_train objectives (Sec. 2.4; the paper names gradient-based training as
+ * future work, Sec. 4):
+ *   GP_OBJ_LML          ln L(h)
+ *   GP_OBJ_AUGMENTED    (2 - s(h)) ln L(h), Eq. eq:augmented (gp_augmented)
+ *   GP_OBJ_CONSTRAINED  ln L(h) subject to s(h) < s_max, Eq. eq:constrained */
+#define GP_OBJ_LML 0
+#define GP_OBJ_AUGMENTED 1
+#define GP_OBJ_CONSTRAINED 2
+
+typedef struct {
+  int32_t objective;      /* GP_OBJ_* */
+  int32_t n_steps;        /* ascent steps, 0..100000 (each needs one gp_lml_grad evaluation) */
+  double lr;              /* Adam step size (> 0) in the parametrisation of gp_train */
+  double beta1, beta2;    /* Adam moment decays in [0, 1) (0, 0: 0.9, 0.999) */
+  double eps;             /* Adam denominator guard (> 0; 0: 1e-8) */
+  double domain_volume;   /* V of the sparsity estimate s(h) (gp_sparsity_estimate), > 0 */
+  double s_max;           /* GP_OBJ_CONSTRAINED: the sparsity requirement; s(h) < s_max at the start */
+  int32_t max_halvings;   /* GP_OBJ_CONSTRAINED: halvings of a step that would reach s >= s_max
+                             before the step is skipped (0: 30) */
+} gp_train_opts;
+
+/* Gradient ascent on an objective of the hyperparameters h (gp_n_params
+ * doubles, host, updated in place) for the data x, y (as gp_lml_grad), with
+ * Adam (Kingma and Ba, 2015) on theta: theta_q = ln h_q for the entries that
+ * must stay positive (bump radii, r_s, A, sigma_n^2 and the core length
+ * scale; A must then start > 0), theta_q = h_q for centres and amplitudes, so
+ * d obj / d theta_q = h_q d obj / d h_q for the former.  Step t (1-based):
+ *   g = d obj / d theta at h_{t-1} (ln L and its gradient from gp_lml_grad
+ *       with opts, s and its gradient from gp_sparsity_estimate),
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   theta += lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * GP_OBJ_CONSTRAINED keeps every iterate feasible: a step that would reach
+ * s >= s_max is halved until s < s_max, and skipped after max_halvings
+ * halvings (s depends on the radii alone, so this needs no evaluation).
+ * trace (may be NULL): (n_steps + 1) rows of 3 doubles, (objective, ln L, s)
+ * at h_0 .. h_{n_steps}; info (may be NULL) describes the last evaluation.
+ * Errors: GP_ERR_INVALID_ARG for bad options, a non-positive A, or an
+ * infeasible start; an evaluation's error (GP_ERR_NOT_CONVERGED included)
+ * stops the run and is returned, with h the iterate it was evaluated at and
+ * the trace filled up to the row before it. */
+int gp_train(gp_ctx* ctx, const double* x, const double* y, int64_t n, double* h, const gp_opts* opts,
+             const gp_train_opts* train, double* trace, gp_info* info);
+
 /* Default options: FP32_MIXED, 32 probes, 50 Lanczos steps, 10000 iterations,
  * rtol 1e-6, seed 0x5eed, check every 16 iterations, precond_block 128. */
 void gp_default_opts(gp_opts* opts);

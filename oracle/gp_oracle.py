@@ -18,6 +18,9 @@ Paper sections used (arXiv 2205.09070):
   * Sec. 2.2, Eq. (eq:kstat): the compactly supported stationary kernel k~.
   * Sec. 2.2, Eq. (eq:sparsity_estimate) and the two equations after it: the
     sparsity upper bound used as a statistical check.
+  * Sec. 2.4, Eqs. (eq:constrained) and (eq:augmented): the training
+    objectives, driven by Adam (a reading: Sec. 4 names gradient-based
+    training as future work without a method).
   * Sec. 2.5: CG for K x = y and a randomized log-determinant (the cited
     estimator of Boutsidis et al., truncated Taylor series of ln(I - C) with
     Hutchinson probes, beside stochastic Lanczos quadrature).
@@ -830,3 +833,82 @@ def augmented_objective(lml, grad_lml, h, dim, n1, n2, domain_volume=1.0):
     s = sparsity_upper_bound(h, dim, n1, n2, domain_volume)
     ds = sparsity_upper_bound_grad(h, dim, n1, n2, domain_volume)
     return (2.0 - s) * lml, (2.0 - s) * np.asarray(grad_lml, dtype=np.float64) - lml * ds, s
+
+
+# ----------------------------------------------------------------------------
+# gradient-based training on the objectives of Sec. 2.4 (Sec. 4 names
+# gradient-based optimisation of the hyperparameters as future work and fixes
+# no method: the reading here is Adam, Kingma and Ba 2015, Algorithm 1)
+# ----------------------------------------------------------------------------
+def positive_entries(n_params, dim, n1, n2):
+    """Entries of h that must stay positive and are stepped in ln h: every bump
+    radius, then r_s, A, sigma_n^2 (and the core length scale, if present)."""
+    pos = np.zeros(n_params, dtype=bool)
+    for b in range(n1 * n2):
+        pos[b * (dim + 2) + dim] = True
+    pos[n1 * n2 * (dim + 2):] = True
+    return pos
+
+
+def adam_ascent(objective, h0, positive, n_steps, lr, beta1=0.9, beta2=0.999, eps=1e-8, feasible=None,
+                max_halvings=30):
+    """Adam ascending objective(h) -> (value, d value / d h, extra) over
+    theta = ln h on the positive entries and theta = h elsewhere, so that
+    d value / d theta = h * d value / d h there.  Step t = 1, 2, ...:
+      m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+      theta <- theta + lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+    With feasible(h) given (the constraint of Eq. eq:constrained), a step whose
+    end is infeasible is halved until it is feasible and not taken after
+    max_halvings halvings.  Returns (h_n, [(value, extra) at h_0 .. h_n])."""
+    h = np.array(h0, dtype=np.float64)
+    m = np.zeros_like(h)
+    v = np.zeros_like(h)
+    trace = []
+    for t in range(1, n_steps + 2):
+        value, grad_h, extra = objective(h)
+        trace.append((value, extra))
+        if t == n_steps + 1:
+            break
+        g = np.where(positive, h * grad_h, grad_h)
+        m = beta1 * m + (1.0 - beta1) * g
+        v = beta2 * v + (1.0 - beta2) * g * g
+        step = lr * (m / (1.0 - beta1 ** t)) / (np.sqrt(v / (1.0 - beta2 ** t)) + eps)
+        f = 1.0
+        for _ in range(max_halvings + 1):
+            h_new = h + f * step
+            h_new[positive] = np.exp(np.log(h[positive]) + f * step[positive])
+            if feasible is None or feasible(h_new):
+                break
+            f *= 0.5
+        else:
+            h_new = h.copy()
+        h = h_new
+    return h, trace
+
+
+def train_same_probes(x, y, h0, dim, n1, n2, n_probes, lanczos_steps, seed, objective, n_steps, lr,
+                      beta1=0.9, beta2=0.999, eps=1e-8, domain_volume=1.0, s_max=None, max_halvings=30,
+                      beta=1.0):
+    """Adam on one of the Sec. 2.4 objectives with the same-probe estimator of
+    ln L and its gradient (lml_grad_same_probes) and the sparsity bound s(h):
+      "lml"          ln L
+      "augmented"    (2 - s) ln L, Eq. eq:augmented
+      "constrained"  ln L with every iterate kept at s(h) < s_max, Eq. eq:constrained.
+    Returns (h_n, trace rows (objective, ln L, s) at h_0 .. h_n)."""
+    h0 = np.asarray(h0, dtype=np.float64)
+
+    def obj(h):
+        lml, g, _ = lml_grad_same_probes(x, y, h, dim, n1, n2, n_probes, lanczos_steps, seed, beta=beta)
+        if objective == "augmented":
+            value, grad, s = augmented_objective(lml, g, h, dim, n1, n2, domain_volume)
+        else:
+            value, grad, s = lml, g, sparsity_upper_bound(h, dim, n1, n2, domain_volume)
+        return value, grad, (lml, s)
+
+    feasible = None
+    if objective == "constrained":
+        def feasible(h):
+            return sparsity_upper_bound(h, dim, n1, n2, domain_volume) < s_max
+    h, trace = adam_ascent(obj, h0, positive_entries(len(h0), dim, n1, n2), n_steps, lr, beta1, beta2, eps,
+                           feasible, max_halvings)
+    return h, np.array([[value, lml, s] for value, (lml, s) in trace])

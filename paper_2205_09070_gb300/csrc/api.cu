@@ -696,6 +696,80 @@ int gp_lml_grad(gp_ctx* c, const double* x, const double* y, int64_t n, const do
   return evaluate(c, x, y, n, h, o, lml, grad, info);
 }
 
+int gp_train(gp_ctx* c, const double* x, const double* y, int64_t n, double* h, const gp_opts* o,
+             const gp_train_opts* t, double* trace, gp_info* info) {
+  if (!c || !h || !o || !t) return GP_ERR_INVALID_ARG;
+  if (t->objective < GP_OBJ_LML || t->objective > GP_OBJ_CONSTRAINED || t->n_steps < 0 || t->n_steps > 100000 ||
+      !(t->lr > 0.0) || !isfinite(t->lr) || !(t->domain_volume > 0.0) || !isfinite(t->domain_volume) ||
+      t->max_halvings < 0 || t->max_halvings > 1000)
+    return GP_ERR_INVALID_ARG;
+  double b1 = t->beta1, b2 = t->beta2, eps = t->eps;
+  if (b1 == 0.0 && b2 == 0.0) {
+    b1 = 0.9;
+    b2 = 0.999;
+  }
+  if (eps == 0.0) eps = 1e-8;
+  if (!(b1 >= 0.0 && b1 < 1.0) || !(b2 >= 0.0 && b2 < 1.0) || !(eps > 0.0) || !isfinite(eps))
+    return GP_ERR_INVALID_ARG;
+  const bool constrained = t->objective == GP_OBJ_CONSTRAINED;
+  if (constrained && !(t->s_max > 0.0 && isfinite(t->s_max))) return GP_ERR_INVALID_ARG;
+  const int halvings = t->max_halvings > 0 ? t->max_halvings : 30;
+  GP_CHECK(check_h(c, h));
+  const gp_kernel_desc d{c->dim, c->n1, c->n2, c->beta, c->core};
+  const int64_t np = gp_n_params(&d);
+  const int bp = c->dim + 2;
+  // entries stepped in ln h: the bump radii, then r_s, A, sigma_n^2 (and l)
+  std::vector<char> logp((size_t)np, 0);
+  for (int b = 0; b < c->nb; ++b) logp[(size_t)b * bp + c->dim] = 1;
+  for (int64_t q = (int64_t)c->nb * bp; q < np; ++q) logp[(size_t)q] = 1;
+  if (!(h[(int64_t)c->nb * bp + 1] > 0.0)) return GP_ERR_INVALID_ARG;  // A
+  std::vector<double> gl((size_t)np), ds((size_t)np), m((size_t)np, 0.0), v((size_t)np, 0.0), delta((size_t)np),
+      hn((size_t)np);
+  double s = 0.0;
+  GP_CHECK(gp_sparsity_estimate(&d, h, t->domain_volume, &s, nullptr));
+  if (constrained && !(s < t->s_max)) return GP_ERR_INVALID_ARG;
+  for (int step = 0;; ++step) {
+    double lml = 0.0;
+    const int st = evaluate(c, x, y, n, h, o, &lml, gl.data(), info);
+    if (st != GP_OK) return st;
+    GP_CHECK(gp_sparsity_estimate(&d, h, t->domain_volume, &s, ds.data()));
+    const bool aug = t->objective == GP_OBJ_AUGMENTED;
+    const double obj = aug ? (2.0 - s) * lml : lml;
+    if (trace) {
+      trace[3 * step] = obj;
+      trace[3 * step + 1] = lml;
+      trace[3 * step + 2] = s;
+    }
+    if (step == t->n_steps) break;
+    // Adam on theta (bias-corrected moments of d obj / d theta)
+    const double c1 = 1.0 - pow(b1, step + 1), c2 = 1.0 - pow(b2, step + 1);
+    for (int64_t q = 0; q < np; ++q) {
+      const double gh = aug ? (2.0 - s) * gl[q] - lml * ds[q] : gl[q];  // d obj / d h_q
+      const double g = logp[q] ? h[q] * gh : gh;
+      if (!isfinite(g)) return GP_ERR_INVALID_ARG;
+      m[q] = b1 * m[q] + (1.0 - b1) * g;
+      v[q] = b2 * v[q] + (1.0 - b2) * g * g;
+      delta[q] = t->lr * (m[q] / c1) / (sqrt(v[q] / c2) + eps);
+    }
+    // h_t = h(theta + f delta): f = 1, halved while the constraint fails
+    double f = 1.0;
+    for (int k = 0;; ++k) {
+      for (int64_t q = 0; q < np; ++q) hn[q] = logp[q] ? h[q] * exp(f * delta[q]) : h[q] + f * delta[q];
+      if (!constrained) break;
+      double sn = 0.0;
+      GP_CHECK(gp_sparsity_estimate(&d, hn.data(), t->domain_volume, &sn, nullptr));
+      if (sn < t->s_max) break;
+      if (k == halvings) {
+        for (int64_t q = 0; q < np; ++q) hn[q] = h[q];  // no feasible step: stay
+        break;
+      }
+      f *= 0.5;
+    }
+    memcpy(h, hn.data(), (size_t)np * sizeof(double));
+  }
+  return GP_OK;
+}
+
 int gp_lml_grad_batched(gp_ctx* c, int32_t n_inst, const int64_t* offsets, const double* x, const double* y,
                         const double* h, const gp_opts* o, double* lml, double* grad, gp_info* info) {
   if (!c || !o || n_inst < 0 || (n_inst > 0 && (!offsets || !h || !lml))) return GP_ERR_INVALID_ARG;

@@ -54,7 +54,13 @@ SPMM_FLAGS = {"cpasync": GP_FLAG_SPMM_CPASYNC, "tma": GP_FLAG_SPMM_TMA, "tma_wid
 
 EXPORTED = ["gp_n_params", "gp_default_opts", "gp_create", "gp_destroy", "gp_set_stream", "gp_assemble",
             "gp_get_csr", "gp_get_csr_noalloc", "gp_solve", "gp_predict", "gp_lml", "gp_lml_grad",
-            "gp_lml_grad_batched", "gp_status_string", "gp_sparsity_estimate", "gp_augmented", "gp_predict_var"]
+            "gp_lml_grad_batched", "gp_status_string", "gp_sparsity_estimate", "gp_augmented", "gp_predict_var",
+            "gp_train"]
+
+GP_OBJ_LML = 0
+GP_OBJ_AUGMENTED = 1
+GP_OBJ_CONSTRAINED = 2
+OBJECTIVES = {"lml": GP_OBJ_LML, "augmented": GP_OBJ_AUGMENTED, "constrained": GP_OBJ_CONSTRAINED}
 
 
 GP_CORE_NONE = 0
@@ -64,6 +70,12 @@ GP_CORE_SQEXP = 1
 class KernelDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_funcs", ctypes.c_int32), ("n_bumps", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("core", ctypes.c_int32)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("domain_volume", ctypes.c_double), ("s_max", ctypes.c_double), ("max_halvings", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -133,6 +145,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                         ctypes.POINTER(Info)]
     lib.gp_sparsity_estimate.argtypes = [ctypes.POINTER(KernelDesc), dp, ctypes.c_double, dp, dp]
     lib.gp_augmented.argtypes = [ctypes.POINTER(KernelDesc), dp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
+    lib.gp_train.argtypes = [vp, dp, dp, i64, dp, ctypes.POINTER(Opts), ctypes.POINTER(TrainOpts), dp,
+                             ctypes.POINTER(Info)]
     lib.gp_status_string.argtypes = [ctypes.c_int]
     lib.gp_status_string.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_destroy", "gp_set_stream", "gp_assemble", "gp_get_csr", "gp_get_csr_noalloc",
@@ -381,6 +395,26 @@ class GP:
         self._check(self._lib.gp_lml_grad(self._h, xp, yp, int(x.shape[0]), hh.ctypes.data, ctypes.byref(o),
                                           ctypes.byref(out), gp_, ctypes.byref(info)), "gp_lml_grad", allow)
         return out.value, grad, info.as_dict()
+
+    def train(self, x, y, h, opts: Opts | None = None, objective="lml", n_steps=10, lr=0.01, beta1=0.0,
+              beta2=0.0, eps=0.0, domain_volume=1.0, s_max=0.0, max_halvings=0, allow_not_converged=False):
+        """gp_train: Adam ascent on ln L, (2 - s) ln L or ln L with s < s_max.
+        Returns (h after the steps, trace rows (objective, ln L, s) at each
+        iterate, info of the last evaluation)."""
+        self._sync_stream()
+        o = opts or default_opts()
+        t = TrainOpts(OBJECTIVES[objective] if isinstance(objective, str) else int(objective), int(n_steps),
+                      float(lr), float(beta1), float(beta2), float(eps), float(domain_volume), float(s_max),
+                      int(max_halvings))
+        xp, xk = _ptr(x)
+        yp, yk = _ptr(y)
+        hh = self._hyper(h).copy()
+        trace = np.zeros((max(int(n_steps), 0) + 1, 3), np.float64)
+        info = Info()
+        allow = (GP_OK, GP_ERR_NOT_CONVERGED) if allow_not_converged else (GP_OK,)
+        self._check(self._lib.gp_train(self._h, xp, yp, int(x.shape[0]), hh.ctypes.data, ctypes.byref(o),
+                                       ctypes.byref(t), trace.ctypes.data, ctypes.byref(info)), "gp_train", allow)
+        return hh, trace, info.as_dict()
 
     def lml_grad_batched(self, offsets, x, y, h, opts: Opts | None = None, with_grad=True):
         self._sync_stream()
