@@ -171,11 +171,12 @@ def _singles(G, gp, probs, o):
     return out
 
 
-@pytest.mark.parametrize("precond_block", [128, 0])
+@pytest.mark.parametrize("precond_block", [128, 64, 16, 0])
 def test_grouped_batch_matches_single_calls(G, precond_block):
     """The grouped CG launches (the batched default for FP32): every
     instance's ln L and gradient bitwise equal to its own call with the wide
-    cp.async product, with and without the block-Jacobi preconditioner."""
+    cp.async product, for each form of the block-Jacobi apply (128-, 64- and
+    16-row blocks) and without the preconditioner."""
     probs, offsets, x, y, h = _batch(G)
     gp = G.GP(2, 2, 4)
     o = opts(G, "fp32", precond_block=precond_block)
