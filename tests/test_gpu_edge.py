@@ -190,6 +190,19 @@ def test_grouped_batch_matches_single_calls(G, precond_block):
     gp.close()
 
 
+def test_grouped_batch_from_host_inputs(G):
+    """Host arrays for x, y, lml and grad: each instance is staged in on its
+    own worker stream before the grouped launches, with the device-input
+    results bit for bit."""
+    probs, offsets, x, y, h = _batch(G)
+    gp = G.GP(2, 2, 4)
+    o = opts(G, "fp32")
+    lml_d, grad_d, _ = gp.lml_grad_batched(offsets, x, y, h, o)
+    lml_h, grad_h, _ = gp.lml_grad_batched(offsets, x.cpu().numpy(), y.cpu().numpy(), h, o)
+    assert np.array_equal(lml_d, lml_h) and np.array_equal(grad_d, grad_h)
+    gp.close()
+
+
 def test_worker_stream_batch_matches_single_calls(G):
     """GP_FLAG_BATCH_STREAMS: whole instances on the worker streams, each
     bitwise equal to its own call with the same options."""
