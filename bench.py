@@ -445,8 +445,8 @@ def main():
 
     roofline = roof(kname, bytes_spmm, spmm_ms, traffic=trec["bytes_per_launch"] if trec else None,
                     launches_timed=n_spmm, share_of_step=(t_spmm / len(tinfos)) / (ms / a.steps),
-                    limiter=("L1/shared data pipe: gathers of 144-byte P rows staged through shared memory "
-                             "(ncu: l1tex throughput 66-77 % of peak, DRAM 17 %)")
+                    limiter=("issue and latency at 12 warps per SM over gathers of 144-byte P rows staged "
+                             "through shared memory (ncu: 50 % issue active, l1tex 54 % of peak, DRAM about 20 %)")
                     if kname.startswith("k_bspmm_f32") else
                     ("latency: one persistent CTA of 8 consumer warps per SM, warps paced by the slowest "
                      "block row of each tile") if kname.startswith("k_wspmm") else "TMA gather4 request rate")
