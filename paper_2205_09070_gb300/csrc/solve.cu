@@ -1818,11 +1818,17 @@ int cg_run_group(gp_ctx* owner, gp_ctx* const* cs, int nc, int k, int kp, const 
     I.grid[kGUpdR] = (int)L[i].g_upd_r;
     live.push_back(i);
     // the group's stream starts after the instance's preparation
-    GP_CUDA(cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming));
-    GP_CUDA(cudaEventRecord(ready[i], c->stream));
-    GP_CUDA(cudaStreamWaitEvent(s, ready[i], 0));
+    cudaError_t ce = cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ready[i], c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ready[i], 0);
+    if (ce != cudaSuccess) {
+      result = cuda_status(ce);
+      break;
+    }
   }
-  if (result == GP_OK && !live.empty()) {
+  // the iterations; a failure inside still reaches the ordering below, so no
+  // instance's buffers are reused while a grouped launch may read them
+  auto iterate = [&]() -> int {
     const CgLoop& L0 = L[first];
     const int kq = L0.kq;
     const bool pc = L0.pc;
@@ -1887,18 +1893,28 @@ int cg_run_group(gp_ctx* owner, gp_ctx* const* cs, int nc, int k, int kp, const 
       rebuild = still.size() != live.size();
       live.swap(still);
     }
-  }
+    return GP_OK;
+  };
+  if (result == GP_OK && !live.empty()) result = iterate();
   // every instance's stream continues after the group's launches
   cudaEvent_t after = nullptr;
-  GP_CUDA(cudaEventCreateWithFlags(&after, cudaEventDisableTiming));
-  GP_CUDA(cudaEventRecord(after, s));
+  cudaError_t e = cudaEventCreateWithFlags(&after, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(after, s);
+  if (e != cudaSuccess) {
+    // no event to order by: wait for the group's stream instead
+    cudaStreamSynchronize(s);
+    if (result == GP_OK) result = cuda_status(e);
+  }
   for (int i = 0; i < nc; ++i) {
     if (ready[i]) cudaEventDestroy(ready[i]);
     if (cs[i]->n_act == 0 || status[i] != GP_OK) continue;
-    GP_CUDA(cudaStreamWaitEvent(cs[i]->stream, after, 0));
+    if (e == cudaSuccess) {
+      const cudaError_t w = cudaStreamWaitEvent(cs[i]->stream, after, 0);
+      if (w != cudaSuccess && result == GP_OK) result = cuda_status(w);
+    }
     if (result == GP_OK) status[i] = cg_finish(cs[i], k, &iters[i], &max_rel[i]);
   }
-  cudaEventDestroy(after);
+  if (after) cudaEventDestroy(after);
   return result;
 }
 
