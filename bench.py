@@ -57,6 +57,8 @@ def args_parse():
     ap.add_argument("--cpu-sample", type=int, default=1200)
     ap.add_argument("--n5m", type=int, default=1, help="add the 5M-point leg to the 1M line (0: skip)")
     ap.add_argument("--batch", type=int, default=1, help="add the 256-instance leg to the 1M line (0: skip)")
+    ap.add_argument("--batch-only", type=int, default=0,
+                    help="run only the many-instance leg's grouped path, on its first N instances (profiling runs)")
     ap.add_argument("--precond-block", type=int, default=None,
                     help="block-Jacobi block size of the preconditioned CG (default: the library's)")
     ap.add_argument("--spmm", default="auto", choices=["auto", "cpasync", "tma", "tma_wide", "cpasync_wide", "window"],
@@ -297,7 +299,7 @@ def leg_5m(GP, default_opts, spmm_flag, pc_kw, dev, local, stream, a):
     return out
 
 
-def leg_batch(GP, default_opts, dev, local, stream):
+def leg_batch(GP, default_opts, dev, local, stream, n_inst=256, streams=True):
     """The many-instance configuration: 256 independent 2-D GPs, N_i uniform in
     [1,000, 50,000], each with its own 2 x 4 bumps and r_s, y plus 16 probes,
     32 Lanczos steps, rtol 1e-6, LML + gradient per instance through
@@ -307,7 +309,7 @@ def leg_batch(GP, default_opts, dev, local, stream):
     import torch
     from paper_2205_09070_gb300 import workloads as W
     from paper_2205_09070_gb300.gpsparse import GP_FLAG_BATCH_STREAMS
-    probs = W.batch_2d(seed=4)
+    probs = W.batch_2d(seed=4)[:n_inst]
     offsets = np.concatenate([[0], np.cumsum([q.n for q in probs])])
     x = torch.as_tensor(np.concatenate([q.x for q in probs]), device=dev)
     y = torch.as_tensor(np.concatenate([q.y for q in probs]), device=dev)
@@ -327,16 +329,19 @@ def leg_batch(GP, default_opts, dev, local, stream):
         return e0.elapsed_time(e1), lml, info
 
     ms, lml, info = timed(0)
-    ms_s, lml_s, _ = timed(GP_FLAG_BATCH_STREAMS)
+    if streams:
+        ms_s, lml_s, _ = timed(GP_FLAG_BATCH_STREAMS)
     gp.close()
-    return {"workload": "batch_2d", "n_inst": len(probs), "n_total": int(offsets[-1]),
-            "n_active": info["n_active"], "nnz": info["nnz"], "value": len(probs) / (ms * 1e-3),
-            "unit": "instance evals/s", "ms_per_batch": ms, "max_iters": info["iters"],
-            "path": "grouped CG launches: the iterations of all running instances in single launches",
-            "lml_finite": bool(np.all(np.isfinite(lml))),
-            "worker_streams": {"value": len(probs) / (ms_s * 1e-3), "ms_per_batch": ms_s,
-                               "path": "each instance on its own on 8 worker streams",
-                               "lml_max_abs_diff": float(np.max(np.abs(lml - lml_s)))}}
+    out = {"workload": "batch_2d", "n_inst": len(probs), "n_total": int(offsets[-1]),
+           "n_active": info["n_active"], "nnz": info["nnz"], "value": len(probs) / (ms * 1e-3),
+           "unit": "instance evals/s", "ms_per_batch": ms, "max_iters": info["iters"],
+           "path": "grouped CG launches: the iterations of all running instances in single launches",
+           "lml_finite": bool(np.all(np.isfinite(lml)))}
+    if streams:
+        out["worker_streams"] = {"value": len(probs) / (ms_s * 1e-3), "ms_per_batch": ms_s,
+                                 "path": "each instance on its own on 8 worker streams",
+                                 "lml_max_abs_diff": float(np.max(np.abs(lml - lml_s)))}
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -363,6 +368,10 @@ def main():
     from paper_2205_09070_gb300 import GP, default_opts
     from paper_2205_09070_gb300.gpsparse import GP_FLAG_TIME_KERNELS
 
+    if a.batch_only > 0:
+        print(json.dumps({"batch_only": leg_batch(GP, default_opts, dev, local, torch.cuda.current_stream(dev),
+                                                  a.batch_only, streams=False)}))
+        return
     p = workload(a.n)
     x = torch.as_tensor(p.x, device=dev)
     y = torch.as_tensor(p.y, device=dev)
